@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark of the IMF hot path on GB300: orientation-convolutions/s.
+
+One step = one pass of the hot path over one synthetic design with the tools already set
+(Alg. 1 then the sensitivity penalty of Eq. eq_filtered_sens): imf_compute followed by
+imf_penalize_sensitivity, both through the C ABI on the current CUDA stream. Tool rotation,
+resampling and spectra (imf_set_tool) are per-tool-set setup and run before timing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ...]
+
+Default workload: 3D beams 128^3, 40 beams (r 2-5), 6-voxel base-plate fixture, cylinder cutter
+r=3 L=20 with holder r=8 L=16, 64 Fibonacci-hemisphere orientations, FP32 FFT path with the
+near-threshold re-check. Under torchrun (N > 1) every rank runs its own design (weak scaling,
+no data-path collective); only the step timing is reduced (max over ranks).
+
+Rank 0 prints one JSON line. `--impl reference` times the FP64 CPU oracle (the only other
+place this file runs it) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "orientation-convolutions/s (voxels x orientations/s) at stated IMF error; p50/p99 latency"
+UNIT = "voxel-orientations/s"
+
+WORKLOADS = {
+    "beams128": dict(n=128, n_beams=40, n_orient=64),
+    "beams256": dict(n=256, n_beams=120, n_orient=128),
+    "beams64": dict(n=64, n_beams=10, n_orient=16),
+}
+
+
+def make_design(name, seed):
+    from paper_2002_07627_gb300 import synth
+    if name == "planar64":
+        return synth.config_planar64(seed=seed)
+    w = WORKLOADS[name]
+    return synth.config_beams(w["n"], w["n_beams"], w["n_orient"], seed=seed)
+
+
+def workload_config(name, d):
+    t = d.tools[0]
+    nz, ny, nx = d.rho.shape
+    return {"workload": f"IMF {name}: {nx}x{ny}x{nz} grid, {len(t.quats)} orientations, one design per call",
+            "grid": [nx, ny, nz], "n_orient": int(len(t.quats)),
+            "tool": "cylinder cutter r=3 L=20 + holder r=8 L=16" if name != "planar64" else "3x12 cutter + 9x10 holder",
+            "fixture": "base plate" if name != "planar64" else "bottom 4 rows",
+            "precision": "FP32 FFT, FP64 near-threshold re-check and normalisation",
+            "step": "imf_compute + imf_penalize_sensitivity"}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d.get("bf16_tflops", 1900.0)), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(kernel, info, shape, nb):
+    """Bytes a launch must move at minimum (per launch, nb orientations), by kernel class."""
+    Px, Py, Pz = info.P
+    Hx = Px // 2 + 1
+    Wx, Wy, Wz = info.win
+    nz, ny, nx = shape
+    nG = nx * ny * nz
+    bitsw = (Wx + 31) // 32 * 4
+    spec = Pz * Py * Hx * 8
+    if kernel == "fft_z_inv_mul":
+        return nb * spec + spec + nb * Wz * Py * Hx * 8
+    if kernel == "fft_y_inv":
+        return nb * (Wz * Py * Hx * 8 + Wz * Wy * Hx * 8)
+    if kernel == "irfft_x_threshold":
+        return nb * (Wz * Wy * Hx * 8 + Wz * Wy * Wx * 4 + Wz * Wy * bitsw)
+    if kernel == "erode_min":
+        return nb * Wz * Wy * Wx * 4 + 2 * nG * 4
+    if kernel == "sweep_dilate":
+        return nb * Wz * Wy * bitsw + 2 * nz * ny * ((nx + 31) // 32) * 4
+    if kernel == "rfft_x_fwd":
+        return nG * 5 + nz * ny * Hx * 8
+    if kernel == "fft_axis_fwd":
+        return nz * ny * Hx * 8 + nz * Py * Hx * 8
+    if kernel == "finalize":
+        return nG * (4 + 4 + 1 + 4 + 1) + nz * ny * ((nx + 31) // 32) * 4
+    if kernel == "penalize":
+        return nG * (4 + 4 + 4 + 1 + 4)
+    return None
+
+
+def traffic_record(kernel):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if the kernel source is
+    unchanged since the capture (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    rec = d.get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != rec.get("source_sha256_16"):
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def run_cpu_oracle_sample(d, block, seed=0):
+    import oracle
+    nz, ny, nx = d.rho.shape
+    rng = np.random.default_rng(seed)
+    x0 = [int(rng.integers(0, max(1, nx - block + 1))), int(rng.integers(0, max(1, ny - block + 1))),
+          int(rng.integers(0, max(1, nz - block + 1)))]
+    ext = [min(block, nx), min(block, ny), min(block, nz)]
+    t0 = time.perf_counter()
+    oracle.imf_subblock(d, x0, ext)
+    dt = time.perf_counter() - t0
+    units = ext[0] * ext[1] * ext[2] * sum(len(t.quats) for t in d.tools)
+    return units, dt, x0, ext
+
+
+def oracle_cores():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else os.cpu_count()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    d = make_design(args.workload, 0)
+    block = 12 if args.workload != "planar64" else 64
+    for _ in range(args.warmup):
+        run_cpu_oracle_sample(d, block)
+    times, units = [], 0
+    for k in range(args.steps):
+        u, dt, x0, ext = run_cpu_oracle_sample(d, block, seed=k)
+        times.append(dt)
+        units = u
+    mean = statistics.mean(times)
+    val = units / mean
+    sample = (f"oracle sub-block {ext[0]}x{ext[1]}x{ext[2]} per step (random offset) x {units // (ext[0]*ext[1]*ext[2])} "
+              f"orientations, FP64 direct sums")
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(args.workload, d),
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2002_07627_gb300 import build, binding
+    build.build()
+    d = make_design(args.workload, seed=rank)
+    shape = d.rho.shape
+    nG = int(np.prod(shape))
+    n_orient = sum(len(t.quats) for t in d.tools)
+    imf = binding.Imf(shape)
+    imf.set_tools(d.tools)
+    info = imf.tool_info(0)
+    rho = torch.from_numpy(d.rho).to(dev)
+    fix = torch.from_numpy(d.fixture).to(dev) if d.fixture is not None else None
+    fbar = torch.empty_like(rho)
+    sec = torch.empty(shape, dtype=torch.uint8, device=dev)
+    sens0 = torch.from_numpy(np.random.default_rng(rank).normal(size=shape).astype(np.float32)).to(dev)
+    sens = sens0.clone()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        imf.compute(rho, fix, fbar, sec, stream=stream)
+        imf.penalize(sens, rho, fbar, sec, fix, w_acc=0.5, stream=stream)
+
+    def timed_steps(k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a, b in ev:
+            flush.zero_()
+            sens.copy_(sens0)
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    for _ in range(args.warmup):
+        sens.copy_(sens0)
+        step()
+    imf.sync()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = imf.stats().launches
+    with ClockSampler(dev.index) as clk:
+        times = timed_steps(args.steps)
+    imf.sync()
+    launches = imf.stats().launches - l0
+    total_ms = sum(times)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = total_ms / args.steps
+    value = ws * nG * n_orient / (ms_per_step * 1e-3)
+    flagged = imf.stats().flagged
+
+    # per-kernel times with CUDA events on the launching stream (separate pass of K steps)
+    imf.reset_kernel_times()
+    imf.set_profiling(True)
+    timed_steps(args.steps)
+    kt = imf.kernel_times()
+    imf.set_profiling(False)
+    dom = max(((k, v) for k, v in kt.items()), key=lambda kv: kv[1][0])
+    dname, (dms, dcnt) = dom
+    nb = max(1.0, n_orient * args.steps / max(1, kt.get("fft_z_inv_mul", (0, 1))[1]))
+    abytes = algorithmic_bytes(dname, info, shape, nb)
+    hbm, bf16, peak_src = measured_peaks()
+    roof = None
+    if abytes is not None:
+        ach = abytes / (dms / dcnt * 1e-3) / 1e9
+        tr = traffic_record(dname)
+        roof = {"kernel": dname, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": tr, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": dms / dcnt}
+    kernel_share = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                    for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if rank == 0 or ws > 1:
+        hr = torch.from_numpy(d.rho).pin_memory()
+        hf = torch.from_numpy(d.fixture).pin_memory() if d.fixture is not None else None
+        ob = torch.empty(shape, dtype=torch.float32).pin_memory()
+        osec = torch.empty(shape, dtype=torch.uint8).pin_memory()
+        lib = imf.lib
+        for _ in range(2):
+            lib.imf_compute_host(imf.h, hr.data_ptr(), hf.data_ptr() if hf is not None else None, ob.data_ptr(),
+                                 osec.data_ptr(), None, None, stream.cuda_stream)
+        et = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = lib.imf_compute_host(imf.h, hr.data_ptr(), hf.data_ptr() if hf is not None else None,
+                                      ob.data_ptr(), osec.data_ptr(), None, None, stream.cuda_stream)
+            et.append(time.perf_counter() - t0)
+            assert st == 0, imf.lib.imf_last_error(imf.h)
+        e_s = statistics.mean(et)
+        if ws > 1:
+            t = torch.tensor([e_s], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_s = float(t.item())
+        e2e = {"value": ws * nG * n_orient / e_s, "unit": UNIT, "h2d_bytes_per_step": nG * 4 + (nG if hf is not None else 0),
+               "d2h_bytes_per_step": nG * 4 + nG, "entry_point": "imf_compute_host (pinned host buffers)"}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # stated IMF error: oracle point queries at the argmax and at random points
+    import oracle
+    raw = torch.empty_like(rho)
+    acc = torch.empty(shape, dtype=torch.uint8, device=dev)
+    imf.compute(rho, fix, fbar, sec, raw=raw, accessible=acc)
+    imf.sync()
+    f = raw.cpu().numpy()
+    rng = np.random.default_rng(1)
+    om0 = d.fixture == 0 if d.fixture is not None else np.ones(shape, bool)
+    pts = [np.array(np.unravel_index(np.argmax(np.where(om0, f, -1)), shape))[::-1]]
+    for _ in range(args.error_points - 1):
+        pts.append(np.array([rng.integers(0, shape[2]), rng.integers(0, shape[1]), rng.integers(0, shape[0])]))
+    fo, _ = oracle.point_query(d.rho, d.fixture, d.tools, np.array(pts))
+    M = float(f[pts[0][2], pts[0][1], pts[0][0]])
+    err = max(abs(float(f[z, y, x]) - fv) for (x, y, z), fv in zip(pts, fo)) / max(M, 1e-30)
+
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        u, dt, x0, ext = run_cpu_oracle_sample(d, args.cpu_block)
+        cpu = {"value": u / dt, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
+               "sample": f"FP64 oracle on a {ext[0]}x{ext[1]}x{ext[2]} sub-block at {x0} x {n_orient} orientations "
+                         f"({dt:.1f} s)"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": dict(workload_config(args.workload, d), l2="256 MiB buffer written between timed steps",
+                          fft_grid=list(info.P), translation_window=list(info.win)),
+           "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
+           "imf_error": {"max_abs_over_max_f": err, "points": len(pts), "vs": "FP64 oracle point queries"},
+           "near_threshold_rechecked": int(flagged),
+           "roofline": roof, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="beams128", choices=sorted(WORKLOADS) + ["planar64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-block", type=int, default=24)
+    ap.add_argument("--error-points", type=int, default=6)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * libimf: inaccessibility measure field (IMF) on one GB300 GPU (sm_103a).
+ *
+ * The IMF is defined in Mirzendehdel, Behandish, Nelaturi, "Topology Optimization with
+ * Accessibility Constraint for Multi-Axis Machining" (arXiv 2002.07627), Sec. 2.1:
+ *
+ *   f(x) = min_i min_{R in Theta_i} min_{k in K_i} (rho_O * reflected 1_{R T_i})(x - R k)
+ *                                                   (Eq. eq_imf_4 and Eq. eq_imf_5)
+ *
+ * with rho_O = rho_Omega + 1_F (part density plus fixture), T_i = H_i u K_i (holder plus cutter)
+ * and the accessible set A = U_R (free translations of R T) + R K (Eq. eq_A / eq_conv_A).
+ * Algorithm 1 of the paper normalises f by its maximum, applies the allowance lambda and
+ * returns the secluded region Gamma; Eq. eq_filtered_sens / eq_accFilter turn that into the
+ * penalty on the compliance sensitivity.
+ *
+ * Discrete readings used by this library (the paper leaves these open):
+ *   - grids are C order [nz][ny][nx], x fastest; nz = 1 is a 2D problem;
+ *   - everything outside the grid is empty air (linear, not circular, correlation);
+ *   - Omega_0 (the design domain) is the set of grid cells outside the fixture;
+ *   - rho_O = min(1, rho_Omega + 1_F) and 1_T = 1_H OR 1_K;
+ *   - rotation and resampling: nearest neighbour, inverse map about the tool origin voxel o:
+ *     for an integer offset v, u = floor(R^T v + 1/2) (FP64), 1_RT(v) = 1_T(o + u);
+ *     R is built from the normalised unit quaternion (w, x, y, z) in the standard way;
+ *   - a translation t is collision-free iff g(t) <= theta_i with theta_i = theta_rel * |T_i|
+ *     (|T_i| = voxel count of the unrotated tool);
+ *   - sharp points default to every voxel of the resampled cutter R K;
+ *   - f_bar = f / M with M = max over Omega_0 of f (f_bar = 0 when M = 0); B = [f_bar > lambda];
+ *     f_bar <- f_bar * B; Gamma = Omega_0 * [rho_Omega <= tau] * B; fixture cells get
+ *     f_bar = 0, Gamma = 0 and A = 0.
+ *
+ * Ownership: the caller owns every input and output array (device memory unless stated);
+ * the library never frees them. The library owns the tool spectra and its scratch buffers,
+ * which imf_destroy frees. Calls do not block the host unless stated; errors found on the
+ * host are returned at once, errors found on the device are reported by imf_sync_status.
+ * A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef IMF_H
+#define IMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct imf_handle_s *imf_handle;
+
+typedef enum {
+    IMF_OK = 0,
+    IMF_ERR_INVALID_ARG = 1, /* a host-side argument check failed (see imf_last_error)       */
+    IMF_ERR_OOM = 2,         /* a device allocation failed                                  */
+    IMF_ERR_CUDA = 3,        /* a CUDA runtime call failed                                  */
+    IMF_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                          */
+    IMF_ERR_NOT_READY = 5,   /* imf_compute before any imf_set_tool                         */
+    IMF_ERR_BUDGET = 6,      /* the working set does not fit in hbm_budget_bytes            */
+    IMF_ERR_OVERFLOW = 7     /* the near-threshold re-check list overflowed on the device   */
+} imf_status;
+
+/* collision-convolution path */
+enum { IMF_AUTO = 0, IMF_FP32_FFT = 1, IMF_BF16_DIRECT = 2 };
+
+typedef struct {
+    int nx, ny, nz;          /* design grid; nz = 1 is 2D                                       */
+    double voxel;            /* voxel edge length; f is reported in voxel volumes (Sec. 2.1.5) */
+    double lambda;           /* allowance lambda of Alg. 1 (0.01 in Sec. 2.1.5)                */
+    double tau;              /* density threshold tau of Sec. 2.1.5 / Eq. eq_accFilter (0.5)  */
+    double theta_rel;        /* collision threshold theta_i = theta_rel * |T_i| (0.01)         */
+    int precision;           /* IMF_AUTO | IMF_FP32_FFT | IMF_BF16_DIRECT                      */
+    int recheck;             /* 1: re-check translations with |g - theta| <= band exactly      */
+    double recheck_band;     /* band half-width in voxel volumes; <= 0 picks a default         */
+    int orient_batch;        /* orientations per batch of device work; 0 picks one             */
+    size_t hbm_budget_bytes; /* cap on library-owned device memory; 0 = no cap (App. B)        */
+} imf_options;
+
+/* Fill *opt with the defaults above (grid 0x0x0, which imf_create rejects). */
+void imf_default_options(imf_options *opt);
+
+/* Create a handle for one design grid. Allocates nothing on the device yet.
+ * Errors: IMF_ERR_INVALID_ARG for non-positive extents or parameters out of range. */
+imf_status imf_create(const imf_options *opt, imf_handle *out);
+
+/*
+ * Set tool assembly `tool_id` (0 <= tool_id < 64; ids must be set densely from 0) with its
+ * orientation set Theta_i (Alg. 1 inputs [1_H_i], [1_K_i], Theta_i; Sec. 2.1.4-2.1.5).
+ *   holder, cutter : HOST uint8 arrays [tz][ty][tx], nonzero = inside; copied.
+ *   sharp_mask     : HOST uint8 [tz][ty][tx] subset of the cutter used as sharp points, or
+ *                    NULL for every cutter voxel; resampled like the cutter.
+ *   origin         : tool-frame origin voxel (x, y, z); rotations are about it.
+ *   quats          : HOST double [n_orient][4] unit quaternions (w, x, y, z).
+ * Resamples the tool on the device, builds the conjugated FFT spectra of every orientation
+ * (the reflection of Alg. 1 becomes a conjugation; footnote of Sec. 2.1.5) and keeps them
+ * resident. Synchronous (setup call). Errors: IMF_ERR_INVALID_ARG (empty cutter, bad
+ * sizes, a cutter that vanishes under every orientation), IMF_ERR_OOM, IMF_ERR_BUDGET,
+ * IMF_ERR_CUDA. */
+imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const uint8_t *cutter,
+                        const uint8_t *sharp_mask, int tx, int ty, int tz, const int origin[3],
+                        const double *quats, int n_orient);
+
+/*
+ * Algorithm 1 for the current design, asynchronously on `cuda_stream` (a cudaStream_t;
+ * NULL = legacy default stream).
+ *   rho_omega     : DEVICE float [nz][ny][nx], rho_Omega in [0, 1].
+ *   fixture       : DEVICE uint8 [nz][ny][nx] (nonzero = fixture) or NULL.
+ *   imf_bar       : DEVICE float [nz][ny][nx] out, f_bar after the allowance.
+ *   secluded      : DEVICE uint8 [nz][ny][nx] out, 1_Gamma.
+ *   imf_raw       : DEVICE float out, f before normalisation (voxel volumes), or NULL.
+ *   accessible    : DEVICE uint8 out, 1_A (A = U_i U_R A_i,R on Omega_0), or NULL.
+ * Errors: IMF_ERR_NOT_READY, IMF_ERR_INVALID_ARG (NULL required pointer), IMF_ERR_OOM,
+ * IMF_ERR_CUDA; device-side errors via imf_sync_status. */
+imf_status imf_compute(imf_handle h, const float *rho_omega, const uint8_t *fixture, float *imf_bar,
+                       uint8_t *secluded, float *imf_raw, uint8_t *accessible, void *cuda_stream);
+
+/*
+ * Same as imf_compute with HOST arrays (pageable or pinned): copies the inputs to
+ * library-owned device buffers, computes, copies the outputs back and waits for the stream.
+ * Synchronous. imf_raw and accessible may be NULL. */
+imf_status imf_compute_host(imf_handle h, const float *rho_omega, const uint8_t *fixture,
+                            float *imf_bar, uint8_t *secluded, float *imf_raw, uint8_t *accessible,
+                            void *cuda_stream);
+
+/*
+ * Filtered sensitivity of Eq. eq_filtered_sens with the accessibility filter of
+ * Eq. eq_accFilter, in place, asynchronously on `cuda_stream`:
+ *   S = (1 - w_acc) S_phi / max_{Omega_0} |S_phi| + w_acc S_IMF,
+ *   S_IMF = f_bar where rho_Omega > tau, 1 where Gamma, 0 elsewhere.
+ *   sens     : DEVICE float [nz][ny][nx], S_phi in, S out (left unnormalised if max = 0).
+ *   rho_omega, imf_bar, secluded, fixture (or NULL): DEVICE, as in imf_compute.
+ * Errors: IMF_ERR_INVALID_ARG (NULL pointer, w_acc outside [0, 1)), IMF_ERR_CUDA. */
+imf_status imf_penalize_sensitivity(imf_handle h, float *sens, const float *rho_omega,
+                                    const float *imf_bar, const uint8_t *secluded,
+                                    const uint8_t *fixture, double w_acc, void *cuda_stream);
+
+/* Wait for the last stream used by the handle and return the device-side status
+ * (IMF_OK, IMF_ERR_OVERFLOW, IMF_ERR_TIMEOUT) or IMF_ERR_CUDA; clears it. */
+imf_status imf_sync_status(imf_handle h);
+
+/* Last error message of the handle (static storage owned by the handle; never NULL). */
+const char *imf_last_error(imf_handle h);
+
+/* Free every library-owned device buffer and the handle. NULL is a no-op. */
+void imf_destroy(imf_handle h);
+
+/* ---------------------------------------------------------------------------------------
+ * Introspection for tests and benchmarks.
+ * ------------------------------------------------------------------------------------- */
+
+typedef struct {
+    int n_orient;            /* orientations of the tool                                  */
+    int P[3];                /* padded FFT extents (x, y, z)                              */
+    int kmax[3];             /* max over orientations of the cutter/sharp offsets          */
+    int win[3];              /* extents of the translation window t in [-kmax, n-1-kmin]   */
+    long size_T;             /* |T_i|, voxels of the unrotated tool                       */
+    double theta;            /* theta_i                                                   */
+    double band;             /* re-check band half-width                                  */
+    long n_rt, n_rk, n_sharp;/* total resampled voxels over all orientations             */
+    int path;                /* IMF_FP32_FFT or IMF_BF16_DIRECT                           */
+    size_t spectra_bytes;    /* resident tool-spectrum bytes                              */
+} imf_tool_info;
+
+imf_status imf_get_tool_info(imf_handle h, int tool_id, imf_tool_info *out);
+
+/* Copy the resampled offsets of one orientation to HOST int32 [n][3] (x, y, z) arrays:
+ * which = 0 (R T), 1 (R K), 2 (sharp points). *n receives the count; `out` may be NULL to
+ * query it; `cap` is the capacity of `out` in triples. Synchronous. */
+imf_status imf_get_offsets(imf_handle h, int tool_id, int orient, int which, int32_t *out,
+                           long cap, long *n);
+
+/* Copy the last batch's collision field g (FP32, the translation window of `tool_id`) and
+ * its free bits into HOST buffers, for tests: the last orientation batch of the last
+ * imf_compute is kept when `keep` was enabled with imf_set_debug. Synchronous. */
+imf_status imf_set_debug(imf_handle h, int keep_last_g);
+imf_status imf_get_last_g(imf_handle h, int slot, float *g_out, long cap, int *orient_out);
+
+typedef struct {
+    long launches;           /* kernels launched by the library since creation             */
+    long computes;           /* imf_compute calls                                          */
+    long flagged;            /* near-threshold translations re-checked (last compute)      */
+    long flagged_total;      /* since creation                                             */
+    int n_kernels;           /* entries filled in the per-kernel timing table              */
+} imf_stats;
+
+imf_status imf_get_stats(imf_handle h, imf_stats *out);
+
+/* Per-kernel timing with CUDA events on the launching stream (off by default). When on,
+ * every launch is bracketed by events; imf_get_kernel_times accumulates their durations. */
+imf_status imf_set_profiling(imf_handle h, int on);
+/* name/ms/count of kernel class `i` (0 <= i < n_kernels); synchronizes the handle's stream. */
+imf_status imf_get_kernel_time(imf_handle h, int i, const char **name, double *total_ms,
+                               long *count);
+imf_status imf_reset_kernel_times(imf_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IMF_H */

@@ -16,6 +16,6 @@ effect of the penalty on a full topology optimisation run, which needs the paper
 geometry ("parity unpinned" for that use only; the penalty formula itself is pinned).
 """
 from .ref import (  # noqa: F401
-    quat_to_matrix, rotate_indicator, resample_tool, collision, sweep, erode, imf, finalize,
+    quat_to_matrix, rotate_indicator, resample_tool, collision, sweep, erode, imf, imf_subblock, finalize,
     penalize, point_query, rho_obstacle, lib,
 )

@@ -288,3 +288,31 @@ def point_query(rho, fixture, tools, pts, theta_rel: float = 0.01):
     lib().oracle_point_query(_p(rhoO), nx, ny, nz, len(nrt), _p(RTc), _p(nrt), _p(SHc), _p(nsh),
                              _p(RKc), _p(nrk), _p(th), len(pts), _p(pts), _p(f), _p(A))
     return f, A
+
+
+def imf_subblock(design, x0, ext, theta_rel: float = 0.01):
+    """f and A (before normalisation) on the sub-block [x0, x0 + ext) of a large grid, by the
+    same literal steps as `imf` (direct FP64 collision sums on the translations the block
+    needs, brute-force sweep and minimum), with the whole design as obstacle. x0, ext are
+    (x, y, z)."""
+    rho = np.asarray(design.rho)
+    rhoO = rho_obstacle(rho, design.fixture)
+    x0 = np.asarray(x0, np.int32)
+    ext = np.asarray(ext, np.int32)
+    shape = (int(ext[2]), int(ext[1]), int(ext[0]))
+    f = np.full(shape, np.inf)
+    A = np.zeros(shape, bool)
+    for tool in design.tools:
+        T = (tool.holder != 0) | (tool.cutter != 0)
+        theta = theta_rel * float(T.sum())
+        for q in tool.quats:
+            rs = resample_tool(tool, q)
+            if len(rs["RK"]) == 0:
+                continue
+            tlo_rel, text = translation_box(shape, rs["RK"], rs["sharp"])
+            g = collision(rhoO, rs["RT"], tlo_rel + x0, text)
+            free = (g <= theta).astype(np.uint8)
+            A |= sweep(free, tlo_rel, rs["RK"], shape).astype(bool)
+            if len(rs["sharp"]):
+                f = np.minimum(f, erode(g, tlo_rel, rs["sharp"], shape))
+    return f, A.astype(np.uint8)

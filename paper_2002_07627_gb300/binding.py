@@ -1,0 +1,276 @@
+"""Thin ctypes binding of libimf (include/imf.h): argument marshalling only.
+
+Every step of the IMF path runs in the library's CUDA kernels. There is no CPU fallback: if
+the library has not been built, or no GPU is present, these calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from .build import LIB, HOSTLIB
+
+IMF_OK = 0
+STATUS_NAMES = {0: "IMF_OK", 1: "IMF_ERR_INVALID_ARG", 2: "IMF_ERR_OOM", 3: "IMF_ERR_CUDA",
+                4: "IMF_ERR_TIMEOUT", 5: "IMF_ERR_NOT_READY", 6: "IMF_ERR_BUDGET", 7: "IMF_ERR_OVERFLOW"}
+IMF_AUTO, IMF_FP32_FFT, IMF_BF16_DIRECT = 0, 1, 2
+
+# every symbol include/imf.h declares
+EXPORTS = ["imf_default_options", "imf_create", "imf_set_tool", "imf_compute", "imf_compute_host",
+           "imf_penalize_sensitivity", "imf_sync_status", "imf_last_error", "imf_destroy",
+           "imf_get_tool_info", "imf_get_offsets", "imf_set_debug", "imf_get_last_g", "imf_get_stats",
+           "imf_set_profiling", "imf_get_kernel_time", "imf_reset_kernel_times"]
+
+
+class ImfOptions(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("voxel", ctypes.c_double), ("lambda_", ctypes.c_double), ("tau", ctypes.c_double),
+                ("theta_rel", ctypes.c_double), ("precision", ctypes.c_int), ("recheck", ctypes.c_int),
+                ("recheck_band", ctypes.c_double), ("orient_batch", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_size_t)]
+
+
+class ImfToolInfo(ctypes.Structure):
+    _fields_ = [("n_orient", ctypes.c_int), ("P", ctypes.c_int * 3), ("kmax", ctypes.c_int * 3),
+                ("win", ctypes.c_int * 3), ("size_T", ctypes.c_long), ("theta", ctypes.c_double),
+                ("band", ctypes.c_double), ("n_rt", ctypes.c_long), ("n_rk", ctypes.c_long),
+                ("n_sharp", ctypes.c_long), ("path", ctypes.c_int), ("spectra_bytes", ctypes.c_size_t)]
+
+
+class ImfStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_long), ("computes", ctypes.c_long), ("flagged", ctypes.c_long),
+                ("flagged_total", ctypes.c_long), ("n_kernels", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libimf.so (built by paper_2002_07627_gb300.build). Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libimf is not built ({path} missing): run __graft_entry__.build() first")
+    L = ctypes.CDLL(path)
+    P, I, D, Lg = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
+    H = ctypes.c_void_p
+    L.imf_default_options.argtypes = [ctypes.POINTER(ImfOptions)]
+    L.imf_default_options.restype = None
+    L.imf_create.argtypes = [ctypes.POINTER(ImfOptions), ctypes.POINTER(H)]
+    L.imf_set_tool.argtypes = [H, I, P, P, P, I, I, I, P, P, I]
+    L.imf_compute.argtypes = [H, P, P, P, P, P, P, P]
+    L.imf_compute_host.argtypes = [H, P, P, P, P, P, P, P]
+    L.imf_penalize_sensitivity.argtypes = [H, P, P, P, P, P, D, P]
+    L.imf_sync_status.argtypes = [H]
+    L.imf_last_error.argtypes = [H]
+    L.imf_last_error.restype = ctypes.c_char_p
+    L.imf_destroy.argtypes = [H]
+    L.imf_destroy.restype = None
+    L.imf_get_tool_info.argtypes = [H, I, ctypes.POINTER(ImfToolInfo)]
+    L.imf_get_offsets.argtypes = [H, I, I, I, P, Lg, ctypes.POINTER(Lg)]
+    L.imf_set_debug.argtypes = [H, I]
+    L.imf_get_last_g.argtypes = [H, I, P, Lg, ctypes.POINTER(I)]
+    L.imf_get_stats.argtypes = [H, ctypes.POINTER(ImfStats)]
+    L.imf_set_profiling.argtypes = [H, I]
+    L.imf_get_kernel_time.argtypes = [H, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(D),
+                                      ctypes.POINTER(Lg)]
+    L.imf_reset_kernel_times.argtypes = [H]
+    for name in EXPORTS:
+        if name not in ("imf_default_options", "imf_destroy", "imf_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def host_fft(x: np.ndarray, sign: int = -1) -> np.ndarray:
+    """Run the kernels' Stockham butterflies on the CPU (host emulation, tests only)."""
+    L = ctypes.CDLL(HOSTLIB)
+    L.imf_host_fft.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    a = np.ascontiguousarray(np.stack([x.real, x.imag], -1).astype(np.float32))
+    out = np.zeros_like(a)
+    rc = L.imf_host_fft(len(x), sign, a.ctypes.data, out.ctypes.data)
+    if rc < 0:
+        raise ValueError(f"no plan for length {len(x)}")
+    return out[..., 0].astype(np.float64) + 1j * out[..., 1]
+
+
+class ImfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+@dataclass
+class ToolInfo:
+    n_orient: int
+    P: tuple
+    kmax: tuple
+    win: tuple
+    size_T: int
+    theta: float
+    band: float
+    n_rt: int
+    n_rk: int
+    n_sharp: int
+    path: int
+    spectra_bytes: int
+
+
+class Imf:
+    """One design grid on the current CUDA device; mirrors the C ABI one-to-one."""
+
+    def __init__(self, shape_zyx, lam=0.01, tau=0.5, theta_rel=0.01, precision=IMF_AUTO, recheck=True,
+                 recheck_band=0.0, orient_batch=0, hbm_budget_bytes=0, voxel=1.0):
+        self.lib = load()
+        opt = ImfOptions()
+        self.lib.imf_default_options(ctypes.byref(opt))
+        nz, ny, nx = shape_zyx
+        opt.nx, opt.ny, opt.nz = nx, ny, nz
+        opt.voxel, opt.lambda_, opt.tau, opt.theta_rel = voxel, lam, tau, theta_rel
+        opt.precision, opt.recheck, opt.recheck_band = precision, int(recheck), recheck_band
+        opt.orient_batch, opt.hbm_budget_bytes = orient_batch, hbm_budget_bytes
+        self.shape = (nz, ny, nx)
+        self.opt = opt
+        h = ctypes.c_void_p()
+        self._check(self.lib.imf_create(ctypes.byref(opt), ctypes.byref(h)), handle=None)
+        self.h = h
+
+    def _check(self, st, handle="self"):
+        if st != IMF_OK:
+            msg = ""
+            if handle is not None and getattr(self, "h", None):
+                msg = self.lib.imf_last_error(self.h).decode()
+            raise ImfError(st, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.imf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- setup
+    def set_tool(self, tool_id, holder, cutter, origin, quats, sharp=None):
+        holder = np.ascontiguousarray(holder, np.uint8)
+        cutter = np.ascontiguousarray(cutter, np.uint8)
+        tz, ty, tx = cutter.shape
+        if holder.shape != cutter.shape:
+            raise ValueError("holder and cutter shapes differ")
+        sh = None if sharp is None else np.ascontiguousarray(sharp, np.uint8)
+        o = (ctypes.c_int * 3)(*[int(v) for v in origin])
+        q = np.ascontiguousarray(np.asarray(quats, np.float64).reshape(-1, 4))
+        self._check(self.lib.imf_set_tool(self.h, tool_id, holder.ctypes.data, cutter.ctypes.data,
+                                          None if sh is None else sh.ctypes.data, tx, ty, tz, o,
+                                          q.ctypes.data, len(q)))
+
+    def set_tools(self, tools):
+        for i, t in enumerate(tools):
+            self.set_tool(i, t.holder, t.cutter, t.origin, t.quats, getattr(t, "sharp", None))
+
+    # --- compute (torch CUDA tensors)
+    def compute(self, rho, fixture=None, fbar=None, secluded=None, raw=None, accessible=None, stream=None):
+        import torch
+        self._check_tensor(rho, torch.float32)
+        if fixture is not None:
+            self._check_tensor(fixture, torch.uint8)
+        if fbar is None:
+            fbar = torch.empty_like(rho)
+        if secluded is None:
+            secluded = torch.empty(rho.shape, dtype=torch.uint8, device=rho.device)
+        s = (stream or torch.cuda.current_stream(rho.device)).cuda_stream
+        self._check(self.lib.imf_compute(self.h, _ptr(rho), _ptr(fixture), _ptr(fbar), _ptr(secluded),
+                                         _ptr(raw), _ptr(accessible), s))
+        return fbar, secluded
+
+    def compute_host(self, rho: np.ndarray, fixture=None, want_raw=True, want_acc=True, stream=None):
+        rho = np.ascontiguousarray(rho, np.float32)
+        fix = None if fixture is None else np.ascontiguousarray(fixture, np.uint8)
+        fbar = np.empty(self.shape, np.float32)
+        sec = np.empty(self.shape, np.uint8)
+        raw = np.empty(self.shape, np.float32) if want_raw else None
+        acc = np.empty(self.shape, np.uint8) if want_acc else None
+        s = 0 if stream is None else stream.cuda_stream
+        p = lambda a: None if a is None else a.ctypes.data
+        self._check(self.lib.imf_compute_host(self.h, p(rho), p(fix), p(fbar), p(sec), p(raw), p(acc), s))
+        return fbar, sec, raw, acc
+
+    def penalize(self, sens, rho, fbar, secluded, fixture=None, w_acc=0.5, stream=None):
+        import torch
+        s = (stream or torch.cuda.current_stream(sens.device)).cuda_stream
+        self._check(self.lib.imf_penalize_sensitivity(self.h, _ptr(sens), _ptr(rho), _ptr(fbar), _ptr(secluded),
+                                                      _ptr(fixture), float(w_acc), s))
+        return sens
+
+    def sync(self):
+        self._check(self.lib.imf_sync_status(self.h))
+
+    # --- introspection
+    def tool_info(self, tool_id=0) -> ToolInfo:
+        info = ImfToolInfo()
+        self._check(self.lib.imf_get_tool_info(self.h, tool_id, ctypes.byref(info)))
+        return ToolInfo(info.n_orient, tuple(info.P), tuple(info.kmax), tuple(info.win), info.size_T, info.theta,
+                        info.band, info.n_rt, info.n_rk, info.n_sharp, info.path, info.spectra_bytes)
+
+    def offsets(self, tool_id, orient, which) -> np.ndarray:
+        n = ctypes.c_long()
+        self._check(self.lib.imf_get_offsets(self.h, tool_id, orient, which, None, 0, ctypes.byref(n)))
+        out = np.zeros((max(n.value, 1), 3), np.int32)
+        self._check(self.lib.imf_get_offsets(self.h, tool_id, orient, which, out.ctypes.data, n.value,
+                                             ctypes.byref(n)))
+        return out[:n.value]
+
+    def last_g(self, slot=0):
+        info = self.tool_info(0)
+        o = ctypes.c_int()
+        self._check(self.lib.imf_get_last_g(self.h, slot, None, 0, ctypes.byref(o)))
+        wx, wy, wz = info.win
+        gpx = (wx + 3) & ~3
+        buf = np.zeros(wz * wy * gpx, np.float32)
+        self._check(self.lib.imf_get_last_g(self.h, slot, buf.ctypes.data, buf.size, ctypes.byref(o)))
+        return o.value, buf.reshape(wz, wy, gpx)[:, :, :wx]
+
+    def stats(self) -> ImfStats:
+        s = ImfStats()
+        self._check(self.lib.imf_get_stats(self.h, ctypes.byref(s)))
+        return s
+
+    def set_profiling(self, on=True):
+        self._check(self.lib.imf_set_profiling(self.h, int(on)))
+
+    def kernel_times(self) -> dict:
+        out = {}
+        st = self.stats()
+        for i in range(st.n_kernels):
+            name = ctypes.c_char_p()
+            ms = ctypes.c_double()
+            cnt = ctypes.c_long()
+            self._check(self.lib.imf_get_kernel_time(self.h, i, ctypes.byref(name), ctypes.byref(ms),
+                                                     ctypes.byref(cnt)))
+            if cnt.value:
+                out[name.value.decode()] = (ms.value, cnt.value)
+        return out
+
+    def reset_kernel_times(self):
+        self._check(self.lib.imf_reset_kernel_times(self.h))
+
+    @staticmethod
+    def _check_tensor(t, dtype):
+        if not t.is_cuda:
+            raise ValueError("libimf takes CUDA tensors (device memory); use compute_host for host arrays")
+        if t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"expected a contiguous {dtype} tensor")

@@ -1,0 +1,242 @@
+// FFT pass kernels of the collision convolution (Alg. 1 Convolve; App. B).
+//
+// The 3D real FFT of a padded grid [Pz][Py][Px] is split into one pass per axis. The x pass
+// packs a real row of length P = 2M into M complex samples, transforms them and unpacks the
+// half spectrum (M + 1 bins); the y and z passes transform columns of the half spectrum
+// [z][y][kx] with W consecutive kx columns per block so that every global access is a
+// 128-byte segment. Each pass stages its tile in shared memory and runs the Stockham stages
+// of fft.cuh there. The inverse z pass multiplies the design spectrum by a tool spectrum as
+// it loads (the pointwise product of App. B), and the inverse x pass writes the collision
+// measure g together with the bit mask of collision-free translations (threshold of
+// Eq. eq_conv_D) and the list of translations whose g lies within the re-check band.
+#include "imf_internal.cuh"
+
+namespace imf {
+
+namespace {
+
+template <int S>
+__device__ void run_stages(const FftPlan &plan, float2 *&src, float2 *&dst, int ntile, int sw, int sj,
+                           bool interleaved, const float2 *tw)
+{
+    const int L = plan.L;
+    int Ns = 1;
+    for (int s = 0; s < plan.nrad; ++s) {
+        const int R = plan.rad[s];
+        const int per = L / R;
+        const int nb = per * ntile;
+        for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+            int w, jb;
+            if (interleaved) { w = q % ntile; jb = q / ntile; }
+            else { jb = q % per; w = q / per; }
+            stockham_dispatch<S>(R, src, dst, w, jb, L, Ns, sw, sj, tw);
+        }
+        __syncthreads();
+        float2 *t = src; src = dst; dst = t;
+        Ns *= R;
+    }
+}
+
+constexpr int kAxisW = 16;
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) axis_fft_kernel(AxisArgs a)
+{
+    extern __shared__ float2 sm[];
+    const int L = a.plan.L;
+    float2 *buf0 = sm, *buf1 = sm + kAxisW * L, *tw = sm + 2 * kAxisW * L;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = a.tw[i];
+    const int kx0 = blockIdx.x * kAxisW;
+    const long b = blockIdx.y, o = blockIdx.z;
+    const float2 *in = a.in + o * a.in_so + b * a.in_sb + kx0;
+    const float2 *mul = a.mul ? a.mul + o * a.mul_so + b * a.mul_sb + kx0 : nullptr;
+    for (int idx = threadIdx.x; idx < kAxisW * L; idx += blockDim.x) {
+        const int w = idx % kAxisW, j = idx / kAxisW;
+        float2 v = make_float2(0.f, 0.f);
+        if (j < a.lin && kx0 + w < a.nx) {
+            v = in[(long)j * a.in_sl + w];
+            if (mul) v = c_mul(v, mul[(long)j * a.mul_sl + w]);
+        }
+        buf0[j * kAxisW + w] = v;
+    }
+    __syncthreads();
+    float2 *src = buf0, *dst = buf1;
+    run_stages<S>(a.plan, src, dst, kAxisW, 1, kAxisW, true, tw);
+    float2 *out = a.out + o * a.out_so + b * a.out_sb + kx0;
+    for (int idx = threadIdx.x; idx < kAxisW * a.lout; idx += blockDim.x) {
+        const int w = idx % kAxisW, jj = idx / kAxisW;
+        if (kx0 + w < a.nx) {
+            float2 v = c_scale(src[(a.j0 + jj) * kAxisW + w], a.scale);
+            if (a.conj_out) v.y = -v.y;
+            out[(long)jj * a.out_sl + w] = v;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) rfft_fwd_kernel(RfftArgs a, int W)
+{
+    extern __shared__ float2 sm[];
+    const int M = a.M, ld = M + 1;
+    float2 *buf0 = sm, *buf1 = sm + W * ld, *twM = sm + 2 * W * ld, *twP = twM + M;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) twM[i] = a.twM[i];
+    for (int i = threadIdx.x; i <= M; i += blockDim.x) twP[i] = a.twP[i];
+    const int r0 = blockIdx.x * W;
+    for (int idx = threadIdx.x; idx < W * M; idx += blockDim.x) {
+        const int w = idx / M, n = idx % M, r = r0 + w;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < a.rows) {
+            const int y = r % a.rows_y, z = r / a.rows_y;
+            const long base = z * a.src_sz + y * a.src_sy;
+            const int x0 = 2 * n, x1 = 2 * n + 1;
+            if (x0 < a.nin) {
+                float e = a.src[base + x0];
+                if (a.fix) e = fminf(1.f, e + (a.fix[base + x0] ? 1.f : 0.f));
+                v.x = e;
+            }
+            if (x1 < a.nin) {
+                float e = a.src[base + x1];
+                if (a.fix) e = fminf(1.f, e + (a.fix[base + x1] ? 1.f : 0.f));
+                v.y = e;
+            }
+        }
+        buf0[w * ld + n] = v;
+    }
+    __syncthreads();
+    float2 *src = buf0, *dst = buf1;
+    run_stages<-1>(a.plan, src, dst, W, ld, 1, false, twM);
+    // unpack: X[k] = (Z[k] + conj Z[M-k]) / 2 + exp(-2 pi i k / P) (Z[k] - conj Z[M-k]) / (2 i)
+    for (int idx = threadIdx.x; idx < W * (M + 1); idx += blockDim.x) {
+        const int w = idx / (M + 1), k = idx % (M + 1), r = r0 + w;
+        if (r >= a.rows) continue;
+        const float2 zk = src[w * ld + (k == M ? 0 : k)];
+        const float2 zc = c_conj(src[w * ld + (k == 0 ? 0 : M - k)]);
+        const float2 e = c_scale(c_add(zk, zc), 0.5f);
+        const float2 od = c_mul_si<-1>(c_scale(c_sub(zk, zc), 0.5f));
+        const float2 X = c_add(e, c_mul(twP[k], od));
+        const int y = r % a.rows_y, z = r / a.rows_y;
+        a.out[z * a.out_sz + y * a.out_sy + k] = X;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) irfft_threshold_kernel(IrfftArgs a, int W)
+{
+    extern __shared__ float2 sm[];
+    const int M = a.M, ld = M + 1;
+    float2 *buf0 = sm, *buf1 = sm + W * ld, *twM = sm + 2 * W * ld, *twP = twM + M;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) twM[i] = a.twM[i];
+    for (int i = threadIdx.x; i <= M; i += blockDim.x) twP[i] = a.twP[i];
+    const int r0 = blockIdx.x * W;
+    const long o = blockIdx.z;
+    const float2 *in = a.in + o * a.in_so;
+    for (int idx = threadIdx.x; idx < W * (M + 1); idx += blockDim.x) {
+        const int w = idx / (M + 1), k = idx % (M + 1), r = r0 + w;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < a.rows) {
+            const int y = r % a.rows_y, z = r / a.rows_y;
+            v = in[z * a.in_sz + y * a.in_sy + k];
+        }
+        buf1[w * ld + k] = v;
+    }
+    __syncthreads();
+    // pack: Z[k] = (X[k] + conj X[M-k]) + i exp(+2 pi i k / P) (X[k] - conj X[M-k]), k < M
+    for (int idx = threadIdx.x; idx < W * M; idx += blockDim.x) {
+        const int w = idx / M, k = idx % M;
+        const float2 xk = buf1[w * ld + k];
+        const float2 xc = c_conj(buf1[w * ld + M - k]);
+        const float2 e = c_add(xk, xc);
+        const float2 od = c_mul(c_conj(twP[k]), c_sub(xk, xc));
+        buf0[w * ld + k] = c_add(e, c_mul_si<1>(od));
+    }
+    __syncthreads();
+    float2 *src = buf0, *dst = buf1;
+    run_stages<1>(a.plan, src, dst, W, ld, 1, false, twM);
+    // g[i] = Re z[i/2] (i even) or Im z[i/2] (i odd), clamped at 0 (g >= 0 exactly)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int nwords = (a.nout + 31) >> 5;
+    float *g = a.g + o * a.g_so;
+    uint32_t *bits = a.bits + o * a.b_so;
+    for (int p = warp; p < W * nwords; p += nwarp) {
+        const int w = p / nwords, q = p % nwords, r = r0 + w;
+        if (r >= a.rows) continue;  // warp-uniform
+        const int y = r % a.rows_y, z = r / a.rows_y;
+        const int i = q * 32 + lane;
+        const bool valid = i < a.nout;
+        float gv = 0.f;
+        if (valid) {
+            const float2 zz = src[w * ld + (i >> 1)];
+            gv = fmaxf((i & 1) ? zz.y : zz.x, 0.f);
+            g[z * a.g_sz + y * a.g_sy + i] = gv;
+        }
+        const unsigned freeb = __ballot_sync(0xffffffffu, valid && gv <= a.theta);
+        if (lane == 0) bits[z * a.b_sz + y * a.b_sy + q] = freeb;
+        if (a.flag) {
+            const bool near = valid && fabsf(gv - a.theta) <= a.band;
+            const unsigned nm = __ballot_sync(0xffffffffu, near);
+            if (nm) {
+                int base = 0;
+                if (lane == 0) {
+                    base = atomicAdd(a.flag_count, __popc(nm));
+                    atomicAdd(a.flag_total, __popc(nm));
+                }
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (near) {
+                    const int slot = base + __popc(nm & ((1u << lane) - 1u));
+                    if (slot < a.flag_cap) {
+                        const long lin = ((long)z * a.rows_y + y) * a.nout + i;
+                        a.flags[slot] = make_int2(a.orient_base + (int)o, (int)lin);
+                    } else {
+                        atomicExch(a.status, kDevOverflow);
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <typename K> void set_smem(K kernel, size_t bytes)
+{
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int x_rows_per_block(int M)
+{
+    int W = 4096 / (M + 1);
+    if (W < 1) W = 1;
+    if (W > 32) W = 32;
+    return W;
+}
+
+} // namespace
+
+void launch_axis_fft(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s)
+{
+    const size_t smem = (size_t)(2 * kAxisW * a.plan.L + a.plan.L) * sizeof(float2);
+    dim3 grid((a.nx + kAxisW - 1) / kAxisW, nbatch, norient);
+    if (sign < 0) {
+        set_smem(axis_fft_kernel<-1>, smem);
+        axis_fft_kernel<-1><<<grid, kThreads, smem, s>>>(a);
+    } else {
+        set_smem(axis_fft_kernel<1>, smem);
+        axis_fft_kernel<1><<<grid, kThreads, smem, s>>>(a);
+    }
+}
+
+void launch_rfft_fwd(const RfftArgs &a, cudaStream_t s)
+{
+    const int W = x_rows_per_block(a.M);
+    const size_t smem = (size_t)(2 * W * (a.M + 1) + 2 * a.M + 1) * sizeof(float2);
+    set_smem(rfft_fwd_kernel, smem);
+    dim3 grid((a.rows + W - 1) / W);
+    rfft_fwd_kernel<<<grid, kThreads, smem, s>>>(a, W);
+}
+
+void launch_irfft_threshold(const IrfftArgs &a, int norient, cudaStream_t s)
+{
+    const int W = x_rows_per_block(a.M);
+    const size_t smem = (size_t)(2 * W * (a.M + 1) + 2 * a.M + 1) * sizeof(float2);
+    set_smem(irfft_threshold_kernel, smem);
+    dim3 grid((a.rows + W - 1) / W, 1, norient);
+    irfft_threshold_kernel<<<grid, kThreads, smem, s>>>(a, W);
+}
+
+} // namespace imf

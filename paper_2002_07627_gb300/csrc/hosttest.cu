@@ -1,0 +1,25 @@
+// Host-only exports that run the kernels' FFT building blocks (fft.cuh) on the CPU, for the
+// CPU unit tests. Not part of libimf and never loaded by the product path.
+#include <cmath>
+#include <vector>
+
+#include "fft.cuh"
+
+extern "C" int imf_host_fft(int L, int sign, const float *in, float *out)
+{
+    imf::FftPlan p;
+    if (L < 1 || !imf::make_plan(L, &p)) return -1;
+    std::vector<float2> tw(L), a(L), b(L);
+    for (int m = 0; m < L; ++m) {
+        const double ang = -2.0 * M_PI * (double)m / (double)L;
+        tw[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        a[m] = make_float2(in[2 * m], in[2 * m + 1]);
+    }
+    float2 *r = sign < 0 ? imf::fft_pencil_host<-1>(p, a.data(), b.data(), tw.data())
+                         : imf::fft_pencil_host<1>(p, a.data(), b.data(), tw.data());
+    for (int m = 0; m < L; ++m) {
+        out[2 * m] = r[m].x;
+        out[2 * m + 1] = r[m].y;
+    }
+    return p.nrad;
+}

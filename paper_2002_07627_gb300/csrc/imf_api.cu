@@ -1,0 +1,957 @@
+// C ABI of libimf (include/imf.h): handle, tool setup, planning and the launch sequence of
+// Algorithm 1 on one GPU. Host code only; kernels live in fft_kernels.cu and imf_kernels.cu.
+//
+// Data layout in device memory (per tool plan, x fastest everywhere):
+//   spectra   [n_orient][Pz][Py][Hs] complex64, conj(FFT(1_RT)) / (Px Py Pz), resident
+//   rho spec  [Pz][Py][Hs]            FFT(rho_O), once per imf_compute and plan
+//   per batch slot (orientations processed together):
+//     Y1 [Wz][Py][Hs], Y2 [Wz][Wy][Hs] complex64 (inverse-FFT intermediates)
+//     g  [Wz][Wy][gpx] float  collision measure on the translation window
+//     free bits [Wz][Wy][wpr] uint32
+//   f [nz][ny][nx] float running minimum; A bits [nz][ny][awords]
+// The translation window holds t in [-kmax, n - 1 - kmin] per axis at index t + kmax, where
+// kmin / kmax bound the cutter and sharp-point offsets of every orientation of the tool.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <unordered_map>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "imf.h"
+#include "imf_internal.cuh"
+
+using namespace imf;
+
+namespace {
+
+enum KernelId {
+    KID_ROTATE, KID_SPEC, KID_RFFT_FWD, KID_AXIS_FWD, KID_AXIS_INV_MUL, KID_AXIS_INV, KID_IRFFT_THRESH,
+    KID_RECHECK, KID_SWEEP, KID_ERODE, KID_INIT, KID_MAX, KID_FINALIZE, KID_ABSMAX, KID_PENALIZE, KID_COUNT
+};
+const char *kKernelNames[KID_COUNT] = {
+    "rotate_resample", "tool_spectrum", "rfft_x_fwd", "fft_axis_fwd", "fft_z_inv_mul", "fft_y_inv",
+    "irfft_x_threshold", "recheck_near_threshold", "sweep_dilate", "erode_min", "init", "max_omega0",
+    "finalize", "absmax_omega0", "penalize"};
+
+struct Tool {
+    bool set = false;
+    int tx = 0, ty = 0, tz = 0, o[3] = {0, 0, 0}, n_orient = 0;
+    long size_T = 0;
+    double theta = 0, band = 0;
+    std::vector<std::vector<int32_t>> rt, rk, sh;   // per-orientation offset triples
+    int kmin[3] = {0, 0, 0}, kmax[3] = {0, 0, 0};
+    int P[3] = {1, 1, 1}, M = 1, Hx = 2, Hs = 2;
+    int win[3] = {1, 1, 1}, gpx = 4, wpr = 3;
+    FftPlan plM{}, ply{}, plz{};
+    float2 *twM = nullptr, *twP = nullptr, *twy = nullptr, *twz = nullptr;
+    float2 *spec = nullptr;
+    size_t spec_bytes = 0;
+    uint32_t *rt_off = nullptr;
+    int *rt_start = nullptr;
+    int4 *iv = nullptr;
+    int *iv_start = nullptr;
+    int *sh_lin = nullptr;
+    int *sh_start = nullptr;
+    long n_rt = 0, n_rk = 0, n_sh = 0;
+};
+
+struct ProfRec {
+    int kid;
+    cudaEvent_t a, b;
+};
+
+} // namespace
+
+struct imf_handle_s {
+    imf_options opt{};
+    std::string err = "";
+    Tool tools[64];
+    int n_tools = 0;
+    // compute work buffers (grow only)
+    float2 *rho_spec = nullptr, *X1 = nullptr, *X2 = nullptr;
+    size_t rho_spec_n = 0, X1_n = 0, X2_n = 0;
+    float2 *Y1 = nullptr, *Y2 = nullptr;
+    float *g = nullptr;
+    uint32_t *bits = nullptr;
+    size_t Y1_n = 0, Y2_n = 0, g_n = 0, bits_n = 0;  // per slot
+    int slots = 0;
+    float *f = nullptr;
+    uint32_t *A = nullptr;
+    int awords = 0;
+    int2 *flags = nullptr;
+    int flag_cap = 0;
+    int *dev_small = nullptr;   // [0] status, [1] flag count of the batch, [2] maxbits,
+                                // [3] maxbits (penalize), [4] flags of the last compute
+    // host staging for imf_compute_host
+    float *h_rho = nullptr, *h_fbar = nullptr, *h_raw = nullptr;
+    uint8_t *h_fix = nullptr, *h_sec = nullptr, *h_acc = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool used_stream = false;
+    size_t owned_bytes = 0;
+    std::unordered_map<void *, size_t> sizes;
+    // stats
+    long launches = 0, computes = 0, flagged_last = 0, flagged_total = 0;
+    // profiling
+    bool prof = false;
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_ms[KID_COUNT] = {0};
+    long prof_cnt[KID_COUNT] = {0};
+    // debug
+    bool keep_g = false;
+    int last_batch_base = -1, last_batch_n = 0, last_tool = -1;
+};
+
+namespace {
+
+imf_status fail(imf_handle h, imf_status st, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+imf_status fail(imf_handle h, imf_status st, const char *fmt, ...)
+{
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return st;
+}
+
+#define CU(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? IMF_ERR_OOM : IMF_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                         \
+    } while (0)
+
+template <typename T> imf_status dalloc(imf_handle h, T **p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    const size_t bytes = n * sizeof(T);
+    if (h->opt.hbm_budget_bytes && h->owned_bytes + bytes > h->opt.hbm_budget_bytes)
+        return fail(h, IMF_ERR_BUDGET, "device allocation of %zu bytes exceeds hbm_budget_bytes (%zu owned)",
+                    bytes, h->owned_bytes);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(h, IMF_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    h->owned_bytes += bytes;
+    h->sizes[(void *)*p] = bytes;
+    return IMF_OK;
+}
+
+template <typename T> void dfree(imf_handle h, T *&p, size_t = 0)
+{
+    if (p) {
+        cudaFree(p);
+        auto it = h->sizes.find((void *)p);
+        if (it != h->sizes.end()) {
+            h->owned_bytes -= std::min(h->owned_bytes, it->second);
+            h->sizes.erase(it);
+        }
+    }
+    p = nullptr;
+}
+
+#define TRY(x)                                                                                      \
+    do {                                                                                            \
+        imf_status s_ = (x);                                                                        \
+        if (s_ != IMF_OK) return s_;                                                                \
+    } while (0)
+
+// ----------------------------------------------------------------------------- profiling
+cudaEvent_t get_event(imf_handle h)
+{
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct Launch {
+    imf_handle h;
+    int kid;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    Launch(imf_handle h_, int kid_, cudaStream_t s_) : h(h_), kid(kid_), s(s_)
+    {
+        if (h->prof) {
+            a = get_event(h);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~Launch()
+    {
+        h->launches++;
+        if (h->prof) {
+            cudaEvent_t b = get_event(h);
+            cudaEventRecord(b, s);
+            h->prof_pending.push_back({kid, a, b});
+        }
+    }
+};
+
+void drain_profile(imf_handle h)
+{
+    for (auto &r : h->prof_pending) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        h->prof_ms[r.kid] += ms;
+        h->prof_cnt[r.kid] += 1;
+        h->ev_pool.push_back(r.a);
+        h->ev_pool.push_back(r.b);
+    }
+    h->prof_pending.clear();
+}
+
+// ----------------------------------------------------------------------------- planning
+bool is_smooth(long n)
+{
+    for (long p : {2L, 3L, 5L, 7L})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+int next_smooth(int n)
+{
+    if (n < 1) n = 1;
+    while (!is_smooth(n)) ++n;
+    return n;
+}
+
+// R from the unit quaternion (w, x, y, z), normalised first; row major, v = R u.
+void quat_to_R(const double *q, double *R)
+{
+    const double n = std::sqrt(((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3]);
+    const double w = q[0] / n, x = q[1] / n, y = q[2] / n, z = q[3] / n;
+    R[0] = 1.0 - 2.0 * (y * y + z * z);
+    R[1] = 2.0 * (x * y - w * z);
+    R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);
+    R[4] = 1.0 - 2.0 * (x * x + z * z);
+    R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);
+    R[7] = 2.0 * (y * z + w * x);
+    R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+// Scan box of the rotated array: the tool's voxel cubes rotate into the hull of the rotated
+// corners of its voxel-edge box; one voxel of margin on every side.
+void scan_box(const double *R, int tx, int ty, int tz, const int *o, int *box)
+{
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    const double ex[3][2] = {{-o[0] - 0.5, tx - o[0] - 0.5}, {-o[1] - 0.5, ty - o[1] - 0.5}, {-o[2] - 0.5, tz - o[2] - 0.5}};
+    for (int c = 0; c < 8; ++c) {
+        const double u[3] = {ex[0][c & 1], ex[1][(c >> 1) & 1], ex[2][(c >> 2) & 1]};
+        for (int r = 0; r < 3; ++r) {
+            const double v = R[3 * r] * u[0] + R[3 * r + 1] * u[1] + R[3 * r + 2] * u[2];
+            lo[r] = std::min(lo[r], v);
+            hi[r] = std::max(hi[r], v);
+        }
+    }
+    for (int r = 0; r < 3; ++r) {
+        box[r] = (int)std::floor(lo[r]) - 1;
+        box[3 + r] = (int)std::ceil(hi[r]) + 1 - box[r] + 1;
+    }
+}
+
+void twiddles(int L, int denom, int count, std::vector<float2> &out)
+{
+    out.resize(std::max(count, 1));
+    for (int m = 0; m < count; ++m) {
+        const double a = -2.0 * M_PI * (double)m / (double)denom;
+        out[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    (void)L;
+}
+
+template <typename T> imf_status upload(imf_handle h, T **dst, const std::vector<T> &src)
+{
+    TRY(dalloc(h, dst, src.size()));
+    if (!src.empty()) CU(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return IMF_OK;
+}
+
+void free_tool(imf_handle h, Tool &t)
+{
+    dfree(h, t.twM, (size_t)t.M);
+    dfree(h, t.twP, (size_t)t.M + 1);
+    dfree(h, t.twy, (size_t)t.P[1]);
+    dfree(h, t.twz, (size_t)t.P[2]);
+    dfree(h, t.spec, t.spec_bytes / sizeof(float2));
+    dfree(h, t.rt_off, (size_t)t.n_rt);
+    dfree(h, t.rt_start, (size_t)t.n_orient + 1);
+    dfree(h, t.iv, (size_t)0);
+    dfree(h, t.iv_start, (size_t)t.n_orient + 1);
+    dfree(h, t.sh_lin, (size_t)t.n_sh);
+    dfree(h, t.sh_start, (size_t)t.n_orient + 1);
+    t = Tool();
+}
+
+imf_status ensure_work(imf_handle h)
+{
+    const imf_options &op = h->opt;
+    const long N = (long)op.nx * op.ny * op.nz;
+    size_t rs = 0, x1 = 0, x2 = 0, y1 = 0, y2 = 0, gn = 0, bn = 0;
+    int maxo = 1;
+    for (int i = 0; i < h->n_tools; ++i) {
+        const Tool &t = h->tools[i];
+        rs = std::max(rs, (size_t)t.P[2] * t.P[1] * t.Hs);
+        x1 = std::max(x1, (size_t)op.nz * op.ny * t.Hs);
+        x2 = std::max(x2, (size_t)op.nz * t.P[1] * t.Hs);
+        y1 = std::max(y1, (size_t)t.win[2] * t.P[1] * t.Hs);
+        y2 = std::max(y2, (size_t)t.win[2] * t.win[1] * t.Hs);
+        gn = std::max(gn, (size_t)t.win[2] * t.win[1] * t.gpx);
+        bn = std::max(bn, (size_t)t.win[2] * t.win[1] * t.wpr);
+        maxo = std::max(maxo, t.n_orient);
+    }
+    if (!h->f) {
+        TRY(dalloc(h, &h->f, (size_t)N));
+        h->awords = (op.nx + 31) / 32;
+        TRY(dalloc(h, &h->A, (size_t)op.nz * op.ny * h->awords));
+        TRY(dalloc(h, &h->dev_small, (size_t)8));
+        CU(cudaMemset(h->dev_small, 0, 8 * sizeof(int)));
+    }
+    if (rs > h->rho_spec_n) { dfree(h, h->rho_spec, h->rho_spec_n); TRY(dalloc(h, &h->rho_spec, rs)); h->rho_spec_n = rs; }
+    if (x1 > h->X1_n) { dfree(h, h->X1, h->X1_n); TRY(dalloc(h, &h->X1, x1)); h->X1_n = x1; }
+    if (x2 > h->X2_n) { dfree(h, h->X2, h->X2_n); TRY(dalloc(h, &h->X2, x2)); h->X2_n = x2; }
+    int want = op.orient_batch > 0 ? op.orient_batch : 4;
+    want = std::min(want, maxo);
+    const size_t per_slot = y1 * 8 + y2 * 8 + gn * 4 + bn * 4;
+    if (op.hbm_budget_bytes) {
+        const size_t have = op.hbm_budget_bytes > h->owned_bytes ? op.hbm_budget_bytes - h->owned_bytes : 0;
+        const size_t cur = (size_t)h->slots * (h->Y1_n * 8 + h->Y2_n * 8 + h->g_n * 4 + h->bits_n * 4);
+        int fit = (int)((have + cur) / std::max<size_t>(per_slot, 1));
+        if (fit < 1) return fail(h, IMF_ERR_BUDGET, "one orientation slot needs %zu bytes; budget has %zu", per_slot, have + cur);
+        want = std::min(want, fit);
+    }
+    if (y1 > h->Y1_n || y2 > h->Y2_n || gn > h->g_n || bn > h->bits_n || want != h->slots) {
+        dfree(h, h->Y1, h->Y1_n * h->slots);
+        dfree(h, h->Y2, h->Y2_n * h->slots);
+        dfree(h, h->g, h->g_n * h->slots);
+        dfree(h, h->bits, h->bits_n * h->slots);
+        h->Y1_n = std::max(y1, h->Y1_n);
+        h->Y2_n = std::max(y2, h->Y2_n);
+        h->g_n = std::max(gn, h->g_n);
+        h->bits_n = std::max(bn, h->bits_n);
+        h->slots = want;
+        TRY(dalloc(h, &h->Y1, h->Y1_n * want));
+        TRY(dalloc(h, &h->Y2, h->Y2_n * want));
+        TRY(dalloc(h, &h->g, h->g_n * want));
+        TRY(dalloc(h, &h->bits, h->bits_n * want));
+        CU(cudaMemset(h->bits, 0, h->bits_n * want * sizeof(uint32_t)));
+        CU(cudaMemset(h->g, 0, h->g_n * want * sizeof(float)));
+    }
+    const long wcap = std::max<long>(1 << 16, (long)(gn * want / 32));
+    if (wcap > h->flag_cap) {
+        dfree(h, h->flags, (size_t)h->flag_cap);
+        TRY(dalloc(h, &h->flags, (size_t)wcap));
+        h->flag_cap = (int)std::min<long>(wcap, 1L << 30);
+    }
+    return IMF_OK;
+}
+
+// forward 3D real FFT of a real grid [nz][ny][nx] (optionally min(1, x + fixture)) into the
+// half spectrum [Pz][Py][Hs] of plan `t`, using X1 / X2 as intermediates
+imf_status forward_real_3d(imf_handle h, const Tool &t, const float *src, const uint8_t *fix, int nx, int ny, int nz,
+                           float2 *X1, float2 *X2, float2 *out, float scale, int conj_out, cudaStream_t s)
+{
+    {
+        RfftArgs a{};
+        a.src = src; a.fix = fix; a.src_sy = nx; a.src_sz = (long)nx * ny; a.rows_y = ny; a.rows = ny * nz;
+        a.nin = nx; a.out = X1; a.out_sy = t.Hs; a.out_sz = (long)ny * t.Hs; a.M = t.M; a.twM = t.twM; a.twP = t.twP;
+        a.plan = t.plM;
+        Launch L(h, KID_RFFT_FWD, s);
+        launch_rfft_fwd(a, s);
+    }
+    {
+        AxisArgs a{};
+        a.in = X1; a.in_sb = (long)ny * t.Hs; a.in_sl = t.Hs;
+        a.out = X2; a.out_sb = (long)t.P[1] * t.Hs; a.out_sl = t.Hs;
+        a.nx = t.Hx; a.lin = ny; a.j0 = 0; a.lout = t.P[1]; a.scale = 1.f; a.tw = t.twy; a.plan = t.ply;
+        Launch L(h, KID_AXIS_FWD, s);
+        launch_axis_fft(-1, a, nz, 1, s);
+    }
+    {
+        AxisArgs a{};
+        a.in = X2; a.in_sb = t.Hs; a.in_sl = (long)t.P[1] * t.Hs;
+        a.out = out; a.out_sb = t.Hs; a.out_sl = (long)t.P[1] * t.Hs;
+        a.nx = t.Hx; a.lin = nz; a.j0 = 0; a.lout = t.P[2]; a.scale = scale; a.conj_out = conj_out;
+        a.tw = t.twz; a.plan = t.plz;
+        Launch L(h, KID_AXIS_FWD, s);
+        launch_axis_fft(-1, a, t.P[1], 1, s);
+    }
+    return IMF_OK;
+}
+
+} // namespace
+
+// ============================================================================== C ABI
+
+extern "C" {
+
+void imf_default_options(imf_options *opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->voxel = 1.0;
+    opt->lambda = 0.01;
+    opt->tau = 0.5;
+    opt->theta_rel = 0.01;
+    opt->precision = IMF_AUTO;
+    opt->recheck = 1;
+    opt->recheck_band = 0.0;
+    opt->orient_batch = 0;
+    opt->hbm_budget_bytes = 0;
+}
+
+imf_status imf_create(const imf_options *opt, imf_handle *out)
+{
+    if (!out) return IMF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!opt) return IMF_ERR_INVALID_ARG;
+    if (opt->nx < 1 || opt->ny < 1 || opt->nz < 1) return IMF_ERR_INVALID_ARG;
+    if ((long)opt->nx * opt->ny * opt->nz > (1L << 31) - 1) return IMF_ERR_INVALID_ARG;
+    if (!(opt->lambda >= 0 && opt->lambda < 1) || !(opt->tau >= 0 && opt->tau <= 1) || !(opt->theta_rel >= 0) ||
+        !(opt->voxel > 0))
+        return IMF_ERR_INVALID_ARG;
+    if (opt->precision < IMF_AUTO || opt->precision > IMF_BF16_DIRECT) return IMF_ERR_INVALID_ARG;
+    imf_handle h = new (std::nothrow) imf_handle_s();
+    if (!h) return IMF_ERR_OOM;
+    h->opt = *opt;
+    *out = h;
+    return IMF_OK;
+}
+
+void imf_destroy(imf_handle h)
+{
+    if (!h) return;
+    if (h->used_stream) cudaStreamSynchronize(h->last_stream);
+    for (auto &t : h->tools) free_tool(h, t);
+    dfree(h, h->rho_spec, h->rho_spec_n);
+    dfree(h, h->X1, h->X1_n);
+    dfree(h, h->X2, h->X2_n);
+    dfree(h, h->Y1, h->Y1_n * h->slots);
+    dfree(h, h->Y2, h->Y2_n * h->slots);
+    dfree(h, h->g, h->g_n * h->slots);
+    dfree(h, h->bits, h->bits_n * h->slots);
+    dfree(h, h->f, 0);
+    dfree(h, h->A, 0);
+    dfree(h, h->flags, (size_t)h->flag_cap);
+    dfree(h, h->dev_small, 8);
+    for (float **p : {&h->h_rho, &h->h_fbar, &h->h_raw}) dfree(h, *p, 0);
+    for (uint8_t **p : {&h->h_fix, &h->h_sec, &h->h_acc}) dfree(h, *p, 0);
+    for (auto &r : h->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    delete h;
+}
+
+const char *imf_last_error(imf_handle h)
+{
+    if (!h) return "null handle";
+    return h->err.c_str();
+}
+
+imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const uint8_t *cutter,
+                        const uint8_t *sharp_mask, int tx, int ty, int tz, const int origin[3], const double *quats,
+                        int n_orient)
+{
+    if (!h) return IMF_ERR_INVALID_ARG;
+    if (tool_id < 0 || tool_id >= 64 || tool_id > h->n_tools)
+        return fail(h, IMF_ERR_INVALID_ARG, "tool_id %d: ids are set densely from 0 (have %d)", tool_id, h->n_tools);
+    if (!holder || !cutter || !origin || !quats) return fail(h, IMF_ERR_INVALID_ARG, "NULL tool argument");
+    if (tx < 1 || ty < 1 || tz < 1 || tx > 340 || ty > 340 || tz > 340)
+        return fail(h, IMF_ERR_INVALID_ARG, "tool extents %dx%dx%d outside [1, 340]", tx, ty, tz);
+    if (n_orient < 1 || n_orient > 4096) return fail(h, IMF_ERR_INVALID_ARG, "n_orient %d outside [1, 4096]", n_orient);
+    const long tv = (long)tx * ty * tz;
+    std::vector<uint8_t> T(tv), K(tv), S(tv);
+    long nK = 0, nT = 0;
+    for (long i = 0; i < tv; ++i) {
+        K[i] = cutter[i] ? 1 : 0;
+        T[i] = (holder[i] || cutter[i]) ? 1 : 0;
+        S[i] = sharp_mask ? (uint8_t)(sharp_mask[i] && cutter[i]) : K[i];
+        nK += K[i];
+        nT += T[i];
+    }
+    if (nK == 0) return fail(h, IMF_ERR_INVALID_ARG, "empty cutter");
+    for (int i = 0; i < n_orient; ++i) {
+        const double *q = quats + 4 * i;
+        const double nn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+        if (!(nn > 1e-300) || !std::isfinite(nn)) return fail(h, IMF_ERR_INVALID_ARG, "quaternion %d is zero or not finite", i);
+    }
+    if (h->used_stream) CU(cudaStreamSynchronize(h->last_stream));
+    Tool &t = h->tools[tool_id];
+    if (t.set) free_tool(h, t);
+    t.tx = tx; t.ty = ty; t.tz = tz;
+    t.o[0] = origin[0]; t.o[1] = origin[1]; t.o[2] = origin[2];
+    t.n_orient = n_orient;
+    t.size_T = nT;
+    t.theta = h->opt.theta_rel * (double)nT;
+
+    // --- rotate and resample on the device (Alg. 1 Rotate)
+    std::vector<double> R(9 * (size_t)n_orient);
+    std::vector<int> box(6 * (size_t)n_orient);
+    std::vector<long> boff(n_orient + 1, 0);
+    long maxb = 0;
+    for (int i = 0; i < n_orient; ++i) {
+        quat_to_R(quats + 4 * i, &R[9 * i]);
+        scan_box(&R[9 * i], tx, ty, tz, t.o, &box[6 * i]);
+        const long v = (long)box[6 * i + 3] * box[6 * i + 4] * box[6 * i + 5];
+        boff[i + 1] = boff[i] + v;
+        maxb = std::max(maxb, v);
+    }
+    const long tot = boff[n_orient];
+    uint8_t *dT = nullptr, *dK = nullptr, *dS = nullptr, *dout = nullptr;
+    double *dR = nullptr;
+    int *dbox = nullptr;
+    long *dboff = nullptr;
+    imf_status st = IMF_OK;
+    std::vector<uint8_t> hout;
+    {
+        auto cleanup = [&]() {
+            dfree(h, dT, (size_t)tv); dfree(h, dK, (size_t)tv); dfree(h, dS, (size_t)tv);
+            dfree(h, dout, (size_t)tot * 3); dfree(h, dR, R.size()); dfree(h, dbox, box.size());
+            dfree(h, dboff, boff.size());
+        };
+        if ((st = upload(h, &dT, T)) || (st = upload(h, &dK, K)) || (st = upload(h, &dS, S)) ||
+            (st = upload(h, &dR, R)) || (st = upload(h, &dbox, box)) || (st = upload(h, &dboff, boff)) ||
+            (st = dalloc(h, &dout, (size_t)tot * 3))) {
+            cleanup();
+            return st;
+        }
+        RotateArgs a{};
+        a.T = dT; a.K = dK; a.Sm = dS; a.tx = tx; a.ty = ty; a.tz = tz; a.ox = t.o[0]; a.oy = t.o[1]; a.oz = t.o[2];
+        a.R = dR; a.box = dbox; a.box_off = dboff; a.outT = dout; a.outK = dout + tot; a.outS = dout + 2 * tot;
+        a.n_orient = n_orient; a.max_box = maxb;
+        {
+            Launch L(h, KID_ROTATE, 0);
+            launch_rotate(a, 0);
+        }
+        hout.resize((size_t)tot * 3);
+        cudaError_t e = cudaMemcpy(hout.data(), dout, (size_t)tot * 3, cudaMemcpyDeviceToHost);
+        cleanup();
+        if (e != cudaSuccess) return fail(h, IMF_ERR_CUDA, "rotate: %s", cudaGetErrorString(e));
+    }
+    // --- offset lists, cutter row intervals
+    t.rt.assign(n_orient, {});
+    t.rk.assign(n_orient, {});
+    t.sh.assign(n_orient, {});
+    std::vector<std::vector<int32_t>> ivs(n_orient);
+    int vlo[3] = {1 << 30, 1 << 30, 1 << 30}, vhi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+    std::vector<int> rvlo(3 * n_orient), rvhi(3 * n_orient);
+    bool anyK = false;
+    for (int k = 0; k < 3; ++k) { t.kmin[k] = 1 << 30; t.kmax[k] = -(1 << 30); }
+    for (int i = 0; i < n_orient; ++i) {
+        const int *b = &box[6 * i];
+        const uint8_t *bT = hout.data() + boff[i], *bK = hout.data() + tot + boff[i], *bS = hout.data() + 2 * tot + boff[i];
+        int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+        for (int z = 0; z < b[5]; ++z)
+            for (int y = 0; y < b[4]; ++y) {
+                int run = -1;
+                for (int x = 0; x <= b[3]; ++x) {
+                    const long id = ((long)z * b[4] + y) * b[3] + x;
+                    const int v[3] = {b[0] + x, b[1] + y, b[2] + z};
+                    const bool inK = x < b[3] && bK[id];
+                    if (x < b[3] && bT[id]) {
+                        t.rt[i].insert(t.rt[i].end(), v, v + 3);
+                        for (int c = 0; c < 3; ++c) { lo[c] = std::min(lo[c], v[c]); hi[c] = std::max(hi[c], v[c]); }
+                    }
+                    if (inK) {
+                        t.rk[i].insert(t.rk[i].end(), v, v + 3);
+                        for (int c = 0; c < 3; ++c) { t.kmin[c] = std::min(t.kmin[c], v[c]); t.kmax[c] = std::max(t.kmax[c], v[c]); }
+                        if (run < 0) run = x;
+                    } else if (run >= 0) {
+                        ivs[i].insert(ivs[i].end(), {b[0] + run, b[0] + x - 1, b[1] + y, b[2] + z});
+                        run = -1;
+                    }
+                    if (x < b[3] && bS[id]) t.sh[i].insert(t.sh[i].end(), v, v + 3);
+                }
+            }
+        for (int c = 0; c < 3; ++c) { rvlo[3 * i + c] = lo[c]; rvhi[3 * i + c] = hi[c]; }
+        if (!t.rk[i].empty()) anyK = true;
+        for (int c = 0; c < 3; ++c) { vlo[c] = std::min(vlo[c], lo[c]); vhi[c] = std::max(vhi[c], hi[c]); }
+    }
+    if (!anyK) {
+        free_tool(h, t);
+        return fail(h, IMF_ERR_INVALID_ARG, "the cutter vanishes under every orientation");
+    }
+    // --- plan: padded sizes and the translation window
+    const int n[3] = {h->opt.nx, h->opt.ny, h->opt.nz};
+    int req[3];
+    for (int c = 0; c < 3; ++c) {
+        t.win[c] = n[c] + t.kmax[c] - t.kmin[c];
+        int r = t.win[c];
+        for (int i = 0; i < n_orient; ++i) {
+            if (t.rk[i].empty()) continue;
+            r = std::max(r, n[c] + std::max(t.kmax[c] - rvlo[3 * i + c], rvhi[3 * i + c] - t.kmin[c]));
+        }
+        req[c] = r;
+        if (vlo[c] < -511 || vhi[c] > 511) {
+            free_tool(h, t);
+            return fail(h, IMF_ERR_INVALID_ARG, "rotated tool offsets exceed +-511 voxels");
+        }
+    }
+    t.M = next_smooth((req[0] + 1) / 2);
+    t.P[0] = 2 * t.M;
+    t.P[1] = next_smooth(req[1]);
+    t.P[2] = next_smooth(req[2]);
+    t.Hx = t.M + 1;
+    t.Hs = (t.Hx + 1) & ~1;
+    t.gpx = (t.win[0] + 3) & ~3;
+    t.wpr = (t.win[0] + 31) / 32 + 2;
+    if (!make_plan(t.M, &t.plM) || !make_plan(t.P[1], &t.ply) || !make_plan(t.P[2], &t.plz)) {
+        free_tool(h, t);
+        return fail(h, IMF_ERR_INVALID_ARG, "no FFT plan for %d x %d x %d", t.P[0], t.P[1], t.P[2]);
+    }
+    const double ptot = (double)t.P[0] * t.P[1] * t.P[2];
+    const double band_auto = 4e-6 * (double)nT + 1e-3;
+    t.band = h->opt.recheck_band > 0 ? h->opt.recheck_band : band_auto;
+    // --- device tables
+    std::vector<float2> tw;
+    std::vector<uint32_t> rto;
+    std::vector<int> rts(n_orient + 1, 0), ivst(n_orient + 1, 0), shs(n_orient + 1, 0), shl;
+    std::vector<int4> ivv;
+    for (int i = 0; i < n_orient; ++i) {
+        for (size_t m = 0; m < t.rt[i].size(); m += 3)
+            rto.push_back((uint32_t)(t.rt[i][m] + 512) | ((uint32_t)(t.rt[i][m + 1] + 512) << 10) |
+                          ((uint32_t)(t.rt[i][m + 2] + 512) << 20));
+        rts[i + 1] = (int)rto.size();
+        for (size_t m = 0; m < ivs[i].size(); m += 4) ivv.push_back(make_int4(ivs[i][m], ivs[i][m + 1], ivs[i][m + 2], ivs[i][m + 3]));
+        ivst[i + 1] = (int)ivv.size();
+        for (size_t m = 0; m < t.sh[i].size(); m += 3)
+            shl.push_back((int)(((long)t.sh[i][m + 2] * t.win[1] + t.sh[i][m + 1]) * t.gpx + t.sh[i][m]));
+        shs[i + 1] = (int)shl.size();
+    }
+    t.n_rt = (long)rto.size();
+    t.n_rk = 0;
+    for (auto &v : t.rk) t.n_rk += (long)v.size() / 3;
+    t.n_sh = (long)shl.size();
+    st = IMF_OK;
+    auto bail = [&](imf_status s2) { free_tool(h, t); return s2; };
+    twiddles(t.M, t.M, t.M, tw);
+    if ((st = upload(h, &t.twM, tw))) return bail(st);
+    twiddles(t.P[0], t.P[0], t.M + 1, tw);
+    if ((st = upload(h, &t.twP, tw))) return bail(st);
+    twiddles(t.P[1], t.P[1], t.P[1], tw);
+    if ((st = upload(h, &t.twy, tw))) return bail(st);
+    twiddles(t.P[2], t.P[2], t.P[2], tw);
+    if ((st = upload(h, &t.twz, tw))) return bail(st);
+    if ((st = upload(h, &t.rt_off, rto)) || (st = upload(h, &t.rt_start, rts)) || (st = upload(h, &t.iv, ivv)) ||
+        (st = upload(h, &t.iv_start, ivst)) || (st = upload(h, &t.sh_lin, shl)) || (st = upload(h, &t.sh_start, shs)))
+        return bail(st);
+    // --- tool spectra: conj(FFT(1_RT)) / Ptot (reflection as conjugation, Alg. 1 footnote)
+    const size_t per = (size_t)t.P[2] * t.P[1] * t.Hs;
+    t.spec_bytes = per * n_orient * sizeof(float2);
+    if ((st = dalloc(h, &t.spec, per * n_orient))) return bail(st);
+    float *dense = nullptr;
+    float2 *s1 = nullptr, *s2 = nullptr;
+    const size_t dn = (size_t)t.P[0] * t.P[1] * t.P[2];
+    if ((st = dalloc(h, &dense, dn)) || (st = dalloc(h, &s1, per)) || (st = dalloc(h, &s2, per))) {
+        dfree(h, dense, dn); dfree(h, s1, per); dfree(h, s2, per);
+        return bail(st);
+    }
+    for (int i = 0; i < n_orient && st == IMF_OK; ++i) {
+        cudaMemsetAsync(dense, 0, dn * sizeof(float), 0);
+        const int cnt = rts[i + 1] - rts[i];
+        {
+            Launch L(h, KID_SPEC, 0);
+            if (cnt > 0) launch_scatter_tool(dense, t.P[0], t.P[1], t.P[2], t.rt_off + rts[i], cnt, t.kmax[0], t.kmax[1], t.kmax[2], 0);
+        }
+        st = forward_real_3d(h, t, dense, nullptr, t.P[0], t.P[1], t.P[2], s1, s2, t.spec + per * i, (float)(1.0 / ptot), 1, 0);
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    dfree(h, dense, dn); dfree(h, s1, per); dfree(h, s2, per);
+    if (st != IMF_OK) return bail(st);
+    if (e != cudaSuccess) return bail(fail(h, IMF_ERR_CUDA, "tool spectrum: %s", cudaGetErrorString(e)));
+    t.set = true;
+    if (tool_id == h->n_tools) h->n_tools++;
+    return IMF_OK;
+}
+
+static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fix, float *fbar, uint8_t *sec,
+                               float *raw, uint8_t *acc, cudaStream_t s)
+{
+    const imf_options &op = h->opt;
+    const long N = (long)op.nx * op.ny * op.nz;
+    TRY(ensure_work(h));
+    h->last_stream = s;
+    h->used_stream = true;
+    int *status = h->dev_small, *fcount = h->dev_small + 1;
+    unsigned *maxbits = (unsigned *)(h->dev_small + 2);
+    {
+        Launch L(h, KID_INIT, s);
+        launch_fill_f32(h->f, INFINITY, N, s);
+    }
+    CU(cudaMemsetAsync(h->A, 0, sizeof(uint32_t) * (size_t)op.nz * op.ny * h->awords, s));
+    CU(cudaMemsetAsync(maxbits, 0, sizeof(unsigned), s));
+    CU(cudaMemsetAsync(h->dev_small + 4, 0, sizeof(int), s));
+    for (int ti = 0; ti < h->n_tools; ++ti) {
+        const Tool &t = h->tools[ti];
+        TRY(forward_real_3d(h, t, rho, fix, op.nx, op.ny, op.nz, h->X1, h->X2, h->rho_spec, 1.f, 0, s));
+        const long y1so = (long)t.win[2] * t.P[1] * t.Hs;
+        const long y2so = (long)t.win[2] * t.win[1] * t.Hs;
+        const long gso = (long)t.win[2] * t.win[1] * t.gpx;
+        const long bso = (long)t.win[2] * t.win[1] * t.wpr;
+        const long spso = (long)t.P[2] * t.P[1] * t.Hs;
+        for (int o0 = 0; o0 < t.n_orient; o0 += h->slots) {
+            const int nb = std::min(h->slots, t.n_orient - o0);
+            if (op.recheck) CU(cudaMemsetAsync(fcount, 0, sizeof(int), s));
+            {
+                AxisArgs a{};
+                a.in = t.spec + spso * o0; a.in_so = spso; a.in_sb = t.Hs; a.in_sl = (long)t.P[1] * t.Hs;
+                a.mul = h->rho_spec; a.mul_so = 0; a.mul_sb = t.Hs; a.mul_sl = (long)t.P[1] * t.Hs;
+                a.out = h->Y1; a.out_so = y1so; a.out_sb = t.Hs; a.out_sl = (long)t.P[1] * t.Hs;
+                a.nx = t.Hx; a.lin = t.P[2]; a.j0 = 0; a.lout = t.win[2]; a.scale = 1.f; a.tw = t.twz; a.plan = t.plz;
+                Launch L(h, KID_AXIS_INV_MUL, s);
+                launch_axis_fft(1, a, t.P[1], nb, s);
+            }
+            {
+                AxisArgs a{};
+                a.in = h->Y1; a.in_so = y1so; a.in_sb = (long)t.P[1] * t.Hs; a.in_sl = t.Hs;
+                a.out = h->Y2; a.out_so = y2so; a.out_sb = (long)t.win[1] * t.Hs; a.out_sl = t.Hs;
+                a.nx = t.Hx; a.lin = t.P[1]; a.j0 = 0; a.lout = t.win[1]; a.scale = 1.f; a.tw = t.twy; a.plan = t.ply;
+                Launch L(h, KID_AXIS_INV, s);
+                launch_axis_fft(1, a, t.win[2], nb, s);
+            }
+            {
+                IrfftArgs a{};
+                a.in = h->Y2; a.in_sy = t.Hs; a.in_sz = (long)t.win[1] * t.Hs; a.in_so = y2so;
+                a.rows_y = t.win[1]; a.rows = t.win[1] * t.win[2]; a.nout = t.win[0];
+                a.g = h->g; a.g_sy = t.gpx; a.g_sz = (long)t.win[1] * t.gpx; a.g_so = gso;
+                a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
+                a.theta = (float)t.theta; a.band = (float)t.band; a.flag = op.recheck;
+                a.flags = h->flags; a.flag_count = fcount; a.flag_total = h->dev_small + 4; a.flag_cap = h->flag_cap;
+                a.status = status;
+                a.orient_base = o0; a.M = t.M; a.twM = t.twM; a.twP = t.twP; a.plan = t.plM;
+                Launch L(h, KID_IRFFT_THRESH, s);
+                launch_irfft_threshold(a, nb, s);
+            }
+            if (op.recheck) {
+                RecheckArgs a{};
+                a.flags = h->flags; a.count = fcount; a.cap = h->flag_cap; a.rho = rho; a.fix = fix;
+                a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.rt_off = t.rt_off; a.rt_start = t.rt_start;
+                a.wx = t.win[0]; a.wy = t.win[1]; a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2];
+                a.g = h->g; a.g_sy = t.gpx; a.g_sz = (long)t.win[1] * t.gpx; a.g_so = gso;
+                a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
+                a.theta = t.theta; a.orient_base = o0;
+                Launch L(h, KID_RECHECK, s);
+                launch_recheck(a, s);
+            }
+            {
+                SweepArgs a{};
+                a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
+                a.iv = t.iv; a.iv_start = t.iv_start; a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.awords = h->awords;
+                a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2]; a.orient_base = o0; a.nb = nb; a.A = h->A;
+                Launch L(h, KID_SWEEP, s);
+                launch_sweep(a, s);
+            }
+            {
+                ErodeArgs a{};
+                a.g = h->g; a.g_so = gso; a.gpx = t.gpx; a.gpy = t.win[1]; a.sh_lin = t.sh_lin; a.sh_start = t.sh_start;
+                a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2];
+                a.orient_base = o0; a.nb = nb; a.f = h->f;
+                Launch L(h, KID_ERODE, s);
+                launch_erode(a, s);
+            }
+            h->last_batch_base = o0;
+            h->last_batch_n = nb;
+            h->last_tool = ti;
+        }
+    }
+    {
+        Launch L(h, KID_MAX, s);
+        launch_max_omega0(h->f, fix, N, maxbits, s);
+    }
+    {
+        FinalizeArgs a{};
+        a.f = h->f; a.rho = rho; a.fix = fix; a.A = h->A; a.nx = op.nx; a.ny = op.ny; a.nz = op.nz;
+        a.awords = h->awords; a.maxbits = maxbits; a.lambda = op.lambda; a.tau = op.tau;
+        a.fbar = fbar; a.secluded = sec; a.raw = raw; a.acc = acc;
+        Launch L(h, KID_FINALIZE, s);
+        launch_finalize(a, s);
+    }
+    CU(cudaGetLastError());
+    h->computes++;
+    return IMF_OK;
+}
+
+imf_status imf_compute(imf_handle h, const float *rho_omega, const uint8_t *fixture, float *imf_bar,
+                       uint8_t *secluded, float *imf_raw, uint8_t *accessible, void *cuda_stream)
+{
+    if (!h) return IMF_ERR_INVALID_ARG;
+    if (h->n_tools == 0) return fail(h, IMF_ERR_NOT_READY, "imf_compute before imf_set_tool");
+    for (int i = 0; i < h->n_tools; ++i)
+        if (!h->tools[i].set) return fail(h, IMF_ERR_NOT_READY, "tool %d not set", i);
+    if (!rho_omega || !imf_bar || !secluded) return fail(h, IMF_ERR_INVALID_ARG, "NULL required array");
+    return compute_impl(h, rho_omega, fixture, imf_bar, secluded, imf_raw, accessible, (cudaStream_t)cuda_stream);
+}
+
+imf_status imf_compute_host(imf_handle h, const float *rho_omega, const uint8_t *fixture, float *imf_bar,
+                            uint8_t *secluded, float *imf_raw, uint8_t *accessible, void *cuda_stream)
+{
+    if (!h) return IMF_ERR_INVALID_ARG;
+    if (!rho_omega || !imf_bar || !secluded) return fail(h, IMF_ERR_INVALID_ARG, "NULL required array");
+    const size_t N = (size_t)h->opt.nx * h->opt.ny * h->opt.nz;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!h->h_rho) {
+        TRY(dalloc(h, &h->h_rho, N)); TRY(dalloc(h, &h->h_fbar, N)); TRY(dalloc(h, &h->h_raw, N));
+        TRY(dalloc(h, &h->h_fix, N)); TRY(dalloc(h, &h->h_sec, N)); TRY(dalloc(h, &h->h_acc, N));
+    }
+    CU(cudaMemcpyAsync(h->h_rho, rho_omega, N * sizeof(float), cudaMemcpyHostToDevice, s));
+    if (fixture) CU(cudaMemcpyAsync(h->h_fix, fixture, N, cudaMemcpyHostToDevice, s));
+    TRY(imf_compute(h, h->h_rho, fixture ? h->h_fix : nullptr, h->h_fbar, h->h_sec, imf_raw ? h->h_raw : nullptr,
+                    accessible ? h->h_acc : nullptr, cuda_stream));
+    CU(cudaMemcpyAsync(imf_bar, h->h_fbar, N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(secluded, h->h_sec, N, cudaMemcpyDeviceToHost, s));
+    if (imf_raw) CU(cudaMemcpyAsync(imf_raw, h->h_raw, N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (accessible) CU(cudaMemcpyAsync(accessible, h->h_acc, N, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return IMF_OK;
+}
+
+imf_status imf_penalize_sensitivity(imf_handle h, float *sens, const float *rho_omega, const float *imf_bar,
+                                    const uint8_t *secluded, const uint8_t *fixture, double w_acc, void *cuda_stream)
+{
+    if (!h) return IMF_ERR_INVALID_ARG;
+    if (!sens || !rho_omega || !imf_bar || !secluded) return fail(h, IMF_ERR_INVALID_ARG, "NULL required array");
+    if (!(w_acc >= 0.0 && w_acc < 1.0)) return fail(h, IMF_ERR_INVALID_ARG, "w_acc %g outside [0, 1)", w_acc);
+    const long N = (long)h->opt.nx * h->opt.ny * h->opt.nz;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!h->dev_small) {
+        TRY(dalloc(h, &h->dev_small, (size_t)8));
+        CU(cudaMemset(h->dev_small, 0, 8 * sizeof(int)));
+    }
+    unsigned *mb = (unsigned *)(h->dev_small + 3);
+    h->last_stream = s;
+    h->used_stream = true;
+    CU(cudaMemsetAsync(mb, 0, sizeof(unsigned), s));
+    {
+        Launch L(h, KID_ABSMAX, s);
+        launch_absmax_omega0(sens, fixture, N, mb, s);
+    }
+    {
+        Launch L(h, KID_PENALIZE, s);
+        launch_penalize(sens, rho_omega, imf_bar, secluded, N, mb, w_acc, h->opt.tau, s);
+    }
+    CU(cudaGetLastError());
+    return IMF_OK;
+}
+
+imf_status imf_sync_status(imf_handle h)
+{
+    if (!h) return IMF_ERR_INVALID_ARG;
+    if (h->used_stream) CU(cudaStreamSynchronize(h->last_stream));
+    CU(cudaGetLastError());
+    if (!h->dev_small) return IMF_OK;
+    int st[5] = {0, 0, 0, 0, 0};
+    CU(cudaMemcpy(st, h->dev_small, sizeof st, cudaMemcpyDeviceToHost));
+    h->flagged_last = st[4];
+    h->flagged_total += st[4];
+    if (st[0] != 0) {
+        int z = 0;
+        CU(cudaMemcpy(h->dev_small, &z, sizeof z, cudaMemcpyHostToDevice));
+        return fail(h, (imf_status)st[0], "device status %d (near-threshold list capacity %d)", st[0], h->flag_cap);
+    }
+    return IMF_OK;
+}
+
+imf_status imf_get_tool_info(imf_handle h, int tool_id, imf_tool_info *out)
+{
+    if (!h || !out || tool_id < 0 || tool_id >= h->n_tools || !h->tools[tool_id].set) return IMF_ERR_INVALID_ARG;
+    const Tool &t = h->tools[tool_id];
+    out->n_orient = t.n_orient;
+    for (int c = 0; c < 3; ++c) { out->P[c] = t.P[c]; out->kmax[c] = t.kmax[c]; out->win[c] = t.win[c]; }
+    out->size_T = t.size_T;
+    out->theta = t.theta;
+    out->band = t.band;
+    out->n_rt = t.n_rt;
+    out->n_rk = t.n_rk;
+    out->n_sharp = t.n_sh;
+    out->path = IMF_FP32_FFT;
+    out->spectra_bytes = t.spec_bytes;
+    return IMF_OK;
+}
+
+imf_status imf_get_offsets(imf_handle h, int tool_id, int orient, int which, int32_t *out, long cap, long *n)
+{
+    if (!h || !n || tool_id < 0 || tool_id >= h->n_tools || !h->tools[tool_id].set) return IMF_ERR_INVALID_ARG;
+    const Tool &t = h->tools[tool_id];
+    if (orient < 0 || orient >= t.n_orient || which < 0 || which > 2) return IMF_ERR_INVALID_ARG;
+    const std::vector<int32_t> &v = which == 0 ? t.rt[orient] : which == 1 ? t.rk[orient] : t.sh[orient];
+    *n = (long)v.size() / 3;
+    if (out) {
+        if (cap < *n) return fail(h, IMF_ERR_INVALID_ARG, "capacity %ld < %ld", cap, *n);
+        std::memcpy(out, v.data(), v.size() * sizeof(int32_t));
+    }
+    return IMF_OK;
+}
+
+imf_status imf_set_debug(imf_handle h, int keep_last_g)
+{
+    if (!h) return IMF_ERR_INVALID_ARG;
+    h->keep_g = keep_last_g != 0;
+    return IMF_OK;
+}
+
+imf_status imf_get_last_g(imf_handle h, int slot, float *g_out, long cap, int *orient_out)
+{
+    if (!h || h->last_tool < 0 || slot < 0 || slot >= h->last_batch_n) return IMF_ERR_INVALID_ARG;
+    const Tool &t = h->tools[h->last_tool];
+    const long n = (long)t.win[2] * t.win[1] * t.gpx;
+    if (orient_out) *orient_out = h->last_batch_base + slot;
+    if (!g_out) return IMF_OK;
+    if (cap < n) return fail(h, IMF_ERR_INVALID_ARG, "capacity %ld < %ld", cap, n);
+    if (h->used_stream) CU(cudaStreamSynchronize(h->last_stream));
+    CU(cudaMemcpy(g_out, h->g + (size_t)slot * h->g_n, n * sizeof(float), cudaMemcpyDeviceToHost));
+    return IMF_OK;
+}
+
+imf_status imf_get_stats(imf_handle h, imf_stats *out)
+{
+    if (!h || !out) return IMF_ERR_INVALID_ARG;
+    out->launches = h->launches;
+    out->computes = h->computes;
+    out->flagged = h->flagged_last;
+    out->flagged_total = h->flagged_total;
+    out->n_kernels = KID_COUNT;
+    return IMF_OK;
+}
+
+imf_status imf_set_profiling(imf_handle h, int on)
+{
+    if (!h) return IMF_ERR_INVALID_ARG;
+    h->prof = on != 0;
+    return IMF_OK;
+}
+
+imf_status imf_get_kernel_time(imf_handle h, int i, const char **name, double *total_ms, long *count)
+{
+    if (!h || i < 0 || i >= KID_COUNT) return IMF_ERR_INVALID_ARG;
+    drain_profile(h);
+    if (name) *name = kKernelNames[i];
+    if (total_ms) *total_ms = h->prof_ms[i];
+    if (count) *count = h->prof_cnt[i];
+    return IMF_OK;
+}
+
+imf_status imf_reset_kernel_times(imf_handle h)
+{
+    if (!h) return IMF_ERR_INVALID_ARG;
+    drain_profile(h);
+    for (int i = 0; i < KID_COUNT; ++i) { h->prof_ms[i] = 0; h->prof_cnt[i] = 0; }
+    return IMF_OK;
+}
+
+} // extern "C"

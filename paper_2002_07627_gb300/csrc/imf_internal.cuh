@@ -1,0 +1,167 @@
+// Internal kernel interface of libimf (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+
+namespace imf {
+
+constexpr int kThreads = 256;
+
+// Device status word values (mirror imf_status).
+constexpr int kDevOk = 0;
+constexpr int kDevOverflow = 7;
+
+// ---------------------------------------------------------------------------------------
+// FFT passes
+// ---------------------------------------------------------------------------------------
+
+// Complex FFT along a strided axis (y or z of the half-spectrum [z][y][kx]). A block
+// transforms W consecutive kx columns of one batch row `b` of one orientation `o`.
+struct AxisArgs {
+    const float2 *in;
+    float2 *out;
+    const float2 *mul;           // optional pointwise factor applied on load
+    long in_so, in_sb, in_sl;    // strides in complex elements: orientation, batch, axis
+    long out_so, out_sb, out_sl;
+    long mul_so, mul_sb, mul_sl;
+    int nx;                      // contiguous extent (number of kx columns)
+    int lin;                     // input samples j < lin are read, the rest are zero
+    int j0, lout;                // output samples j0 .. j0+lout-1 are written
+    float scale;
+    int conj_out;
+    const float2 *tw;            // exp(-2 pi i m / L), m < L
+    FftPlan plan;
+};
+
+// Real-to-complex FFT along x (rows of a real grid), packed as a half-length complex FFT.
+struct RfftArgs {
+    const float *src;            // real rows
+    const uint8_t *fix;          // optional fixture: the row value becomes min(1, src + fix)
+    long src_sy, src_sz;         // row strides (elements)
+    int rows_y, rows;            // rows per z-plane, total rows
+    int nin;                     // valid samples per row (<= 2M), the rest are zero
+    float2 *out;
+    long out_sy, out_sz;         // complex row strides
+    int M;                       // half length: P = 2M
+    const float2 *twM;           // exp(-2 pi i m / M)
+    const float2 *twP;           // exp(-2 pi i k / P), k <= M
+    FftPlan plan;                // length M
+};
+
+// Complex-to-real inverse FFT along x with the collision threshold fused in (Sec. 2.1.1:
+// free translations are those with g <= theta).
+struct IrfftArgs {
+    const float2 *in;
+    long in_sy, in_sz, in_so;
+    int rows_y, rows;            // window rows per z-plane, total window rows
+    int nout;                    // window extent along x
+    float *g;
+    long g_sy, g_sz, g_so;
+    uint32_t *bits;              // free bits, 32 translations per word along x
+    long b_sy, b_sz, b_so;
+    float theta, band;
+    int flag;                    // record translations with |g - theta| <= band
+    int2 *flags;
+    int *flag_count;
+    int *flag_total;
+    int flag_cap;
+    int *status;
+    int orient_base;
+    int M;
+    const float2 *twM, *twP;
+    FftPlan plan;
+};
+
+void launch_axis_fft(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s);
+void launch_rfft_fwd(const RfftArgs &a, cudaStream_t s);
+void launch_irfft_threshold(const IrfftArgs &a, int norient, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
+// IMF kernels
+// ---------------------------------------------------------------------------------------
+
+// Rotation and resampling of the tool (Alg. 1 Rotate): nearest neighbour, inverse map.
+struct RotateArgs {
+    const uint8_t *T, *K, *Sm;   // tool assembly, cutter, sharp-point mask [tz][ty][tx]
+    int tx, ty, tz, ox, oy, oz;
+    const double *R;             // 9 per orientation, row major
+    const int *box;              // 6 per orientation: lo[3], ext[3]
+    const long *box_off;         // start of each orientation's boxes in `out*`
+    uint8_t *outT, *outK, *outS;
+    int n_orient;
+    long max_box;                // largest box volume
+};
+void launch_rotate(const RotateArgs &a, cudaStream_t s);
+
+// Dense padded real tool array for the spectrum: ones at (v - kmax) mod P for v in R T.
+void launch_scatter_tool(float *dst, int Px, int Py, int Pz, const uint32_t *off, int n,
+                         int kx, int ky, int kz, cudaStream_t s);
+
+struct RecheckArgs {
+    const int2 *flags;
+    const int *count;
+    int cap;
+    const float *rho;
+    const uint8_t *fix;
+    int nx, ny, nz;
+    const uint32_t *rt_off;      // packed offsets of R T, all orientations
+    const int *rt_start;         // n_orient + 1
+    int wx, wy;                  // window extents (x, y)
+    int kx, ky, kz;              // kmax: window index = t + kmax
+    float *g;
+    long g_sy, g_sz, g_so;
+    uint32_t *bits;
+    long b_sy, b_sz, b_so;
+    double theta;
+    int orient_base;
+};
+void launch_recheck(const RecheckArgs &a, cudaStream_t s);
+
+struct SweepArgs {
+    const uint32_t *bits;
+    long b_sy, b_sz, b_so;
+    const int4 *iv;              // cutter row intervals (a, b, dy, dz), all orientations
+    const int *iv_start;         // n_orient + 1
+    int nx, ny, nz, awords;
+    int kx, ky, kz;
+    int orient_base, nb;
+    uint32_t *A;                 // accessible bits [nz][ny][awords], OR-accumulated
+};
+void launch_sweep(const SweepArgs &a, cudaStream_t s);
+
+struct ErodeArgs {
+    const float *g;
+    long g_so;
+    int gpx, gpy;                // window pitch (x) and rows per z-plane
+    const int *sh_lin;           // linear window offsets of the sharp points, all orientations
+    const int *sh_start;         // n_orient + 1
+    int nx, ny, nz;
+    int kx, ky, kz;
+    int orient_base, nb;
+    float *f;                    // running minimum over orientations and tools
+};
+void launch_erode(const ErodeArgs &a, cudaStream_t s);
+
+void launch_fill_f32(float *p, float v, long n, cudaStream_t s);
+void launch_max_omega0(const float *f, const uint8_t *fix, long n, unsigned *maxbits, cudaStream_t s);
+struct FinalizeArgs {
+    const float *f;
+    const float *rho;
+    const uint8_t *fix;
+    const uint32_t *A;
+    int nx, ny, nz, awords;
+    const unsigned *maxbits;
+    double lambda, tau;
+    float *fbar;
+    uint8_t *secluded;
+    float *raw;
+    uint8_t *acc;
+};
+void launch_finalize(const FinalizeArgs &a, cudaStream_t s);
+void launch_absmax_omega0(const float *v, const uint8_t *fix, long n, unsigned *maxbits, cudaStream_t s);
+void launch_penalize(float *sens, const float *rho, const float *fbar, const uint8_t *sec, long n,
+                     const unsigned *maxbits, double w, double tau, cudaStream_t s);
+
+} // namespace imf

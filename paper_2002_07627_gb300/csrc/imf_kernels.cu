@@ -1,0 +1,327 @@
+// IMF kernels other than the FFT passes: tool resampling, the exact near-threshold
+// re-check, the sweep of the cutter over the free translations, the minimum over sharp
+// points and orientations, and the normalisation / penalty tail of Alg. 1 and Alg. 2.
+#include <cfloat>
+
+#include "imf_internal.cuh"
+
+namespace imf {
+
+namespace {
+
+inline int blocks_for(long n, int per = kThreads, int cap = 152 * 16)
+{
+    long b = (n + per - 1) / per;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+// ---------------------------------------------------------------------------------------
+// Rotate (Alg. 1): nearest neighbour, inverse map about the origin voxel.
+// u_c = floor((R_0c v_0 + R_1c v_1) + R_2c v_2 + 1/2), every operation rounded to nearest
+// in FP64 with no contraction, so the set of resampled voxels is reproducible exactly.
+// ---------------------------------------------------------------------------------------
+__global__ void rotate_kernel(RotateArgs a)
+{
+    const int o = blockIdx.y;
+    const int *bx = a.box + 6 * o;
+    const long vol = (long)bx[3] * bx[4] * bx[5];
+    const double *R = a.R + 9 * o;
+    uint8_t *oT = a.outT + a.box_off[o], *oK = a.outK + a.box_off[o], *oS = a.outS + a.box_off[o];
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < vol; idx += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % bx[3]);
+        const int j = (int)((idx / bx[3]) % bx[4]);
+        const int k = (int)(idx / ((long)bx[3] * bx[4]));
+        const double v0 = bx[0] + i, v1 = bx[1] + j, v2 = bx[2] + k;
+        int u[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double p = __dadd_rn(__dadd_rn(__dmul_rn(R[c], v0), __dmul_rn(R[3 + c], v1)), __dmul_rn(R[6 + c], v2));
+            u[c] = (int)floor(__dadd_rn(p, 0.5));
+        }
+        const int ax = a.ox + u[0], ay = a.oy + u[1], az = a.oz + u[2];
+        uint8_t t = 0, kk = 0, ss = 0;
+        if (ax >= 0 && ax < a.tx && ay >= 0 && ay < a.ty && az >= 0 && az < a.tz) {
+            const long src = ((long)az * a.ty + ay) * a.tx + ax;
+            t = a.T[src];
+            kk = a.K[src];
+            ss = a.Sm[src];
+        }
+        oT[idx] = t;
+        oK[idx] = kk;
+        oS[idx] = ss;
+    }
+}
+
+__global__ void scatter_tool_kernel(float *dst, int Px, int Py, int Pz, const uint32_t *off, int n, int kx,
+                                    int ky, int kz)
+{
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+        const uint32_t p = off[m];
+        int x = (int)(p & 1023u) - 512 - kx, y = (int)((p >> 10) & 1023u) - 512 - ky, z = (int)((p >> 20) & 1023u) - 512 - kz;
+        x %= Px; if (x < 0) x += Px;
+        y %= Py; if (y < 0) y += Py;
+        z %= Pz; if (z < 0) z += Pz;
+        dst[((long)z * Py + y) * Px + x] = 1.0f;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Near-threshold re-check: g(t) = sum_{v in RT} rho_O(t + v) by a compensated FP32 sum
+// (Neumaier), compared with theta in FP64. One warp per flagged translation.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__global__ void recheck_kernel(RecheckArgs a)
+{
+    const int n = min(*a.count, a.cap);
+    const int lane = threadIdx.x & 31;
+    const long nw = ((long)gridDim.x * blockDim.x) >> 5;
+    for (long e = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n; e += nw) {
+        const int2 fl = a.flags[e];
+        const int og = fl.x, lin = fl.y;
+        const int i = lin % a.wx, y = (lin / a.wx) % a.wy, z = lin / (a.wx * a.wy);
+        const int tx = i - a.kx, ty = y - a.ky, tz = z - a.kz;
+        float s = 0.f, c = 0.f;
+        for (int m = a.rt_start[og] + lane; m < a.rt_start[og + 1]; m += 32) {
+            const uint32_t p = a.rt_off[m];
+            const int x = tx + (int)(p & 1023u) - 512;
+            const int yy = ty + (int)((p >> 10) & 1023u) - 512;
+            const int zz = tz + (int)((p >> 20) & 1023u) - 512;
+            if (x < 0 || yy < 0 || zz < 0 || x >= a.nx || yy >= a.ny || zz >= a.nz) continue;
+            const long idx = ((long)zz * a.ny + yy) * a.nx + x;
+            float r = a.rho[idx];
+            if (a.fix && a.fix[idx]) r = fminf(1.f, r + 1.f);
+            float t, err;
+            two_sum(s, r, t, err);
+            s = t;
+            c += err;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s, off);
+            const float c2 = __shfl_down_sync(0xffffffffu, c, off);
+            float t, err;
+            two_sum(s, s2, t, err);
+            s = t;
+            c = c + c2 + err;
+        }
+        if (lane == 0) {
+            const double tot = (double)s + (double)c;
+            const long slot = og - a.orient_base;
+            a.g[slot * a.g_so + (long)z * a.g_sz + (long)y * a.g_sy + i] = (float)tot;
+            uint32_t *w = a.bits + slot * a.b_so + (long)z * a.b_sz + (long)y * a.b_sy + (i >> 5);
+            const uint32_t bit = 1u << (i & 31);
+            if (tot <= a.theta) atomicOr(w, bit);
+            else atomicAnd(w, ~bit);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Sweep (Eq. eq_conv_A): A_R(x) = OR_{k in RK} free(x - k), on bit-packed rows. RK is a
+// union of runs [a, b] along x at fixed (dy, dz); a run contributes the sliding OR of
+// length b - a + 1 of one source row, computed on 64-bit windows by doubling shifts.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t bit_window(const uint32_t *row, int s)
+{
+    const int w0 = s >> 5, sh = s & 31;
+    uint64_t lo = (uint64_t)row[w0] | ((uint64_t)row[w0 + 1] << 32);
+    if (sh) lo = (lo >> sh) | ((uint64_t)row[w0 + 2] << (64 - sh));
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t dilate_bits(uint64_t w, int L)
+{
+    uint64_t d = w;
+    int span = 1;
+    while (span * 2 <= L) {
+        d |= d >> span;
+        span *= 2;
+    }
+    if (span < L) d |= d >> (L - span);
+    return (uint32_t)d;
+}
+
+__global__ void sweep_kernel(SweepArgs a)
+{
+    const long total = (long)a.awords * a.ny * a.nz;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int q = (int)(t % a.awords);
+        const int y = (int)((t / a.awords) % a.ny);
+        const int z = (int)(t / ((long)a.awords * a.ny));
+        uint32_t acc = 0;
+        for (int ob = 0; ob < a.nb; ++ob) {
+            const int og = a.orient_base + ob;
+            const uint32_t *bits = a.bits + ob * a.b_so;
+            for (int m = a.iv_start[og]; m < a.iv_start[og + 1]; ++m) {
+                const int4 iv = a.iv[m];
+                const uint32_t *row = bits + (long)(z - iv.w + a.kz) * a.b_sz + (long)(y - iv.z + a.ky) * a.b_sy;
+                const int L = iv.y - iv.x + 1;
+                const int s0 = 32 * q + a.kx - iv.y;
+                for (int c0 = 0; c0 < L; c0 += 32) acc |= dilate_bits(bit_window(row, s0 + c0), min(32, L - c0));
+            }
+        }
+        const int rem = a.nx - 32 * q;
+        if (rem < 32) acc &= (1u << rem) - 1u;
+        uint32_t *dst = a.A + ((long)z * a.ny + y) * a.awords + q;
+        *dst |= acc;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Minimum over sharp points (Eq. eq_imf_2): gamma_R(x) = min_k g_R(x - k), folded into the
+// running minimum over orientations and tools (Eq. eq_imf_5).
+// ---------------------------------------------------------------------------------------
+__global__ void erode_kernel(ErodeArgs a)
+{
+    const long n = (long)a.nx * a.ny * a.nz;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % a.nx);
+        const int y = (int)((idx / a.nx) % a.ny);
+        const int z = (int)(idx / ((long)a.nx * a.ny));
+        const long base = ((long)(z + a.kz) * a.gpy + (y + a.ky)) * a.gpx + (x + a.kx);
+        float m = a.f[idx];
+        for (int ob = 0; ob < a.nb; ++ob) {
+            const int og = a.orient_base + ob;
+            const float *g = a.g + ob * a.g_so + base;
+            for (int k = a.sh_start[og]; k < a.sh_start[og + 1]; ++k) m = fminf(m, g[-(long)a.sh_lin[k]]);
+        }
+        a.f[idx] = m;
+    }
+}
+
+__global__ void fill_f32_kernel(float *p, float v, long n)
+{
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) p[i] = v;
+}
+
+__device__ __forceinline__ float block_max(float v)
+{
+    __shared__ float red[32];
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
+        for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    }
+    return v;
+}
+
+// max over Omega_0 (non-fixture cells) of a nonnegative field, as an unsigned bit pattern
+__global__ void max_omega0_kernel(const float *f, const uint8_t *fix, long n, unsigned *maxbits, int absval)
+{
+    float m = 0.f;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        if (fix && fix[i]) continue;
+        float v = f[i];
+        if (absval) v = fabsf(v);
+        m = fmaxf(m, v);
+    }
+    m = block_max(m);
+    if (threadIdx.x == 0) atomicMax(maxbits, __float_as_uint(m));
+}
+
+// Alg. 1 tail: f_bar = f / M (FP64), B = [f_bar > lambda], f_bar <- f_bar B,
+// Gamma = Omega_0 [rho <= tau] B; outputs on fixture cells are 0.
+__global__ void finalize_kernel(FinalizeArgs a)
+{
+    const long n = (long)a.nx * a.ny * a.nz;
+    const float Mf = __uint_as_float(*a.maxbits);
+    const double M = (double)Mf;
+    const bool ok = Mf > 0.f && Mf <= FLT_MAX;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
+        const float f = a.f[idx];
+        const bool fixc = a.fix && a.fix[idx];
+        double fb = (ok && !fixc) ? (double)f / M : 0.0;
+        const bool B = fb > a.lambda;
+        if (!B) fb = 0.0;
+        a.fbar[idx] = (float)fb;
+        a.secluded[idx] = (uint8_t)(B && !((double)a.rho[idx] > a.tau));
+        if (a.raw) a.raw[idx] = f;
+        if (a.acc) {
+            const int x = (int)(idx % a.nx);
+            const long row = idx / a.nx;
+            const uint32_t w = a.A[row * a.awords + (x >> 5)];
+            a.acc[idx] = (uint8_t)(!fixc && ((w >> (x & 31)) & 1u));
+        }
+    }
+}
+
+// Eq. eq_filtered_sens with Eq. eq_accFilter (FP32).
+__global__ void penalize_kernel(float *sens, const float *rho, const float *fbar, const uint8_t *sec, long n,
+                                const unsigned *maxbits, float w, float tau)
+{
+    const float m = __uint_as_float(*maxbits);
+    const float inv = m > 0.f ? 1.f / m : 1.f;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float sb = m > 0.f ? sens[i] * inv : sens[i];
+        const float simf = rho[i] > tau ? fbar[i] : (sec[i] ? 1.f : 0.f);
+        sens[i] = (1.f - w) * sb + w * simf;
+    }
+}
+
+} // namespace
+
+void launch_rotate(const RotateArgs &a, cudaStream_t s)
+{
+    dim3 grid(blocks_for(a.max_box, kThreads, 4096), a.n_orient);
+    rotate_kernel<<<grid, kThreads, 0, s>>>(a);
+}
+
+void launch_scatter_tool(float *dst, int Px, int Py, int Pz, const uint32_t *off, int n, int kx, int ky, int kz,
+                         cudaStream_t s)
+{
+    scatter_tool_kernel<<<blocks_for(n), kThreads, 0, s>>>(dst, Px, Py, Pz, off, n, kx, ky, kz);
+}
+
+void launch_recheck(const RecheckArgs &a, cudaStream_t s)
+{
+    recheck_kernel<<<152 * 8, kThreads, 0, s>>>(a);
+}
+
+void launch_sweep(const SweepArgs &a, cudaStream_t s)
+{
+    sweep_kernel<<<blocks_for((long)a.awords * a.ny * a.nz), kThreads, 0, s>>>(a);
+}
+
+void launch_erode(const ErodeArgs &a, cudaStream_t s)
+{
+    erode_kernel<<<blocks_for((long)a.nx * a.ny * a.nz), kThreads, 0, s>>>(a);
+}
+
+void launch_fill_f32(float *p, float v, long n, cudaStream_t s)
+{
+    fill_f32_kernel<<<blocks_for(n), kThreads, 0, s>>>(p, v, n);
+}
+
+void launch_max_omega0(const float *f, const uint8_t *fix, long n, unsigned *maxbits, cudaStream_t s)
+{
+    max_omega0_kernel<<<blocks_for(n, kThreads, 152 * 4), kThreads, 0, s>>>(f, fix, n, maxbits, 0);
+}
+
+void launch_absmax_omega0(const float *v, const uint8_t *fix, long n, unsigned *maxbits, cudaStream_t s)
+{
+    max_omega0_kernel<<<blocks_for(n, kThreads, 152 * 4), kThreads, 0, s>>>(v, fix, n, maxbits, 1);
+}
+
+void launch_finalize(const FinalizeArgs &a, cudaStream_t s)
+{
+    finalize_kernel<<<blocks_for((long)a.nx * a.ny * a.nz), kThreads, 0, s>>>(a);
+}
+
+void launch_penalize(float *sens, const float *rho, const float *fbar, const uint8_t *sec, long n,
+                     const unsigned *maxbits, double w, double tau, cudaStream_t s)
+{
+    penalize_kernel<<<blocks_for(n), kThreads, 0, s>>>(sens, rho, fbar, sec, n, maxbits, (float)w, (float)tau);
+}
+
+} // namespace imf

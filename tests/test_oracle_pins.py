@@ -402,3 +402,12 @@ def test_translation_box_covers_every_query():
     tlo, text = translation_box((5, 6, 7), RK)
     assert list(tlo) == [-2, -4, -1]
     assert list(text) == [7 + 3 + 2 - 1 + 1, 6 + 4 + 1, 5 + 1 + 0]
+
+
+def test_subblock_equals_slice_of_full_grid():
+    d = synth.config_planar64(seed=4)
+    full = oracle.imf(d)
+    f, A = oracle.imf_subblock(d, (7, 13, 0), (33, 29, 1))
+    assert np.array_equal(f, full["f"][:, 13:42, 7:40])
+    acc = (full["f"][:, 13:42, 7:40] <= 0.01 * 126)
+    assert np.array_equal(A.astype(bool), acc)
