@@ -131,6 +131,26 @@ imf_status imf_penalize_sensitivity(imf_handle h, float *sens, const float *rho_
                                     const float *imf_bar, const uint8_t *secluded,
                                     const uint8_t *fixture, double w_acc, void *cuda_stream);
 
+/*
+ * Same filtered sensitivity as imf_penalize_sensitivity, for callers that cannot allocate
+ * device memory (a host framework that owns all device memory through its own pool, or code
+ * that must not stall the device, which cudaMalloc / cudaFree can do). The paper has no
+ * counterpart: this is a deployment variant of the step above.
+ *   Allocates nothing and needs no handle. Its reduction scratch is a fixed array of
+ *   65,600 floats (256 KiB) inside the library, held by every GPU that loads the library
+ *   until the process exits; it limits n to 268,435,456 voxels.
+ *   sens, rho_omega, imf_bar, secluded, fixture (or NULL): DEVICE arrays of n elements, as in
+ *   imf_penalize_sensitivity; tau is the density threshold (0.5 in the paper).
+ *   The first call on a device looks up the scratch address on that device (the device that
+ *   is current); make that first call before any stream capture.
+ *   Every call shares the scratch array: calls that overlap on the GPU (other streams or
+ *   other host threads) race and must not be issued. Asynchronous on cuda_stream.
+ * Errors: IMF_ERR_INVALID_ARG (NULL array, n < 1 or n above the limit, w_acc outside [0, 1),
+ * tau outside [0, 1]), IMF_ERR_CUDA. */
+imf_status imf_penalize_sensitivity_noalloc(float *sens, const float *rho_omega, const float *imf_bar,
+                                            const uint8_t *secluded, const uint8_t *fixture, long n,
+                                            double w_acc, double tau, void *cuda_stream);
+
 /* Wait for the last stream used by the handle and return the device-side status
  * (IMF_OK, IMF_ERR_OVERFLOW, IMF_ERR_TIMEOUT) or IMF_ERR_CUDA; clears it. */
 imf_status imf_sync_status(imf_handle h);

@@ -22,7 +22,8 @@ IMF_AUTO, IMF_FP32_FFT, IMF_BF16_DIRECT = 0, 1, 2
 EXPORTS = ["imf_default_options", "imf_create", "imf_set_tool", "imf_compute", "imf_compute_host",
            "imf_penalize_sensitivity", "imf_sync_status", "imf_last_error", "imf_destroy",
            "imf_get_tool_info", "imf_get_offsets", "imf_set_debug", "imf_get_last_g", "imf_get_stats",
-           "imf_set_profiling", "imf_get_kernel_time", "imf_reset_kernel_times"]
+           "imf_set_profiling", "imf_get_kernel_time", "imf_reset_kernel_times",
+           "imf_penalize_sensitivity_noalloc"]
 
 
 class ImfOptions(ctypes.Structure):
@@ -80,6 +81,7 @@ def load(path: str | None = None):
     L.imf_get_kernel_time.argtypes = [H, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(D),
                                       ctypes.POINTER(Lg)]
     L.imf_reset_kernel_times.argtypes = [H]
+    L.imf_penalize_sensitivity_noalloc.argtypes = [P, P, P, P, P, Lg, D, D, P]
     for name in EXPORTS:
         if name not in ("imf_default_options", "imf_destroy", "imf_last_error"):
             getattr(L, name).restype = ctypes.c_int
