@@ -1,0 +1,144 @@
+// Minimum over sharp points, tiled (Eq. eq_imf_2; Alg. 1 "Translate" + "min" over Support(K)).
+//
+//   gamma_R(x) = min_{k in sharp_R} g_R(x - k),   f(x) <- min(f(x), gamma_R(x))
+//
+// App. B forms a 4D array of shifted copies of g and reduces it; here the shifted copies are
+// never formed. The sharp points of an orientation are split into runs along x (fixed dy,
+// dz, consecutive dx); a block stages the g tile its outputs need in shared memory and every
+// thread keeps 8 consecutive x outputs in registers, so one run costs 8 + L - 1 shared loads
+// and about L/2 three-input minima per output. Runs are grouped in dz-chunks whose tile fits
+// the shared-memory budget; the run descriptors of a chunk are staged next to the tile. The
+// row pitch is odd and the plane pitch is chosen so that the 32 lanes of a warp (8 rows x 4
+// planes) read 32 different banks.
+#include <cfloat>
+
+#include "imf_internal.cuh"
+
+namespace imf {
+
+namespace {
+
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+template <int L> __device__ __forceinline__ void run_min(const float *__restrict__ s, float *acc)
+{
+    float w[kErXT + L - 1];
+#pragma unroll
+    for (int i = 0; i < kErXT + L - 1; ++i) w[i] = s[i];
+#pragma unroll
+    for (int j = 0; j < kErXT; ++j) {
+        float m = acc[j];
+#pragma unroll
+        for (int t = 0; t < L; t += 2) {
+            if (t + 1 < L) m = fmin3(m, w[j + t], w[j + t + 1]);
+            else m = fminf(m, w[j + t]);
+        }
+        acc[j] = m;
+    }
+}
+
+template <int L> __device__ __forceinline__ void run_group(const int2 *sruns, int q0, int q1, const float *tb, float *acc)
+{
+    for (int q = q0; q < q1; ++q) run_min<L>(tb + sruns[q].x, acc);
+}
+
+__global__ void __launch_bounds__(kErThreads, 2) erode2_kernel(Erode2Args a)
+{
+    extern __shared__ float tile[];
+    __shared__ int2 sruns[kErMaxRunsPerChunk];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warp = tx (8) x tz_hi (2); lane = ty (8) x tz_lo (4)
+    const int ty = lane & 7, tz = ((warp >> 3) << 2) | (lane >> 3), tx = warp & 7;
+    const int X0 = blockIdx.x * kErTX, Y0 = blockIdx.y * kErTY, Z0 = blockIdx.z * kErTZ;
+    const int y = Y0 + ty, z = Z0 + tz;
+    float *frow = a.f + ((long)z * a.ny + y) * a.nx;
+    // the running minimum starts from f; outputs outside the grid start at 0 so that they
+    // never keep a warp busy
+    float acc[kErXT];
+#pragma unroll
+    for (int j = 0; j < kErXT; ++j) {
+        const int x = X0 + tx * kErXT + j;
+        acc[j] = (y < a.ny && z < a.nz && x < a.nx) ? frow[x] : 0.f;
+    }
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tile);
+    for (int ob = 0; ob < a.nb; ++ob) {
+        const int og = a.orient_base + ob;
+        const float *g = a.g + ob * a.g_so;
+        // gamma_R >= 0, so outputs whose minimum is already 0 are final: skip work when a whole
+        // warp (or the whole block) is done
+        bool done = true;
+#pragma unroll
+        for (int j = 0; j < kErXT; ++j) done = done && acc[j] <= 0.f;
+        if (__syncthreads_and(done)) continue;
+        const bool warp_done = __all_sync(0xffffffffu, done);
+        for (int c = a.chunk_start[og]; c < a.chunk_start[og + 1]; ++c) {
+            const ErodeChunk &ch = a.chunks[c];
+            const int gx0 = X0 + ch.ox, gy0 = Y0 + ch.oy, gz0 = Z0 + ch.oz;
+            const int txh = ch.txh, tyh = ch.tyh, nrow = tyh * ch.tzh;
+            const int pz = ch.pitch_z, py = ch.pitch_y;
+            const int run0 = ch.run0, nrun = ch.run1 - ch.run0;
+            __syncthreads();
+            // asynchronous fill, one warp per tile row; cells outside the window (read only by
+            // outputs beyond the grid, which are masked) are zero-filled
+            for (int r = warp; r < nrow; r += kErThreads / 32) {
+                const int iy = r % tyh, iz = r / tyh;
+                const int gy = gy0 + iy, gz = gz0 + iz;
+                const bool rowok = gy < a.wy && gz < a.wz;
+                const float *src = g + ((long)gz * a.gpy + gy) * a.gpx;
+                const uint32_t drow = sbase + 4u * (uint32_t)(iz * pz + iy * py);
+                for (int ix = lane; ix < txh; ix += 32) {
+                    const int gx = gx0 + ix;
+                    const bool ok = rowok && gx < a.wx;
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(drow + 4u * ix),
+                                 "l"(ok ? src + gx : g), "r"(ok ? 4 : 0));
+                }
+            }
+            for (int q = threadIdx.x; q < nrun; q += kErThreads) sruns[q] = a.runs[run0 + q];
+            asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+            __syncthreads();
+            if (warp_done) continue;
+            const float *tb = tile + tz * pz + ty * py + tx * kErXT;
+            const int *le = ch.lend;
+            run_group<1>(sruns, le[0], le[1], tb, acc);
+            run_group<2>(sruns, le[1], le[2], tb, acc);
+            run_group<3>(sruns, le[2], le[3], tb, acc);
+            run_group<4>(sruns, le[3], le[4], tb, acc);
+            run_group<5>(sruns, le[4], le[5], tb, acc);
+            run_group<6>(sruns, le[5], le[6], tb, acc);
+            run_group<7>(sruns, le[6], le[7], tb, acc);
+            run_group<8>(sruns, le[7], le[8], tb, acc);
+            run_group<9>(sruns, le[8], le[9], tb, acc);
+            run_group<10>(sruns, le[9], le[10], tb, acc);
+            run_group<11>(sruns, le[10], le[11], tb, acc);
+            run_group<12>(sruns, le[11], le[12], tb, acc);
+            run_group<13>(sruns, le[12], le[13], tb, acc);
+            run_group<14>(sruns, le[13], le[14], tb, acc);
+            run_group<15>(sruns, le[14], le[15], tb, acc);
+            run_group<16>(sruns, le[15], le[16], tb, acc);
+        }
+    }
+    if (y < a.ny && z < a.nz) {
+#pragma unroll
+        for (int j = 0; j < kErXT; ++j) {
+            const int x = X0 + tx * kErXT + j;
+            if (x < a.nx) frow[x] = acc[j];
+        }
+    }
+}
+
+} // namespace
+
+void launch_erode2(const Erode2Args &a, size_t smem, cudaStream_t s)
+{
+    // the static descriptor table counts against the default 48 KB, so always raise the limit
+    cudaFuncSetAttribute(erode2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((a.nx + kErTX - 1) / kErTX, (a.ny + kErTY - 1) / kErTY, (a.nz + kErTZ - 1) / kErTZ);
+    erode2_kernel<<<grid, kErThreads, smem, s>>>(a);
+}
+
+} // namespace imf

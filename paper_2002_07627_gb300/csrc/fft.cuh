@@ -141,26 +141,40 @@ template <int S, int R> FFT_HD void dft(float2 *v)
     else if constexpr (R == 8) dft8<S>(v);
 }
 
-// Radix plan of one axis length.
+// Radix plan of one axis length. For every stage s, Ns = rad[0] * ... * rad[s-1];
+// j / Ns = fast_div(j, mul[s]) exactly for 0 <= j < 2^20, and step[s] = L / (Ns rad[s]).
 struct FftPlan {
     int L;          // transform length
     int nrad;       // number of stages
     int rad[16];    // radix of each stage
+    unsigned mul[16];
+    int step[16];
 };
+
+// j / d for j < 2^20 and 2 <= d <= 4096 with mul = ceil(2^32 / d): j mul / 2^32 exceeds j / d
+// by less than j / 2^32 < 1 / d, which cannot carry past the next integer. mul = 0 means d = 1.
+FFT_HD unsigned fast_div(unsigned j, unsigned mul)
+{
+    if (mul == 0) return j;
+#ifdef __CUDA_ARCH__
+    return __umulhi(j, mul);
+#else
+    return (unsigned)(((unsigned long long)j * mul) >> 32);
+#endif
+}
 
 // One Stockham butterfly. Element (w, j) of the tile lives at w*sw + j*sj. `tw` holds
 // exp(-2 pi i m / L), m < L.
 template <int S, int R>
 FFT_HD void stockham_bfly(const float2 *src, float2 *dst, int w, int jb, int L, int Ns, int sw, int sj,
-                          const float2 *tw)
+                          const float2 *tw, int jdiv, int step)
 {
     const int NR = L / R;
-    const int k = jb % Ns;
+    const int k = jb - jdiv * Ns;
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[w * sw + (jb + r * NR) * sj];
     if (Ns > 1) {
-        const int step = L / (Ns * R);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
             float2 t = tw[k * r * step];
@@ -169,24 +183,30 @@ FFT_HD void stockham_bfly(const float2 *src, float2 *dst, int w, int jb, int L, 
         }
     }
     dft<S, R>(v);
-    const int base = (jb / Ns) * Ns * R + k;
+    const int base = jdiv * Ns * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[w * sw + (base + r * Ns) * sj] = v[r];
 }
 
+// jdiv = jb / Ns (passed in so the caller can use the plan's exact reciprocal)
 template <int S>
 FFT_HD void stockham_dispatch(int R, const float2 *src, float2 *dst, int w, int jb, int L, int Ns, int sw,
-                              int sj, const float2 *tw)
+                              int sj, const float2 *tw, int jdiv, int step)
 {
     switch (R) {
-    case 2: stockham_bfly<S, 2>(src, dst, w, jb, L, Ns, sw, sj, tw); break;
-    case 3: stockham_bfly<S, 3>(src, dst, w, jb, L, Ns, sw, sj, tw); break;
-    case 4: stockham_bfly<S, 4>(src, dst, w, jb, L, Ns, sw, sj, tw); break;
-    case 5: stockham_bfly<S, 5>(src, dst, w, jb, L, Ns, sw, sj, tw); break;
-    case 7: stockham_bfly<S, 7>(src, dst, w, jb, L, Ns, sw, sj, tw); break;
-    case 8: stockham_bfly<S, 8>(src, dst, w, jb, L, Ns, sw, sj, tw); break;
+    case 2: stockham_bfly<S, 2>(src, dst, w, jb, L, Ns, sw, sj, tw, jdiv, step); break;
+    case 3: stockham_bfly<S, 3>(src, dst, w, jb, L, Ns, sw, sj, tw, jdiv, step); break;
+    case 4: stockham_bfly<S, 4>(src, dst, w, jb, L, Ns, sw, sj, tw, jdiv, step); break;
+    case 5: stockham_bfly<S, 5>(src, dst, w, jb, L, Ns, sw, sj, tw, jdiv, step); break;
+    case 7: stockham_bfly<S, 7>(src, dst, w, jb, L, Ns, sw, sj, tw, jdiv, step); break;
+    case 8: stockham_bfly<S, 8>(src, dst, w, jb, L, Ns, sw, sj, tw, jdiv, step); break;
     default: break;
     }
+}
+
+inline unsigned div_magic(unsigned d)
+{
+    return d <= 1 ? 0u : (unsigned)(((1ull << 32) + d - 1) / d);
 }
 
 // Factor L into stages (largest radices first). Returns false if L has a prime factor > 7.
@@ -201,7 +221,14 @@ inline bool make_plan(int L, FftPlan *p)
     while (m % 4 == 0) { p->rad[p->nrad++] = 4; m /= 4; }
     while (m % 3 == 0) { p->rad[p->nrad++] = 3; m /= 3; }
     while (m % 2 == 0) { p->rad[p->nrad++] = 2; m /= 2; }
-    return m == 1 && p->nrad <= 16;
+    if (m != 1 || p->nrad > 16 || L > 4096) return false;
+    int Ns = 1;
+    for (int s = 0; s < p->nrad; ++s) {
+        p->mul[s] = div_magic((unsigned)Ns);
+        p->step[s] = L / (Ns * p->rad[s]);
+        Ns *= p->rad[s];
+    }
+    return true;
 }
 
 // Host emulation of a whole 1D transform on one pencil (tests only): ping-pongs between
@@ -212,7 +239,8 @@ template <int S> inline float2 *fft_pencil_host(const FftPlan &p, float2 *a, flo
     float2 *src = a, *dst = b;
     for (int s = 0; s < p.nrad; ++s) {
         int R = p.rad[s];
-        for (int jb = 0; jb < p.L / R; ++jb) stockham_dispatch<S>(R, src, dst, 0, jb, p.L, Ns, 0, 1, tw);
+        for (int jb = 0; jb < p.L / R; ++jb)
+            stockham_dispatch<S>(R, src, dst, 0, jb, p.L, Ns, 0, 1, tw, (int)fast_div((unsigned)jb, p.mul[s]), p.step[s]);
         float2 *t = src; src = dst; dst = t;
         Ns *= R;
     }

@@ -15,21 +15,23 @@ namespace imf {
 
 namespace {
 
-template <int S>
-__device__ void run_stages(const FftPlan &plan, float2 *&src, float2 *&dst, int ntile, int sw, int sj,
-                           bool interleaved, const float2 *tw)
+// Stockham stages over a tile of W interleaved pencils (element (w, j) at w + j * sj);
+// W is a power of two so q -> (w, jb) is a mask and a shift, and jb / Ns uses the plan's
+// exact reciprocal.
+template <int S, int LOGW>
+__device__ void run_stages(const FftPlan &plan, float2 *&src, float2 *&dst, int sj, const float2 *tw)
 {
+    constexpr int W = 1 << LOGW;
     const int L = plan.L;
     int Ns = 1;
     for (int s = 0; s < plan.nrad; ++s) {
         const int R = plan.rad[s];
-        const int per = L / R;
-        const int nb = per * ntile;
+        const int nb = (L / R) << LOGW;
+        const unsigned mul = plan.mul[s];
+        const int step = plan.step[s];
         for (int q = threadIdx.x; q < nb; q += blockDim.x) {
-            int w, jb;
-            if (interleaved) { w = q % ntile; jb = q / ntile; }
-            else { jb = q % per; w = q / per; }
-            stockham_dispatch<S>(R, src, dst, w, jb, L, Ns, sw, sj, tw);
+            const int w = q & (W - 1), jb = q >> LOGW;
+            stockham_dispatch<S>(R, src, dst, w, jb, L, Ns, 1, sj, tw, (int)fast_div((unsigned)jb, mul), step);
         }
         __syncthreads();
         float2 *t = src; src = dst; dst = t;
@@ -50,18 +52,31 @@ __global__ void __launch_bounds__(kThreads) axis_fft_kernel(AxisArgs a)
     const long b = blockIdx.y, o = blockIdx.z;
     const float2 *in = a.in + o * a.in_so + b * a.in_sb + kx0;
     const float2 *mul = a.mul ? a.mul + o * a.mul_so + b * a.mul_sb + kx0 : nullptr;
-    for (int idx = threadIdx.x; idx < kAxisW * L; idx += blockDim.x) {
-        const int w = idx % kAxisW, j = idx / kAxisW;
-        float2 v = make_float2(0.f, 0.f);
-        if (j < a.lin && kx0 + w < a.nx) {
-            v = in[(long)j * a.in_sl + w];
-            if (mul) v = c_mul(v, mul[(long)j * a.mul_sl + w]);
+    // loads are issued in groups of 8 per thread before any shared store (memory-level
+    // parallelism); the optional pointwise factor is applied on the way in
+    const int total = kAxisW * L;
+    for (int base = 0; base < total; base += 8 * kThreads) {
+        float2 v[8], m[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * kThreads + threadIdx.x;
+            const int w = idx % kAxisW, j = idx / kAxisW;
+            v[u] = make_float2(0.f, 0.f);
+            m[u] = make_float2(1.f, 0.f);
+            if (idx < total && j < a.lin && kx0 + w < a.nx) {
+                v[u] = in[(long)j * a.in_sl + w];
+                if (mul) m[u] = mul[(long)j * a.mul_sl + w];
+            }
         }
-        buf0[j * kAxisW + w] = v;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * kThreads + threadIdx.x;
+            if (idx < total) buf0[idx] = mul ? c_mul(v[u], m[u]) : v[u];
+        }
     }
     __syncthreads();
     float2 *src = buf0, *dst = buf1;
-    run_stages<S>(a.plan, src, dst, kAxisW, 1, kAxisW, true, tw);
+    run_stages<S, 4>(a.plan, src, dst, kAxisW, tw);
     float2 *out = a.out + o * a.out_so + b * a.out_sb + kx0;
     for (int idx = threadIdx.x; idx < kAxisW * a.lout; idx += blockDim.x) {
         const int w = idx % kAxisW, jj = idx / kAxisW;
@@ -73,43 +88,56 @@ __global__ void __launch_bounds__(kThreads) axis_fft_kernel(AxisArgs a)
     }
 }
 
-__global__ void __launch_bounds__(kThreads) rfft_fwd_kernel(RfftArgs a, int W)
+// x-pass tiles hold W rows interleaved: element (row w, sample j) at j * (W + 1) + w, so the
+// Stockham stages and the row loads / stores touch consecutive or odd-strided banks.
+template <int LOGW> __global__ void __launch_bounds__(kThreads) rfft_fwd_kernel(RfftArgs a)
 {
+    constexpr int W = 1 << LOGW;
     extern __shared__ float2 sm[];
-    const int M = a.M, ld = M + 1;
-    float2 *buf0 = sm, *buf1 = sm + W * ld, *twM = sm + 2 * W * ld, *twP = twM + M;
+    const int M = a.M, ld = W + 1;
+    float2 *buf0 = sm, *buf1 = sm + (M + 1) * ld, *twM = sm + 2 * (M + 1) * ld, *twP = twM + M;
     for (int i = threadIdx.x; i < M; i += blockDim.x) twM[i] = a.twM[i];
     for (int i = threadIdx.x; i <= M; i += blockDim.x) twP[i] = a.twP[i];
     const int r0 = blockIdx.x * W;
-    for (int idx = threadIdx.x; idx < W * M; idx += blockDim.x) {
-        const int w = idx / M, n = idx % M, r = r0 + w;
-        float2 v = make_float2(0.f, 0.f);
-        if (r < a.rows) {
-            const int y = r % a.rows_y, z = r / a.rows_y;
-            const long base = z * a.src_sz + y * a.src_sy;
-            const int x0 = 2 * n, x1 = 2 * n + 1;
-            if (x0 < a.nin) {
-                float e = a.src[base + x0];
-                if (a.fix) e = fminf(1.f, e + (a.fix[base + x0] ? 1.f : 0.f));
-                v.x = e;
-            }
-            if (x1 < a.nin) {
-                float e = a.src[base + x1];
-                if (a.fix) e = fminf(1.f, e + (a.fix[base + x1] ? 1.f : 0.f));
-                v.y = e;
+    const int total = W * M;
+    for (int base = 0; base < total; base += 4 * kThreads) {
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = base + u * kThreads + threadIdx.x;
+            const int w = idx / M, n = idx % M, r = r0 + w;
+            v[u] = make_float2(0.f, 0.f);
+            if (idx < total && r < a.rows) {
+                const int y = r % a.rows_y, z = r / a.rows_y;
+                const long rb = z * a.src_sz + y * a.src_sy;
+                const int x0 = 2 * n, x1 = 2 * n + 1;
+                if (x0 < a.nin) {
+                    float e = a.src[rb + x0];
+                    if (a.fix) e = fminf(1.f, e + (a.fix[rb + x0] ? 1.f : 0.f));
+                    v[u].x = e;
+                }
+                if (x1 < a.nin) {
+                    float e = a.src[rb + x1];
+                    if (a.fix) e = fminf(1.f, e + (a.fix[rb + x1] ? 1.f : 0.f));
+                    v[u].y = e;
+                }
             }
         }
-        buf0[w * ld + n] = v;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = base + u * kThreads + threadIdx.x;
+            if (idx < total) buf0[(idx % M) * ld + idx / M] = v[u];
+        }
     }
     __syncthreads();
     float2 *src = buf0, *dst = buf1;
-    run_stages<-1>(a.plan, src, dst, W, ld, 1, false, twM);
+    run_stages<-1, LOGW>(a.plan, src, dst, ld, twM);
     // unpack: X[k] = (Z[k] + conj Z[M-k]) / 2 + exp(-2 pi i k / P) (Z[k] - conj Z[M-k]) / (2 i)
     for (int idx = threadIdx.x; idx < W * (M + 1); idx += blockDim.x) {
         const int w = idx / (M + 1), k = idx % (M + 1), r = r0 + w;
         if (r >= a.rows) continue;
-        const float2 zk = src[w * ld + (k == M ? 0 : k)];
-        const float2 zc = c_conj(src[w * ld + (k == 0 ? 0 : M - k)]);
+        const float2 zk = src[(k == M ? 0 : k) * ld + w];
+        const float2 zc = c_conj(src[(k == 0 ? 0 : M - k) * ld + w]);
         const float2 e = c_scale(c_add(zk, zc), 0.5f);
         const float2 od = c_mul_si<-1>(c_scale(c_sub(zk, zc), 0.5f));
         const float2 X = c_add(e, c_mul(twP[k], od));
@@ -118,38 +146,49 @@ __global__ void __launch_bounds__(kThreads) rfft_fwd_kernel(RfftArgs a, int W)
     }
 }
 
-__global__ void __launch_bounds__(kThreads) irfft_threshold_kernel(IrfftArgs a, int W)
+template <int LOGW> __global__ void __launch_bounds__(kThreads) irfft_threshold_kernel(IrfftArgs a)
 {
+    constexpr int W = 1 << LOGW;
     extern __shared__ float2 sm[];
-    const int M = a.M, ld = M + 1;
-    float2 *buf0 = sm, *buf1 = sm + W * ld, *twM = sm + 2 * W * ld, *twP = twM + M;
+    const int M = a.M, ld = W + 1;
+    float2 *buf0 = sm, *buf1 = sm + (M + 1) * ld, *twM = sm + 2 * (M + 1) * ld, *twP = twM + M;
     for (int i = threadIdx.x; i < M; i += blockDim.x) twM[i] = a.twM[i];
     for (int i = threadIdx.x; i <= M; i += blockDim.x) twP[i] = a.twP[i];
     const int r0 = blockIdx.x * W;
     const long o = blockIdx.z;
     const float2 *in = a.in + o * a.in_so;
-    for (int idx = threadIdx.x; idx < W * (M + 1); idx += blockDim.x) {
-        const int w = idx / (M + 1), k = idx % (M + 1), r = r0 + w;
-        float2 v = make_float2(0.f, 0.f);
-        if (r < a.rows) {
-            const int y = r % a.rows_y, z = r / a.rows_y;
-            v = in[z * a.in_sz + y * a.in_sy + k];
+    const int total = W * (M + 1);
+    for (int base = 0; base < total; base += 8 * kThreads) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * kThreads + threadIdx.x;
+            const int w = idx / (M + 1), k = idx % (M + 1), r = r0 + w;
+            v[u] = make_float2(0.f, 0.f);
+            if (idx < total && r < a.rows) {
+                const int y = r % a.rows_y, z = r / a.rows_y;
+                v[u] = in[z * a.in_sz + y * a.in_sy + k];
+            }
         }
-        buf1[w * ld + k] = v;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * kThreads + threadIdx.x;
+            if (idx < total) buf1[(idx % (M + 1)) * ld + idx / (M + 1)] = v[u];
+        }
     }
     __syncthreads();
     // pack: Z[k] = (X[k] + conj X[M-k]) + i exp(+2 pi i k / P) (X[k] - conj X[M-k]), k < M
     for (int idx = threadIdx.x; idx < W * M; idx += blockDim.x) {
-        const int w = idx / M, k = idx % M;
-        const float2 xk = buf1[w * ld + k];
-        const float2 xc = c_conj(buf1[w * ld + M - k]);
+        const int w = idx % W, k = idx / W;
+        const float2 xk = buf1[k * ld + w];
+        const float2 xc = c_conj(buf1[(M - k) * ld + w]);
         const float2 e = c_add(xk, xc);
         const float2 od = c_mul(c_conj(twP[k]), c_sub(xk, xc));
-        buf0[w * ld + k] = c_add(e, c_mul_si<1>(od));
+        buf0[k * ld + w] = c_add(e, c_mul_si<1>(od));
     }
     __syncthreads();
     float2 *src = buf0, *dst = buf1;
-    run_stages<1>(a.plan, src, dst, W, ld, 1, false, twM);
+    run_stages<1, LOGW>(a.plan, src, dst, ld, twM);
     // g[i] = Re z[i/2] (i even) or Im z[i/2] (i odd), clamped at 0 (g >= 0 exactly)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int nwords = (a.nout + 31) >> 5;
@@ -163,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) irfft_threshold_kernel(IrfftArgs a, 
         const bool valid = i < a.nout;
         float gv = 0.f;
         if (valid) {
-            const float2 zz = src[w * ld + (i >> 1)];
+            const float2 zz = src[(i >> 1) * ld + w];
             gv = fmaxf((i & 1) ? zz.y : zz.x, 0.f);
             g[z * a.g_sz + y * a.g_sy + i] = gv;
         }
@@ -198,13 +237,15 @@ template <typename K> void set_smem(K kernel, size_t bytes)
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-int x_rows_per_block(int M)
+// rows per x-pass block: 32 while the two staging buffers stay near 100 KB, else 16 or 8
+int x_log_rows(int M)
 {
-    int W = 4096 / (M + 1);
-    if (W < 1) W = 1;
-    if (W > 32) W = 32;
-    return W;
+    if ((size_t)(M + 1) * 33 * 16 <= 100 * 1024) return 5;
+    if ((size_t)(M + 1) * 17 * 16 <= 100 * 1024) return 4;
+    return 3;
 }
+
+size_t x_smem(int M, int W) { return (size_t)(2 * (M + 1) * (W + 1) + 2 * M + 1) * sizeof(float2); }
 
 } // namespace
 
@@ -223,20 +264,22 @@ void launch_axis_fft(int sign, const AxisArgs &a, int nbatch, int norient, cudaS
 
 void launch_rfft_fwd(const RfftArgs &a, cudaStream_t s)
 {
-    const int W = x_rows_per_block(a.M);
-    const size_t smem = (size_t)(2 * W * (a.M + 1) + 2 * a.M + 1) * sizeof(float2);
-    set_smem(rfft_fwd_kernel, smem);
+    const int lw = x_log_rows(a.M), W = 1 << lw;
+    const size_t smem = x_smem(a.M, W);
     dim3 grid((a.rows + W - 1) / W);
-    rfft_fwd_kernel<<<grid, kThreads, smem, s>>>(a, W);
+    if (lw == 5) { set_smem(rfft_fwd_kernel<5>, smem); rfft_fwd_kernel<5><<<grid, kThreads, smem, s>>>(a); }
+    else if (lw == 4) { set_smem(rfft_fwd_kernel<4>, smem); rfft_fwd_kernel<4><<<grid, kThreads, smem, s>>>(a); }
+    else { set_smem(rfft_fwd_kernel<3>, smem); rfft_fwd_kernel<3><<<grid, kThreads, smem, s>>>(a); }
 }
 
 void launch_irfft_threshold(const IrfftArgs &a, int norient, cudaStream_t s)
 {
-    const int W = x_rows_per_block(a.M);
-    const size_t smem = (size_t)(2 * W * (a.M + 1) + 2 * a.M + 1) * sizeof(float2);
-    set_smem(irfft_threshold_kernel, smem);
+    const int lw = x_log_rows(a.M), W = 1 << lw;
+    const size_t smem = x_smem(a.M, W);
     dim3 grid((a.rows + W - 1) / W, 1, norient);
-    irfft_threshold_kernel<<<grid, kThreads, smem, s>>>(a, W);
+    if (lw == 5) { set_smem(irfft_threshold_kernel<5>, smem); irfft_threshold_kernel<5><<<grid, kThreads, smem, s>>>(a); }
+    else if (lw == 4) { set_smem(irfft_threshold_kernel<4>, smem); irfft_threshold_kernel<4><<<grid, kThreads, smem, s>>>(a); }
+    else { set_smem(irfft_threshold_kernel<3>, smem); irfft_threshold_kernel<3><<<grid, kThreads, smem, s>>>(a); }
 }
 
 } // namespace imf

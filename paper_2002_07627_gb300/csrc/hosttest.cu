@@ -23,3 +23,16 @@ extern "C" int imf_host_fft(int L, int sign, const float *in, float *out)
     }
     return p.nrad;
 }
+
+// Number of (d, j) pairs, 2 <= d <= maxd, 0 <= j < maxj, where the stage reciprocal disagrees
+// with integer division.
+extern "C" long imf_host_check_div(int maxd, int maxj)
+{
+    long bad = 0;
+    for (int d = 1; d <= maxd; ++d) {
+        const unsigned mul = imf::div_magic((unsigned)d);
+        for (int j = 0; j < maxj; ++j)
+            if (imf::fast_div((unsigned)j, mul) != (unsigned)(j / d)) ++bad;
+    }
+    return bad;
+}

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <map>
 #include <unordered_map>
 #include <cstdio>
 #include <cstring>
@@ -55,6 +56,10 @@ struct Tool {
     int *iv_start = nullptr;
     int *sh_lin = nullptr;
     int *sh_start = nullptr;
+    ErodeChunk *er_chunks = nullptr;
+    int *er_chunk_start = nullptr;
+    int2 *er_runs = nullptr;
+    size_t erode_smem = 0;
     long n_rt = 0, n_rk = 0, n_sh = 0;
 };
 
@@ -297,7 +302,89 @@ void free_tool(imf_handle h, Tool &t)
     dfree(h, t.iv_start, (size_t)t.n_orient + 1);
     dfree(h, t.sh_lin, (size_t)t.n_sh);
     dfree(h, t.sh_start, (size_t)t.n_orient + 1);
+    dfree(h, t.er_chunks);
+    dfree(h, t.er_chunk_start);
+    dfree(h, t.er_runs);
     t = Tool();
+}
+
+// Runs along x of the sharp points of one orientation, grouped in dz-chunks whose g tile fits
+// `budget` bytes of shared memory (see erode.cu for the tile layout).
+constexpr size_t kErodeBudget = 104 * 1024;
+
+bool bank_free(int P, int Q)
+{
+    bool seen[32] = {false};
+    for (int tz = 0; tz < 4; ++tz)
+        for (int ty = 0; ty < 8; ++ty) {
+            const int b = ((tz * Q + ty * P) % 32 + 32) % 32;
+            if (seen[b]) return false;
+            seen[b] = true;
+        }
+    return true;
+}
+
+void plan_erode(const std::vector<int32_t> &sh, const int K[3], std::vector<ErodeChunk> &chunks,
+                std::vector<int2> &runs, size_t &smem_max)
+{
+    if (sh.empty()) return;
+    int kmn[3] = {1 << 30, 1 << 30, 1 << 30}, kmx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+    std::map<std::pair<int, int>, std::vector<int>> rows;   // (dz, dy) -> dx
+    for (size_t m = 0; m < sh.size(); m += 3) {
+        for (int c = 0; c < 3; ++c) { kmn[c] = std::min(kmn[c], sh[m + c]); kmx[c] = std::max(kmx[c], sh[m + c]); }
+        rows[{sh[m + 2], sh[m + 1]}].push_back(sh[m]);
+    }
+    struct Run { int dz, dy, a, L; };
+    std::vector<Run> rr;
+    for (auto &kv : rows) {
+        auto &v = kv.second;
+        std::sort(v.begin(), v.end());
+        size_t i = 0;
+        while (i < v.size()) {
+            size_t j = i;
+            while (j + 1 < v.size() && v[j + 1] == v[j] + 1) ++j;
+            for (int a0 = v[i]; a0 <= v[j]; a0 += kErMaxL)
+                rr.push_back({kv.first.first, kv.first.second, a0, std::min(kErMaxL, v[j] - a0 + 1)});
+            i = j + 1;
+        }
+    }
+    const int Ex = kmx[0] - kmn[0] + 1, Ey = kmx[1] - kmn[1] + 1;
+    const int txh = kErTX + Ex - 1, tyh = kErTY + Ey - 1;
+    const int P = txh | 1;
+    int Q = tyh * P;
+    while (!bank_free(P, Q)) ++Q;
+    int planes = (int)(kErodeBudget / (4 * (size_t)Q));
+    int dzc = planes - kErTZ + 1;
+    if (dzc < 1) dzc = 1;
+    for (int hi = kmx[2]; hi >= kmn[2]; hi -= dzc) {
+        const int lo = std::max(kmn[2], hi - dzc + 1);
+        std::vector<int2> cr;
+        for (const Run &r : rr) {
+            if (r.dz < lo || r.dz > hi) continue;
+            const int off = (hi - r.dz) * Q + (kmx[1] - r.dy) * P + (kmx[0] - (r.a + r.L - 1));
+            cr.push_back(make_int2(off, r.L));
+        }
+        if (cr.empty()) continue;
+        std::stable_sort(cr.begin(), cr.end(), [](const int2 &x, const int2 &y) { return x.y < y.y; });
+        for (size_t b = 0; b < cr.size(); b += kErMaxRunsPerChunk) {
+            const size_t e = std::min(cr.size(), b + (size_t)kErMaxRunsPerChunk);
+            ErodeChunk ch{};
+            ch.run0 = (int)runs.size();
+            for (size_t i = b; i < e; ++i) runs.push_back(cr[i]);
+            ch.run1 = (int)runs.size();
+            ch.lend[0] = 0;
+            for (int L = 1; L <= kErMaxL; ++L) {
+                int c = ch.lend[L - 1];
+                while (ch.run0 + c < ch.run1 && runs[ch.run0 + c].y == L) ++c;
+                ch.lend[L] = c;
+            }
+            ch.txh = txh; ch.tyh = tyh; ch.tzh = kErTZ + (hi - lo);
+            ch.pitch_y = P; ch.pitch_z = Q;
+            ch.ox = K[0] - kmx[0]; ch.oy = K[1] - kmx[1]; ch.oz = K[2] - hi;
+            chunks.push_back(ch);
+        }
+        smem_max = std::max(smem_max, (size_t)(kErTZ + (hi - lo)) * Q * sizeof(float));
+    }
 }
 
 imf_status ensure_work(imf_handle h)
@@ -573,7 +660,8 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
                         for (int c = 0; c < 3; ++c) { t.kmin[c] = std::min(t.kmin[c], v[c]); t.kmax[c] = std::max(t.kmax[c], v[c]); }
                         if (run < 0) run = x;
                     } else if (run >= 0) {
-                        ivs[i].insert(ivs[i].end(), {b[0] + run, b[0] + x - 1, b[1] + y, b[2] + z});
+                        for (int r0 = run; r0 <= x - 1; r0 += 32)   // sweep runs of at most 32
+                            ivs[i].insert(ivs[i].end(), {b[0] + r0, b[0] + std::min(x - 1, r0 + 31), b[1] + y, b[2] + z});
                         run = -1;
                     }
                     if (x < b[3] && bS[id]) t.sh[i].insert(t.sh[i].end(), v, v + 3);
@@ -638,6 +726,14 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
     t.n_rk = 0;
     for (auto &v : t.rk) t.n_rk += (long)v.size() / 3;
     t.n_sh = (long)shl.size();
+    std::vector<ErodeChunk> chunks;
+    std::vector<int2> eruns;
+    std::vector<int> chst(n_orient + 1, 0);
+    t.erode_smem = 0;
+    for (int i = 0; i < n_orient; ++i) {
+        plan_erode(t.sh[i], t.kmax, chunks, eruns, t.erode_smem);
+        chst[i + 1] = (int)chunks.size();
+    }
     st = IMF_OK;
     auto bail = [&](imf_status s2) { free_tool(h, t); return s2; };
     twiddles(t.M, t.M, t.M, tw);
@@ -649,7 +745,9 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
     twiddles(t.P[2], t.P[2], t.P[2], tw);
     if ((st = upload(h, &t.twz, tw))) return bail(st);
     if ((st = upload(h, &t.rt_off, rto)) || (st = upload(h, &t.rt_start, rts)) || (st = upload(h, &t.iv, ivv)) ||
-        (st = upload(h, &t.iv_start, ivst)) || (st = upload(h, &t.sh_lin, shl)) || (st = upload(h, &t.sh_start, shs)))
+        (st = upload(h, &t.iv_start, ivst)) || (st = upload(h, &t.sh_lin, shl)) || (st = upload(h, &t.sh_start, shs)) ||
+        (st = upload(h, &t.er_chunks, chunks)) || (st = upload(h, &t.er_chunk_start, chst)) ||
+        (st = upload(h, &t.er_runs, eruns)))
         return bail(st);
     // --- tool spectra: conj(FFT(1_RT)) / Ptot (reflection as conjugation, Alg. 1 footnote)
     const size_t per = (size_t)t.P[2] * t.P[1] * t.Hs;
@@ -747,7 +845,7 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
                 a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
                 a.theta = t.theta; a.orient_base = o0;
                 Launch L(h, KID_RECHECK, s);
-                launch_recheck(a, s);
+                launch_recheck_blocks(a, 152 * 8, s);
             }
             {
                 SweepArgs a{};
@@ -755,15 +853,16 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
                 a.iv = t.iv; a.iv_start = t.iv_start; a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.awords = h->awords;
                 a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2]; a.orient_base = o0; a.nb = nb; a.A = h->A;
                 Launch L(h, KID_SWEEP, s);
-                launch_sweep(a, s);
+                launch_sweep2(a, s);
             }
             {
-                ErodeArgs a{};
-                a.g = h->g; a.g_so = gso; a.gpx = t.gpx; a.gpy = t.win[1]; a.sh_lin = t.sh_lin; a.sh_start = t.sh_start;
-                a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2];
-                a.orient_base = o0; a.nb = nb; a.f = h->f;
+                Erode2Args a{};
+                a.g = h->g; a.g_so = gso; a.gpx = t.gpx; a.gpy = t.win[1];
+                a.wx = t.win[0]; a.wy = t.win[1]; a.wz = t.win[2];
+                a.chunks = t.er_chunks; a.chunk_start = t.er_chunk_start; a.runs = t.er_runs;
+                a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.orient_base = o0; a.nb = nb; a.f = h->f;
                 Launch L(h, KID_ERODE, s);
-                launch_erode(a, s);
+                launch_erode2(a, t.erode_smem, s);
             }
             h->last_batch_base = o0;
             h->last_batch_n = nb;

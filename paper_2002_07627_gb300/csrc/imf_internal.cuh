@@ -118,6 +118,7 @@ struct RecheckArgs {
     int orient_base;
 };
 void launch_recheck(const RecheckArgs &a, cudaStream_t s);
+void launch_recheck_blocks(const RecheckArgs &a, int max_points, cudaStream_t s);
 
 struct SweepArgs {
     const uint32_t *bits;
@@ -130,6 +131,7 @@ struct SweepArgs {
     uint32_t *A;                 // accessible bits [nz][ny][awords], OR-accumulated
 };
 void launch_sweep(const SweepArgs &a, cudaStream_t s);
+void launch_sweep2(const SweepArgs &a, cudaStream_t s);
 
 struct ErodeArgs {
     const float *g;
@@ -143,6 +145,32 @@ struct ErodeArgs {
     float *f;                    // running minimum over orientations and tools
 };
 void launch_erode(const ErodeArgs &a, cudaStream_t s);
+
+// Tiled minimum over sharp points. A block owns kErTX x kErTY x kErTZ outputs (16 consecutive
+// x per thread); the sharp points of an orientation are runs along x, grouped in dz-chunks
+// whose g tile fits the shared-memory budget.
+constexpr int kErTX = 64, kErTY = 8, kErTZ = 8, kErXT = 8, kErMaxL = 16, kErThreads = 512;
+constexpr int kErMaxRunsPerChunk = 1024;
+struct ErodeChunk {
+    int run0, run1;              // runs of this chunk, sorted by length
+    int lend[kErMaxL + 1];       // runs of length L are run0 + lend[L-1] .. run0 + lend[L] - 1
+    int txh, tyh, tzh;           // tile extents
+    int pitch_y, pitch_z;        // shared-memory row and plane pitch (floats)
+    int ox, oy, oz;              // tile origin = block output origin + (ox, oy, oz) in window index
+};
+struct Erode2Args {
+    const float *g;
+    long g_so;
+    int gpx, gpy;                // window pitch (x) and rows per z-plane
+    int wx, wy, wz;              // window extents
+    const ErodeChunk *chunks;
+    const int *chunk_start;      // n_orient + 1
+    const int2 *runs;            // (shared-memory offset, length)
+    int nx, ny, nz;
+    int orient_base, nb;
+    float *f;
+};
+void launch_erode2(const Erode2Args &a, size_t smem, cudaStream_t s);
 
 void launch_fill_f32(float *p, float v, long n, cudaStream_t s);
 void launch_max_omega0(const float *f, const uint8_t *fix, long n, unsigned *maxbits, cudaStream_t s);

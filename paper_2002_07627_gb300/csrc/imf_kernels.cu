@@ -175,6 +175,128 @@ __global__ void sweep_kernel(SweepArgs a)
     }
 }
 
+// One thread per (output word, orientation of the batch); results are OR-ed into A. The
+// cutter runs of the orientation are staged in shared memory as (row offset, x shift,
+// length); a run reads the 64 source bits starting at its shift with two funnel shifts and
+// ORs the window of its length by doubling.
+constexpr int kSweepStage = 512;
+
+__global__ void __launch_bounds__(256) sweep2_kernel(SweepArgs a)
+{
+    __shared__ int4 siv[kSweepStage];
+    const long total = (long)a.awords * a.ny * a.nz;
+    const int ob = blockIdx.y;
+    const int og = a.orient_base + ob;
+    const uint32_t *bits = a.bits + ob * a.b_so;
+    const int m0 = a.iv_start[og], m1 = a.iv_start[og + 1];
+    const long tstride = (long)gridDim.x * blockDim.x;
+    for (long tb = (long)blockIdx.x * blockDim.x; tb < total; tb += tstride) {
+        const long t = tb + threadIdx.x;
+        const bool live = t < total;
+        const int q = live ? (int)(t % a.awords) : 0;
+        const int y = live ? (int)((t / a.awords) % a.ny) : 0;
+        const int z = live ? (int)(t / ((long)a.awords * a.ny)) : 0;
+        const uint32_t *base = bits + (long)z * a.b_sz + (long)y * a.b_sy;
+        uint32_t *dstw = a.A + ((long)z * a.ny + y) * a.awords + q;
+        const int rem = a.nx - 32 * q;
+        const uint32_t full = rem < 32 ? (1u << rem) - 1u : 0xffffffffu;
+        // A only grows: words already fully accessible need no more work
+        const uint32_t old = live ? *dstw : full;
+        uint32_t acc = old;
+        for (int c0 = m0; c0 < m1; c0 += kSweepStage) {
+            const int cn = min(kSweepStage, m1 - c0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < cn; i += blockDim.x) {
+                const int4 iv = a.iv[c0 + i];     // (a, b, dy, dz)
+                siv[i] = make_int4((int)((long)(a.kz - iv.w) * a.b_sz + (long)(a.ky - iv.z) * a.b_sy),
+                                   a.kx - iv.y, iv.y - iv.x + 1, 0);
+            }
+            __syncthreads();
+            if (!live || (acc & full) == full) continue;
+            for (int i = 0; i < cn; ++i) {
+                const int4 r = siv[i];
+                const uint32_t *row = base + r.x;
+                const int s0 = 32 * q + r.y;
+                const int w0 = s0 >> 5, sh = s0 & 31;
+                const uint32_t u0 = row[w0], u1 = row[w0 + 1], u2 = row[w0 + 2];
+                uint32_t lo = __funnelshift_r(u0, u1, sh), hi = __funnelshift_r(u1, u2, sh);
+                const int L = r.z;
+                int span = 1;
+                while (span * 2 <= L) {
+                    lo |= __funnelshift_r(lo, hi, span);
+                    hi |= hi >> span;
+                    span *= 2;
+                }
+                if (span < L) lo |= __funnelshift_r(lo, hi, L - span);
+                acc |= lo;
+            }
+        }
+        if (live) {
+            const uint32_t add = acc & full & ~old;
+            if (add) atomicOr(dstw, add);
+        }
+    }
+}
+
+// Block-per-point variant of the re-check: 256 threads split the tool voxels of one flagged
+// translation, then a compensated block reduction.
+__global__ void __launch_bounds__(256) recheck_blocks_kernel(RecheckArgs a)
+{
+    __shared__ float rs[8], rc[8];
+    const int n = min(*a.count, a.cap);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int e = blockIdx.x; e < n; e += gridDim.x) {
+        const int2 fl = a.flags[e];
+        const int og = fl.x, lin = fl.y;
+        const int i = lin % a.wx, y = (lin / a.wx) % a.wy, z = lin / (a.wx * a.wy);
+        const int tx = i - a.kx, ty = y - a.ky, tz = z - a.kz;
+        float s = 0.f, c = 0.f;
+        const int m1 = a.rt_start[og + 1];
+        for (int m = a.rt_start[og] + threadIdx.x; m < m1; m += blockDim.x) {
+            const uint32_t p = __ldg(a.rt_off + m);
+            const int x = tx + (int)(p & 1023u) - 512;
+            const int yy = ty + (int)((p >> 10) & 1023u) - 512;
+            const int zz = tz + (int)((p >> 20) & 1023u) - 512;
+            if (x < 0 || yy < 0 || zz < 0 || x >= a.nx || yy >= a.ny || zz >= a.nz) continue;
+            const long idx = ((long)zz * a.ny + yy) * a.nx + x;
+            float r = __ldg(a.rho + idx);
+            if (a.fix && a.fix[idx]) r = fminf(1.f, r + 1.f);
+            float t, err;
+            two_sum(s, r, t, err);
+            s = t;
+            c += err;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s, off);
+            const float c2 = __shfl_down_sync(0xffffffffu, c, off);
+            float t, err;
+            two_sum(s, s2, t, err);
+            s = t;
+            c = c + c2 + err;
+        }
+        if (lane == 0) { rs[warp] = s; rc[warp] = c; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float S = rs[0], C = rc[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                float t, err;
+                two_sum(S, rs[w], t, err);
+                S = t;
+                C = C + rc[w] + err;
+            }
+            const double tot = (double)S + (double)C;
+            const long slot = og - a.orient_base;
+            a.g[slot * a.g_so + (long)z * a.g_sz + (long)y * a.g_sy + i] = (float)tot;
+            uint32_t *w = a.bits + slot * a.b_so + (long)z * a.b_sz + (long)y * a.b_sy + (i >> 5);
+            const uint32_t bit = 1u << (i & 31);
+            if (tot <= a.theta) atomicOr(w, bit);
+            else atomicAnd(w, ~bit);
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Minimum over sharp points (Eq. eq_imf_2): gamma_R(x) = min_k g_R(x - k), folded into the
 // running minimum over orientations and tools (Eq. eq_imf_5).
@@ -286,6 +408,18 @@ void launch_scatter_tool(float *dst, int Px, int Py, int Pz, const uint32_t *off
 void launch_recheck(const RecheckArgs &a, cudaStream_t s)
 {
     recheck_kernel<<<152 * 8, kThreads, 0, s>>>(a);
+}
+
+void launch_sweep2(const SweepArgs &a, cudaStream_t s)
+{
+    dim3 grid(blocks_for((long)a.awords * a.ny * a.nz, kThreads, 152 * 4), a.nb);
+    sweep2_kernel<<<grid, kThreads, 0, s>>>(a);
+}
+
+void launch_recheck_blocks(const RecheckArgs &a, int max_points, cudaStream_t s)
+{
+    int blocks = max_points < 1 ? 1 : (max_points > 152 * 8 ? 152 * 8 : max_points);
+    recheck_blocks_kernel<<<blocks, 256, 0, s>>>(a);
 }
 
 void launch_sweep(const SweepArgs &a, cudaStream_t s)

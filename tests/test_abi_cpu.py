@@ -70,3 +70,10 @@ def test_default_options_and_create_checks(lib):
     assert lib.imf_penalize_sensitivity(h, None, None, None, None, None, 0.5, None) == 1
     lib.imf_destroy(h)
     lib.imf_destroy(None)
+
+
+def test_stage_reciprocals_are_exact(lib):
+    L = ctypes.CDLL(build.HOSTLIB)
+    L.imf_host_check_div.restype = ctypes.c_long
+    # every stage divisor up to the longest plan, for every butterfly index the kernels use
+    assert L.imf_host_check_div(4096, 1 << 20) == 0
