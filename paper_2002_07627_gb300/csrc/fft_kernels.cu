@@ -99,50 +99,49 @@ template <int LOGW> __global__ void __launch_bounds__(kThreads) rfft_fwd_kernel(
     for (int i = threadIdx.x; i < M; i += blockDim.x) twM[i] = a.twM[i];
     for (int i = threadIdx.x; i <= M; i += blockDim.x) twP[i] = a.twP[i];
     const int r0 = blockIdx.x * W;
-    const int total = W * M;
-    for (int base = 0; base < total; base += 4 * kThreads) {
-        float2 v[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // one warp per row (row -> (y, z) once), lanes over the packed samples
+    for (int w = warp; w < W; w += kThreads / 32) {
+        const int r = r0 + w;
+        const bool rowok = r < a.rows;
+        const int y = rowok ? r % a.rows_y : 0, z = rowok ? r / a.rows_y : 0;
+        const float *row = a.src + z * a.src_sz + y * a.src_sy;
+        const uint8_t *frow = a.fix ? a.fix + z * a.src_sz + y * a.src_sy : nullptr;
+        for (int n0 = 0; n0 < M; n0 += 128) {
+            float2 v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int idx = base + u * kThreads + threadIdx.x;
-            const int w = idx / M, n = idx % M, r = r0 + w;
-            v[u] = make_float2(0.f, 0.f);
-            if (idx < total && r < a.rows) {
-                const int y = r % a.rows_y, z = r / a.rows_y;
-                const long rb = z * a.src_sz + y * a.src_sy;
-                const int x0 = 2 * n, x1 = 2 * n + 1;
-                if (x0 < a.nin) {
-                    float e = a.src[rb + x0];
-                    if (a.fix) e = fminf(1.f, e + (a.fix[rb + x0] ? 1.f : 0.f));
-                    v[u].x = e;
-                }
-                if (x1 < a.nin) {
-                    float e = a.src[rb + x1];
-                    if (a.fix) e = fminf(1.f, e + (a.fix[rb + x1] ? 1.f : 0.f));
-                    v[u].y = e;
+            for (int u = 0; u < 4; ++u) {
+                const int n = n0 + u * 32 + lane;
+                v[u] = make_float2(0.f, 0.f);
+                if (rowok && n < M) {
+                    const int x0 = 2 * n, x1 = 2 * n + 1;
+                    if (x0 < a.nin) v[u].x = frow ? fminf(1.f, row[x0] + (frow[x0] ? 1.f : 0.f)) : row[x0];
+                    if (x1 < a.nin) v[u].y = frow ? fminf(1.f, row[x1] + (frow[x1] ? 1.f : 0.f)) : row[x1];
                 }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int idx = base + u * kThreads + threadIdx.x;
-            if (idx < total) buf0[(idx % M) * ld + idx / M] = v[u];
+            for (int u = 0; u < 4; ++u) {
+                const int n = n0 + u * 32 + lane;
+                if (n < M) buf0[n * ld + w] = v[u];
+            }
         }
     }
     __syncthreads();
     float2 *src = buf0, *dst = buf1;
     run_stages<-1, LOGW>(a.plan, src, dst, ld, twM);
     // unpack: X[k] = (Z[k] + conj Z[M-k]) / 2 + exp(-2 pi i k / P) (Z[k] - conj Z[M-k]) / (2 i)
-    for (int idx = threadIdx.x; idx < W * (M + 1); idx += blockDim.x) {
-        const int w = idx / (M + 1), k = idx % (M + 1), r = r0 + w;
-        if (r >= a.rows) continue;
-        const float2 zk = src[(k == M ? 0 : k) * ld + w];
-        const float2 zc = c_conj(src[(k == 0 ? 0 : M - k) * ld + w]);
-        const float2 e = c_scale(c_add(zk, zc), 0.5f);
-        const float2 od = c_mul_si<-1>(c_scale(c_sub(zk, zc), 0.5f));
-        const float2 X = c_add(e, c_mul(twP[k], od));
+    for (int w = warp; w < W; w += kThreads / 32) {
+        const int r = r0 + w;
+        if (r >= a.rows) break;
         const int y = r % a.rows_y, z = r / a.rows_y;
-        a.out[z * a.out_sz + y * a.out_sy + k] = X;
+        float2 *out = a.out + z * a.out_sz + y * a.out_sy;
+        for (int k = lane; k <= M; k += 32) {
+            const float2 zk = src[(k == M ? 0 : k) * ld + w];
+            const float2 zc = c_conj(src[(k == 0 ? 0 : M - k) * ld + w]);
+            const float2 e = c_scale(c_add(zk, zc), 0.5f);
+            const float2 od = c_mul_si<-1>(c_scale(c_sub(zk, zc), 0.5f));
+            out[k] = c_add(e, c_mul(twP[k], od));
+        }
     }
 }
 
@@ -157,23 +156,24 @@ template <int LOGW> __global__ void __launch_bounds__(kThreads) irfft_threshold_
     const int r0 = blockIdx.x * W;
     const long o = blockIdx.z;
     const float2 *in = a.in + o * a.in_so;
-    const int total = W * (M + 1);
-    for (int base = 0; base < total; base += 8 * kThreads) {
-        float2 v[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int w = warp; w < W; w += kThreads / 32) {
+        const int r = r0 + w;
+        const bool rowok = r < a.rows;
+        const int y = rowok ? r % a.rows_y : 0, z = rowok ? r / a.rows_y : 0;
+        const float2 *row = in + z * a.in_sz + y * a.in_sy;
+        for (int k0 = 0; k0 <= M; k0 += 128) {
+            float2 v[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int idx = base + u * kThreads + threadIdx.x;
-            const int w = idx / (M + 1), k = idx % (M + 1), r = r0 + w;
-            v[u] = make_float2(0.f, 0.f);
-            if (idx < total && r < a.rows) {
-                const int y = r % a.rows_y, z = r / a.rows_y;
-                v[u] = in[z * a.in_sz + y * a.in_sy + k];
+            for (int u = 0; u < 4; ++u) {
+                const int k = k0 + u * 32 + lane;
+                v[u] = (rowok && k <= M) ? row[k] : make_float2(0.f, 0.f);
             }
-        }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int idx = base + u * kThreads + threadIdx.x;
-            if (idx < total) buf1[(idx % (M + 1)) * ld + idx / (M + 1)] = v[u];
+            for (int u = 0; u < 4; ++u) {
+                const int k = k0 + u * 32 + lane;
+                if (k <= M) buf1[k * ld + w] = v[u];
+            }
         }
     }
     __syncthreads();
@@ -190,41 +190,44 @@ template <int LOGW> __global__ void __launch_bounds__(kThreads) irfft_threshold_
     float2 *src = buf0, *dst = buf1;
     run_stages<1, LOGW>(a.plan, src, dst, ld, twM);
     // g[i] = Re z[i/2] (i even) or Im z[i/2] (i odd), clamped at 0 (g >= 0 exactly)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int nwords = (a.nout + 31) >> 5;
     float *g = a.g + o * a.g_so;
     uint32_t *bits = a.bits + o * a.b_so;
-    for (int p = warp; p < W * nwords; p += nwarp) {
-        const int w = p / nwords, q = p % nwords, r = r0 + w;
-        if (r >= a.rows) continue;  // warp-uniform
+    for (int w = warp; w < W; w += nwarp) {
+        const int r = r0 + w;
+        if (r >= a.rows) break;  // warp-uniform
         const int y = r % a.rows_y, z = r / a.rows_y;
-        const int i = q * 32 + lane;
-        const bool valid = i < a.nout;
-        float gv = 0.f;
-        if (valid) {
-            const float2 zz = src[(i >> 1) * ld + w];
-            gv = fmaxf((i & 1) ? zz.y : zz.x, 0.f);
-            g[z * a.g_sz + y * a.g_sy + i] = gv;
-        }
-        const unsigned freeb = __ballot_sync(0xffffffffu, valid && gv <= a.theta);
-        if (lane == 0) bits[z * a.b_sz + y * a.b_sy + q] = freeb;
-        if (a.flag) {
-            const bool near = valid && fabsf(gv - a.theta) <= a.band;
-            const unsigned nm = __ballot_sync(0xffffffffu, near);
-            if (nm) {
-                int base = 0;
-                if (lane == 0) {
-                    base = atomicAdd(a.flag_count, __popc(nm));
-                    atomicAdd(a.flag_total, __popc(nm));
-                }
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (near) {
-                    const int slot = base + __popc(nm & ((1u << lane) - 1u));
-                    if (slot < a.flag_cap) {
-                        const long lin = ((long)z * a.rows_y + y) * a.nout + i;
-                        a.flags[slot] = make_int2(a.orient_base + (int)o, (int)lin);
-                    } else {
-                        atomicExch(a.status, kDevOverflow);
+        float *grow = g + z * a.g_sz + y * a.g_sy;
+        uint32_t *brow = bits + z * a.b_sz + y * a.b_sy;
+        for (int q = 0; q < nwords; ++q) {
+            const int i = q * 32 + lane;
+            const bool valid = i < a.nout;
+            float gv = 0.f;
+            if (valid) {
+                const float2 zz = src[(i >> 1) * ld + w];
+                gv = fmaxf((i & 1) ? zz.y : zz.x, 0.f);
+                grow[i] = gv;
+            }
+            const unsigned freeb = __ballot_sync(0xffffffffu, valid && gv <= a.theta);
+            if (lane == 0) brow[q] = freeb;
+            if (a.flag) {
+                const bool near = valid && fabsf(gv - a.theta) <= a.band;
+                const unsigned nm = __ballot_sync(0xffffffffu, near);
+                if (nm) {
+                    int base = 0;
+                    if (lane == 0) {
+                        base = atomicAdd(a.flag_count, __popc(nm));
+                        atomicAdd(a.flag_total, __popc(nm));
+                    }
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (near) {
+                        const int slot = base + __popc(nm & ((1u << lane) - 1u));
+                        if (slot < a.flag_cap) {
+                            const long lin = ((long)z * a.rows_y + y) * a.nout + i;
+                            a.flags[slot] = make_int2(a.orient_base + (int)o, (int)lin);
+                        } else {
+                            atomicExch(a.status, kDevOverflow);
+                        }
                     }
                 }
             }
