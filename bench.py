@@ -243,7 +243,7 @@ def run_ours(args):
     shape = d.rho.shape
     nG = int(np.prod(shape))
     n_orient = sum(len(t.quats) for t in d.tools)
-    imf = binding.Imf(shape)
+    imf = binding.Imf(shape, orient_batch=args.orient_batch)
     imf.set_tools(d.tools)
     info = imf.tool_info(0)
     rho = torch.from_numpy(d.rho).to(dev)
@@ -395,6 +395,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-block", type=int, default=24)
     ap.add_argument("--error-points", type=int, default=6)
+    ap.add_argument("--orient-batch", type=int, default=0, help="orientations per device batch (0: library default)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

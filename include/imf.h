@@ -69,7 +69,7 @@ typedef struct {
     int precision;           /* IMF_AUTO | IMF_FP32_FFT | IMF_BF16_DIRECT                      */
     int recheck;             /* 1: re-check translations with |g - theta| <= band exactly      */
     double recheck_band;     /* band half-width in voxel volumes; <= 0 picks a default         */
-    int orient_batch;        /* orientations per batch of device work; 0 picks one             */
+    int orient_batch;        /* orientations per batch of device work; 0 = 16 (fewer if budget) */
     size_t hbm_budget_bytes; /* cap on library-owned device memory; 0 = no cap (App. B)        */
 } imf_options;
 

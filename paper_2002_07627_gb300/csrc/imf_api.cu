@@ -414,7 +414,7 @@ imf_status ensure_work(imf_handle h)
     if (rs > h->rho_spec_n) { dfree(h, h->rho_spec, h->rho_spec_n); TRY(dalloc(h, &h->rho_spec, rs)); h->rho_spec_n = rs; }
     if (x1 > h->X1_n) { dfree(h, h->X1, h->X1_n); TRY(dalloc(h, &h->X1, x1)); h->X1_n = x1; }
     if (x2 > h->X2_n) { dfree(h, h->X2, h->X2_n); TRY(dalloc(h, &h->X2, x2)); h->X2_n = x2; }
-    int want = op.orient_batch > 0 ? op.orient_batch : 4;
+    int want = op.orient_batch > 0 ? op.orient_batch : 16;
     want = std::min(want, maxo);
     const size_t per_slot = y1 * 8 + y2 * 8 + gn * 4 + bn * 4;
     if (op.hbm_budget_bytes) {
