@@ -228,6 +228,94 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """Batched form (uneven designs, autotuned, CUDA graphs, stream pool) against the plain
+    one-design-at-a-time form on the same designs."""
+    import torch
+    from paper_2002_07627_gb300 import build, batch, synth
+    build.build()
+    ds = synth.config_batch(args.batch_designs, seed=0)
+    tp, units = batch.run_plain(ds, reps=1)
+    br = batch.BatchRunner(ds, n_streams=args.streams, autotune=True, graphs=True)
+    br.run()
+    times = [br.run() for _ in range(max(1, args.steps))]
+    br.check()
+    tb = statistics.median(times)
+    chosen = sorted(e.batch for e in br.entries)
+    br.close()
+    out = {"metric": METRIC, "value": units / tb, "unit": UNIT, "n_gpus": 1, "steps": len(times),
+           "warmup": 1, "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"batched IMF: {len(ds)} designs, cubic grids 48-192 log-uniform, "
+                                  f"16-128 orientations, cutter radius 2-6 (holder 2.5x)",
+                      "designs": len(ds), "voxel_orientations_per_pass": units,
+                      "form": f"resident handles, autotuned orientation batch, CUDA graphs, {args.streams} streams",
+                      "autotuned_batches": chosen},
+           "plain": {"value": units / tp, "ms_per_pass": tp * 1e3,
+                     "form": "one design at a time on one stream, default options, no graphs"},
+           "speedup_vs_plain": tp / tb}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Served form: Poisson arrivals from simulated TO loops, continuous batching over stream
+    slots, HBM-budget admission; p50/p99 latency and throughput per arrival rate."""
+    import torch
+    from paper_2002_07627_gb300 import build, synth
+    from paper_2002_07627_gb300.serve import DesignSpec, GpuExecutor, ImfServer
+    build.build()
+    rng = np.random.default_rng(0)
+    specs, rhos = {}, {}
+    for i in range(args.serve_loops):
+        n = int(round(np.exp(rng.uniform(np.log(64), np.log(args.serve_max_grid)))))
+        nr = int(rng.integers(32, 129))
+        rho = synth.beam_density((n, n, n), n_beams=max(4, int(40 * (n / 128) ** 2)), seed=100 + i)
+        fix = synth.slab_fixture(rho.shape, max(2, n // 24), axis="z")
+        tool = synth.cylinder_tool(3, 20, 8, 16, synth.fibonacci_quats(nr))
+        specs[i] = DesignSpec(rho.shape, [tool], fix)
+        rhos[i] = rho
+    srv = ImfServer(GpuExecutor(args.streams), hbm_budget=int(args.serve_budget_gb * (1 << 30)), slots=args.streams)
+    for i, sp in specs.items():
+        srv.register(i, sp)
+    # warm every design once (setup: tool spectra), then measure each rate
+    for f in [srv.submit(i, rhos[i]) for i in specs]:
+        f.result(timeout=600)
+    rates = []
+    for rate in args.serve_rates:
+        srv.stats.latencies.clear()
+        units0 = srv.stats.units
+        t_arr = np.cumsum(rng.exponential(1.0 / rate, size=args.serve_requests))
+        t0 = time.perf_counter()
+        futs = []
+        for k, ta in enumerate(t_arr):
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            i = int(rng.integers(0, len(specs)))
+            futs.append(srv.submit(i, np.clip(rhos[i] + 1e-3 * ((k % 7) - 3), 0, 1).astype(np.float32)))
+        for f in futs:
+            f.result(timeout=600)
+        wall = time.perf_counter() - t0
+        lat = np.array(srv.stats.latencies) * 1e3
+        rates.append({"rate_per_s": rate, "requests": len(futs), "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "throughput": (srv.stats.units - units0) / wall,
+                      "offered_load_s": float(t_arr[-1]), "wall_s": wall})
+    st = srv.stats
+    srv.close()
+    best = max(rates, key=lambda r: r["throughput"])
+    out = {"metric": METRIC, "value": best["throughput"], "unit": UNIT, "n_gpus": 1,
+           "steps": sum(r["requests"] for r in rates), "warmup": len(specs), "ms_per_step": best["p50_ms"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"served IMF: {len(specs)} TO loops, cubic grids 64-{args.serve_max_grid} "
+                                  f"log-uniform, 32-128 orientations, Poisson arrivals",
+                      "slots": args.streams, "hbm_budget_gb": args.serve_budget_gb},
+           "rates": rates, "evictions": st.evictions, "creations": st.creations,
+           "max_running": st.max_running}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_setup()
@@ -391,14 +479,25 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="beams128", choices=sorted(WORKLOADS) + ["planar64"])
+    ap.add_argument("--workload", default="beams128", choices=sorted(WORKLOADS) + ["planar64", "batch64", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-block", type=int, default=24)
     ap.add_argument("--error-points", type=int, default=6)
     ap.add_argument("--orient-batch", type=int, default=0, help="orientations per device batch (0: library default)")
+    ap.add_argument("--batch-designs", type=int, default=64)
+    ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--serve-loops", type=int, default=8)
+    ap.add_argument("--serve-max-grid", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=96)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[50, 200, 500, 1000, 2000])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

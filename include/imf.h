@@ -151,6 +151,27 @@ imf_status imf_penalize_sensitivity_noalloc(float *sens, const float *rho_omega,
                                             const uint8_t *secluded, const uint8_t *fixture, long n,
                                             double w_acc, double tau, void *cuda_stream);
 
+/*
+ * Batched and served forms (not in the paper; they reshape how Alg. 1 is launched).
+ *
+ * imf_capture_graph records one imf_compute with these exact arrays into a CUDA graph owned by
+ * the handle (it first runs imf_compute once on `cuda_stream` so every buffer exists, then
+ * captures on that stream). imf_launch_graph replays it on any stream; the arrays given at
+ * capture must stay valid and are read / written in place on every replay. Profiling is
+ * suspended during capture. Synchronous capture; asynchronous replay.
+ * Errors: IMF_ERR_NOT_READY, IMF_ERR_INVALID_ARG, IMF_ERR_CUDA. */
+imf_status imf_capture_graph(imf_handle h, const float *rho_omega, const uint8_t *fixture, float *imf_bar,
+                             uint8_t *secluded, float *imf_raw, uint8_t *accessible, void *cuda_stream);
+imf_status imf_launch_graph(imf_handle h, void *cuda_stream);
+
+/*
+ * Autotuner: times imf_compute on these arrays for each orientation-batch size in
+ * {4, 8, 16, 32, 64} (capped by the orientation count and the HBM budget), keeps the fastest in
+ * the handle's options and returns it in *best (NULL allowed). Synchronous; it replaces a
+ * captured graph, which must be captured again. */
+imf_status imf_autotune(imf_handle h, const float *rho_omega, const uint8_t *fixture, float *imf_bar,
+                        uint8_t *secluded, void *cuda_stream, int *best);
+
 /* Wait for the last stream used by the handle and return the device-side status
  * (IMF_OK, IMF_ERR_OVERFLOW, IMF_ERR_TIMEOUT) or IMF_ERR_CUDA; clears it. */
 imf_status imf_sync_status(imf_handle h);

@@ -23,7 +23,7 @@ EXPORTS = ["imf_default_options", "imf_create", "imf_set_tool", "imf_compute", "
            "imf_penalize_sensitivity", "imf_sync_status", "imf_last_error", "imf_destroy",
            "imf_get_tool_info", "imf_get_offsets", "imf_set_debug", "imf_get_last_g", "imf_get_stats",
            "imf_set_profiling", "imf_get_kernel_time", "imf_reset_kernel_times",
-           "imf_penalize_sensitivity_noalloc"]
+           "imf_penalize_sensitivity_noalloc", "imf_capture_graph", "imf_launch_graph", "imf_autotune"]
 
 
 class ImfOptions(ctypes.Structure):
@@ -82,6 +82,9 @@ def load(path: str | None = None):
                                       ctypes.POINTER(Lg)]
     L.imf_reset_kernel_times.argtypes = [H]
     L.imf_penalize_sensitivity_noalloc.argtypes = [P, P, P, P, P, Lg, D, D, P]
+    L.imf_capture_graph.argtypes = [H, P, P, P, P, P, P, P]
+    L.imf_launch_graph.argtypes = [H, P]
+    L.imf_autotune.argtypes = [H, P, P, P, P, P, ctypes.POINTER(I)]
     for name in EXPORTS:
         if name not in ("imf_default_options", "imf_destroy", "imf_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -217,6 +220,28 @@ class Imf:
         self._check(self.lib.imf_penalize_sensitivity(self.h, _ptr(sens), _ptr(rho), _ptr(fbar), _ptr(secluded),
                                                       _ptr(fixture), float(w_acc), s))
         return sens
+
+    def capture_graph(self, rho, fixture, fbar, secluded, raw=None, accessible=None, stream=None):
+        """Record one compute with these exact tensors into a replayable CUDA graph."""
+        import torch
+        s = (stream or torch.cuda.current_stream(rho.device)).cuda_stream
+        self._check(self.lib.imf_capture_graph(self.h, _ptr(rho), _ptr(fixture), _ptr(fbar), _ptr(secluded),
+                                               _ptr(raw), _ptr(accessible), s))
+
+    def launch_graph(self, stream=None):
+        import torch
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        self._check(self.lib.imf_launch_graph(self.h, s))
+
+    def autotune(self, rho, fixture=None, stream=None) -> int:
+        import torch
+        fb = torch.empty_like(rho)
+        sec = torch.empty(rho.shape, dtype=torch.uint8, device=rho.device)
+        s = (stream or torch.cuda.current_stream(rho.device)).cuda_stream
+        best = ctypes.c_int()
+        self._check(self.lib.imf_autotune(self.h, _ptr(rho), _ptr(fixture), _ptr(fb), _ptr(sec), s,
+                                          ctypes.byref(best)))
+        return best.value
 
     def sync(self):
         self._check(self.lib.imf_sync_status(self.h))

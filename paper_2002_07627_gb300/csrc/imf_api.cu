@@ -105,6 +105,9 @@ struct imf_handle_s {
     std::vector<cudaEvent_t> ev_pool;
     double prof_ms[KID_COUNT] = {0};
     long prof_cnt[KID_COUNT] = {0};
+    // captured graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
     // debug
     bool keep_g = false;
     int last_batch_base = -1, last_batch_n = 0, last_tool = -1;
@@ -416,34 +419,41 @@ imf_status ensure_work(imf_handle h)
     if (x2 > h->X2_n) { dfree(h, h->X2, h->X2_n); TRY(dalloc(h, &h->X2, x2)); h->X2_n = x2; }
     int want = op.orient_batch > 0 ? op.orient_batch : 16;
     want = std::min(want, maxo);
-    const size_t per_slot = y1 * 8 + y2 * 8 + gn * 4 + bn * 4;
+    // per orientation slot: Y1, Y2, g, free bits and its share of the near-threshold list
+    const size_t per_slot = y1 * 8 + y2 * 8 + gn * 4 + bn * 4 + (gn / 32 + 1) * sizeof(int2);
     if (op.hbm_budget_bytes) {
         const size_t have = op.hbm_budget_bytes > h->owned_bytes ? op.hbm_budget_bytes - h->owned_bytes : 0;
-        const size_t cur = (size_t)h->slots * (h->Y1_n * 8 + h->Y2_n * 8 + h->g_n * 4 + h->bits_n * 4);
-        int fit = (int)((have + cur) / std::max<size_t>(per_slot, 1));
+        const size_t cur = (size_t)h->slots * (h->Y1_n * 8 + h->Y2_n * 8 + h->g_n * 4 + h->bits_n * 4) +
+                           (size_t)h->flag_cap * sizeof(int2);
+        const size_t fixed = (size_t)(1 << 16) * sizeof(int2);
+        const long fit = (long)((have + cur > fixed ? have + cur - fixed : 0) / std::max<size_t>(per_slot, 1));
         if (fit < 1) return fail(h, IMF_ERR_BUDGET, "one orientation slot needs %zu bytes; budget has %zu", per_slot, have + cur);
-        want = std::min(want, fit);
+        want = (int)std::min<long>(want, fit);
     }
     if (y1 > h->Y1_n || y2 > h->Y2_n || gn > h->g_n || bn > h->bits_n || want != h->slots) {
-        dfree(h, h->Y1, h->Y1_n * h->slots);
-        dfree(h, h->Y2, h->Y2_n * h->slots);
-        dfree(h, h->g, h->g_n * h->slots);
-        dfree(h, h->bits, h->bits_n * h->slots);
+        dfree(h, h->Y1);
+        dfree(h, h->Y2);
+        dfree(h, h->g);
+        dfree(h, h->bits);
+        dfree(h, h->flags);
+        h->flag_cap = 0;
+        h->slots = 0;          // consistent if an allocation below fails: the next call retries
         h->Y1_n = std::max(y1, h->Y1_n);
         h->Y2_n = std::max(y2, h->Y2_n);
         h->g_n = std::max(gn, h->g_n);
         h->bits_n = std::max(bn, h->bits_n);
-        h->slots = want;
         TRY(dalloc(h, &h->Y1, h->Y1_n * want));
         TRY(dalloc(h, &h->Y2, h->Y2_n * want));
         TRY(dalloc(h, &h->g, h->g_n * want));
         TRY(dalloc(h, &h->bits, h->bits_n * want));
         CU(cudaMemset(h->bits, 0, h->bits_n * want * sizeof(uint32_t)));
         CU(cudaMemset(h->g, 0, h->g_n * want * sizeof(float)));
+        h->slots = want;
     }
-    const long wcap = std::max<long>(1 << 16, (long)(gn * want / 32));
-    if (wcap > h->flag_cap) {
-        dfree(h, h->flags, (size_t)h->flag_cap);
+    const long wcap = std::max<long>(1 << 16, (long)(h->g_n * h->slots / 32));
+    if (!h->flags || wcap > h->flag_cap) {
+        dfree(h, h->flags);
+        h->flag_cap = 0;
         TRY(dalloc(h, &h->flags, (size_t)wcap));
         h->flag_cap = (int)std::min<long>(wcap, 1L << 30);
     }
@@ -540,6 +550,8 @@ void imf_destroy(imf_handle h)
     dfree(h, h->dev_small, 8);
     for (float **p : {&h->h_rho, &h->h_fbar, &h->h_raw}) dfree(h, *p, 0);
     for (uint8_t **p : {&h->h_fix, &h->h_sec, &h->h_acc}) dfree(h, *p, 0);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
     for (auto &r : h->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     delete h;
@@ -734,6 +746,11 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
         plan_erode(t.sh[i], t.kmax, chunks, eruns, t.erode_smem);
         chst[i + 1] = (int)chunks.size();
     }
+    if (t.erode_smem + kErMaxRunsPerChunk * sizeof(int2) > 227 * 1024) {
+        free_tool(h, t);
+        return fail(h, IMF_ERR_INVALID_ARG, "sharp-point set too wide for the tiled minimum (%zu bytes of tile)",
+                    t.erode_smem);
+    }
     st = IMF_OK;
     auto bail = [&](imf_status s2) { free_tool(h, t); return s2; };
     twiddles(t.M, t.M, t.M, tw);
@@ -784,6 +801,9 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
     const imf_options &op = h->opt;
     const long N = (long)op.nx * op.ny * op.nz;
     TRY(ensure_work(h));
+    if (!h->f || !h->A || !h->dev_small || !h->flags || !h->Y1 || !h->Y2 || !h->g || !h->bits || !h->rho_spec ||
+        !h->X1 || !h->X2 || h->slots < 1)
+        return fail(h, IMF_ERR_OOM, "work buffers are not allocated");
     h->last_stream = s;
     h->used_stream = true;
     int *status = h->dev_small, *fcount = h->dev_small + 1;
@@ -945,6 +965,91 @@ imf_status imf_penalize_sensitivity(imf_handle h, float *sens, const float *rho_
         launch_penalize(sens, rho_omega, imf_bar, secluded, N, mb, w_acc, h->opt.tau, s);
     }
     CU(cudaGetLastError());
+    return IMF_OK;
+}
+
+imf_status imf_capture_graph(imf_handle h, const float *rho_omega, const uint8_t *fixture, float *imf_bar,
+                             uint8_t *secluded, float *imf_raw, uint8_t *accessible, void *cuda_stream)
+{
+    if (!h) return IMF_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!s) return fail(h, IMF_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+    TRY(imf_compute(h, rho_omega, fixture, imf_bar, secluded, imf_raw, accessible, cuda_stream));
+    CU(cudaStreamSynchronize(s));
+    if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    const bool prof = h->prof;
+    h->prof = false;
+    CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const long launches = h->launches;
+    imf_status st = compute_impl(h, rho_omega, fixture, imf_bar, secluded, imf_raw, accessible, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    h->prof = prof;
+    h->launches = launches;
+    h->computes--;
+    if (st != IMF_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return fail(h, IMF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    h->graph = g;
+    CU(cudaGraphInstantiate(&h->graph_exec, g, 0));
+    return IMF_OK;
+}
+
+imf_status imf_launch_graph(imf_handle h, void *cuda_stream)
+{
+    if (!h) return IMF_ERR_INVALID_ARG;
+    if (!h->graph_exec) return fail(h, IMF_ERR_NOT_READY, "no captured graph");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    CU(cudaGraphLaunch(h->graph_exec, s));
+    h->last_stream = s;
+    h->used_stream = true;
+    h->computes++;
+    return IMF_OK;
+}
+
+imf_status imf_autotune(imf_handle h, const float *rho_omega, const uint8_t *fixture, float *imf_bar,
+                        uint8_t *secluded, void *cuda_stream, int *best)
+{
+    if (!h) return IMF_ERR_INVALID_ARG;
+    if (h->n_tools == 0) return fail(h, IMF_ERR_NOT_READY, "imf_autotune before imf_set_tool");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int maxo = 1;
+    for (int i = 0; i < h->n_tools; ++i) maxo = std::max(maxo, h->tools[i].n_orient);
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int best_nb = h->opt.orient_batch > 0 ? h->opt.orient_batch : 16;
+    const int cands[5] = {4, 8, 16, 32, 64};
+    imf_status st = IMF_OK;
+    for (int c = 0; c < 5 && st == IMF_OK; ++c) {
+        const int nb = cands[c];
+        if (nb > 4 && nb / 2 >= maxo) break;      // larger batches change nothing
+        h->opt.orient_batch = nb;
+        st = imf_compute(h, rho_omega, fixture, imf_bar, secluded, nullptr, nullptr, cuda_stream);
+        if (st == IMF_ERR_BUDGET || st == IMF_ERR_OOM) { st = IMF_OK; cudaGetLastError(); break; }
+        if (st != IMF_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 2 && st == IMF_OK; ++r)
+            st = imf_compute(h, rho_omega, fixture, imf_bar, secluded, nullptr, nullptr, cuda_stream);
+        cudaEventRecord(e1, s);
+        const cudaError_t es = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (es != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(h, IMF_ERR_CUDA, "autotune: %s", cudaGetErrorString(es != cudaSuccess ? es : cudaGetLastError()));
+        }
+        if (st == IMF_OK && ms < best_ms) { best_ms = ms; best_nb = nb; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != IMF_OK) return st;
+    h->opt.orient_batch = best_nb;
+    TRY(ensure_work(h));
+    if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    if (best) *best = best_nb;
     return IMF_OK;
 }
 

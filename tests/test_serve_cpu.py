@@ -1,0 +1,140 @@
+"""Host logic of the serving loop, driven by a fake executor on the CPU: every request resolves,
+the HBM budget and the slot count are never exceeded, idle designs are evicted least recently
+used first, a design runs one request at a time, and failures stay with their request."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2002_07627_gb300.serve import DesignSpec, ImfServer
+from paper_2002_07627_gb300 import synth
+
+
+class FakeExecutor:
+    def __init__(self, sizes, duration=0.002, fail_on=None):
+        self.sizes = sizes
+        self.duration = duration
+        self.fail_on = fail_on or set()
+        self.lock = threading.Lock()
+        self.resident = {}
+        self.running = set()
+        self.max_bytes = 0
+        self.max_running = 0
+        self.created = []
+        self.destroyed = []
+        self.calls = 0
+
+    def footprint(self, spec):
+        return self.sizes[spec.fixture]        # the fixture slot carries the fake design id
+
+    def create(self, design_id, spec):
+        with self.lock:
+            self.resident[design_id] = self.footprint(spec)
+            self.max_bytes = max(self.max_bytes, sum(self.resident.values()))
+            self.created.append(design_id)
+        return {"id": design_id}
+
+    def destroy(self, st):
+        with self.lock:
+            self.resident.pop(st["id"])
+            self.destroyed.append(st["id"])
+
+    def launch(self, st, rho, slot):
+        with self.lock:
+            self.calls += 1
+            assert st["id"] not in {r[0] for r in self.running}, "two requests of one design in flight"
+            self.running.add((st["id"], slot))
+            self.max_running = max(self.max_running, len(self.running))
+        if float(rho.ravel()[0]) in self.fail_on:
+            with self.lock:
+                self.running.discard((st["id"], slot))
+            raise RuntimeError("injected launch failure")
+        return (st["id"], slot, time.perf_counter() + self.duration, rho)
+
+    def done(self, tok):
+        return time.perf_counter() >= tok[2]
+
+    def result(self, tok):
+        with self.lock:
+            self.running.discard((tok[0], tok[1]))
+        return tok[0], float(tok[3].sum())
+
+
+def _spec(i):
+    tool = synth.planar_tool(n_orient=2)
+    return DesignSpec((1, 4, 4), [tool], fixture=i)
+
+
+def test_all_requests_resolve_within_budget_and_slots():
+    sizes = {i: 30 for i in range(6)}
+    ex = FakeExecutor(sizes)
+    srv = ImfServer(ex, hbm_budget=100, slots=3)
+    for i in range(6):
+        srv.register(i, _spec(i))
+    futs = []
+    rng = np.random.default_rng(0)
+    for k in range(120):
+        d = int(rng.integers(0, 6))
+        futs.append((d, k, srv.submit(d, np.full((1, 4, 4), k, np.float32))))
+    for d, k, f in futs:
+        did, s = f.result(timeout=30)
+        assert did == d and s == 16 * k
+    srv.close()
+    assert ex.max_bytes <= 100
+    assert ex.max_running <= 3
+    assert srv.stats.completed == 120 and srv.stats.failed == 0
+    assert srv.stats.evictions > 0          # 6 x 30 bytes cannot all be resident under 100
+    assert len(srv.stats.latencies) == 120
+
+
+def test_lru_eviction_order():
+    sizes = {0: 40, 1: 40, 2: 40}
+    ex = FakeExecutor(sizes, duration=0.0)
+    srv = ImfServer(ex, hbm_budget=80, slots=1)
+    for i in range(3):
+        srv.register(i, _spec(i))
+    for d in (0, 1, 0):
+        srv.submit(d, np.zeros((1, 4, 4), np.float32)).result(timeout=10)
+    srv.submit(2, np.zeros((1, 4, 4), np.float32)).result(timeout=10)
+    srv.close()
+    assert ex.destroyed[0] == 1              # design 1 was used least recently
+
+
+def test_failures_stay_with_their_request():
+    ex = FakeExecutor({0: 10, 1: 10}, fail_on={7.0})
+    srv = ImfServer(ex, hbm_budget=100, slots=2)
+    srv.register(0, _spec(0))
+    srv.register(1, _spec(1))
+    ok = srv.submit(0, np.full((1, 4, 4), 1, np.float32))
+    bad = srv.submit(1, np.full((1, 4, 4), 7, np.float32))
+    ok2 = srv.submit(1, np.full((1, 4, 4), 2, np.float32))
+    assert ok.result(timeout=10)[1] == 16
+    with pytest.raises(RuntimeError, match="injected"):
+        bad.result(timeout=10)
+    assert ok2.result(timeout=10)[1] == 32
+    unknown = srv.submit(9, np.zeros((1, 4, 4), np.float32))
+    with pytest.raises(KeyError):
+        unknown.result(timeout=1)
+    srv.close()
+    assert srv.stats.failed == 1
+
+
+def test_design_above_budget_is_rejected_not_hung():
+    ex = FakeExecutor({0: 500})
+    srv = ImfServer(ex, hbm_budget=100, slots=2)
+    srv.register(0, _spec(0))
+    with pytest.raises(MemoryError):
+        srv.submit(0, np.zeros((1, 4, 4), np.float32)).result(timeout=10)
+    srv.close()
+
+
+def test_requests_of_one_design_run_in_order():
+    ex = FakeExecutor({0: 10}, duration=0.001)
+    srv = ImfServer(ex, hbm_budget=100, slots=4)
+    srv.register(0, _spec(0))
+    futs = [srv.submit(0, np.full((1, 4, 4), k, np.float32)) for k in range(20)]
+    done = [f.result(timeout=10)[1] for f in futs]
+    srv.close()
+    assert done == [16 * k for k in range(20)]
+    assert ex.max_running == 1
