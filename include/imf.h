@@ -66,7 +66,7 @@ typedef struct {
     double lambda;           /* allowance lambda of Alg. 1 (0.01 in Sec. 2.1.5)                */
     double tau;              /* density threshold tau of Sec. 2.1.5 / Eq. eq_accFilter (0.5)  */
     double theta_rel;        /* collision threshold theta_i = theta_rel * |T_i| (0.01)         */
-    int precision;           /* IMF_AUTO | IMF_FP32_FFT | IMF_BF16_DIRECT                      */
+    int precision;           /* IMF_AUTO | IMF_FP32_FFT | IMF_BF16_DIRECT (collision path)     */
     int recheck;             /* 1: re-check translations with |g - theta| <= band exactly      */
     double recheck_band;     /* band half-width in voxel volumes; <= 0 picks a default         */
     int orient_batch;        /* orientations per batch of device work; 0 = 16 (fewer if budget) */
@@ -200,6 +200,18 @@ typedef struct {
 } imf_tool_info;
 
 imf_status imf_get_tool_info(imf_handle h, int tool_id, imf_tool_info *out);
+
+/* Select the collision path of a tool: IMF_FP32_FFT (needs the spectra, i.e. the handle was not
+ * created with IMF_BF16_DIRECT) or IMF_BF16_DIRECT (available when every orientation group's
+ * union of rotated tool voxels fits the tensor-core kernel). Synchronous. With IMF_AUTO the
+ * path starts as IMF_FP32_FFT and imf_autotune keeps the faster of the two.
+ * Errors: IMF_ERR_INVALID_ARG when the path is not available. */
+imf_status imf_set_path(imf_handle h, int tool_id, int path);
+
+/* Tensor-core self-test: D[128 x N] = A[128 x K] B[N x K]^T for HOST row-major BF16 bit
+ * patterns A, B and a HOST FP32 result D, computed by the same tcgen05 / TMEM / descriptor
+ * code the direct path uses (N a multiple of 16 in [16, 256], K a multiple of 16). Synchronous. */
+imf_status imf_selftest_mma(int N, int K, const uint16_t *A, const uint16_t *B, float *D);
 
 /* Copy the resampled offsets of one orientation to HOST int32 [n][3] (x, y, z) arrays:
  * which = 0 (R T), 1 (R K), 2 (sharp points). *n receives the count; `out` may be NULL to

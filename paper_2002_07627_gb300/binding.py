@@ -23,7 +23,8 @@ EXPORTS = ["imf_default_options", "imf_create", "imf_set_tool", "imf_compute", "
            "imf_penalize_sensitivity", "imf_sync_status", "imf_last_error", "imf_destroy",
            "imf_get_tool_info", "imf_get_offsets", "imf_set_debug", "imf_get_last_g", "imf_get_stats",
            "imf_set_profiling", "imf_get_kernel_time", "imf_reset_kernel_times",
-           "imf_penalize_sensitivity_noalloc", "imf_capture_graph", "imf_launch_graph", "imf_autotune"]
+           "imf_penalize_sensitivity_noalloc", "imf_capture_graph", "imf_launch_graph", "imf_autotune",
+           "imf_set_path", "imf_selftest_mma"]
 
 
 class ImfOptions(ctypes.Structure):
@@ -85,6 +86,8 @@ def load(path: str | None = None):
     L.imf_capture_graph.argtypes = [H, P, P, P, P, P, P, P]
     L.imf_launch_graph.argtypes = [H, P]
     L.imf_autotune.argtypes = [H, P, P, P, P, P, ctypes.POINTER(I)]
+    L.imf_set_path.argtypes = [H, I, I]
+    L.imf_selftest_mma.argtypes = [I, I, P, P, P]
     for name in EXPORTS:
         if name not in ("imf_default_options", "imf_destroy", "imf_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -242,6 +245,9 @@ class Imf:
         self._check(self.lib.imf_autotune(self.h, _ptr(rho), _ptr(fixture), _ptr(fb), _ptr(sec), s,
                                           ctypes.byref(best)))
         return best.value
+
+    def set_path(self, tool_id, path):
+        self._check(self.lib.imf_set_path(self.h, tool_id, path))
 
     def sync(self):
         self._check(self.lib.imf_sync_status(self.h))

@@ -30,12 +30,13 @@ namespace {
 
 enum KernelId {
     KID_ROTATE, KID_SPEC, KID_RFFT_FWD, KID_AXIS_FWD, KID_AXIS_INV_MUL, KID_AXIS_INV, KID_IRFFT_THRESH,
-    KID_RECHECK, KID_SWEEP, KID_ERODE, KID_INIT, KID_MAX, KID_FINALIZE, KID_ABSMAX, KID_PENALIZE, KID_COUNT
+    KID_RECHECK, KID_SWEEP, KID_ERODE, KID_INIT, KID_MAX, KID_FINALIZE, KID_ABSMAX, KID_PENALIZE, KID_RHO_HL,
+    KID_DIRECT, KID_COUNT
 };
 const char *kKernelNames[KID_COUNT] = {
     "rotate_resample", "tool_spectrum", "rfft_x_fwd", "fft_axis_fwd", "fft_z_inv_mul", "fft_y_inv",
     "irfft_x_threshold", "recheck_near_threshold", "sweep_dilate", "erode_min", "init", "max_omega0",
-    "finalize", "absmax_omega0", "penalize"};
+    "finalize", "absmax_omega0", "penalize", "rho_hi_lo", "direct_corr_tcgen05"};
 
 struct Tool {
     bool set = false;
@@ -61,6 +62,18 @@ struct Tool {
     int2 *er_runs = nullptr;
     size_t erode_smem = 0;
     long n_rt = 0, n_rk = 0, n_sh = 0;
+    std::vector<int> perm, iperm;        // internal orientation order -> caller's index, and back
+    int path = IMF_FP32_FFT;             // collision path in use
+    bool has_spec = false;               // FFT spectra built
+    // direct tensor-core path
+    bool dir_ok = false;
+    int dG = 0;                          // orientations per group
+    std::vector<int> grp_start, grp_kpad, grp_N;
+    std::vector<long> grp_tap_off, grp_b_off;
+    int *d_taps = nullptr;
+    uint16_t *d_bmat = nullptr;
+    int dlo[3] = {0, 0, 0}, dP[3] = {1, 1, 1};
+    double direct_macs = 0;              // tensor MACs per compute (both BF16 halves)
 };
 
 struct ProfRec {
@@ -78,6 +91,9 @@ struct imf_handle_s {
     // compute work buffers (grow only)
     float2 *rho_spec = nullptr, *X1 = nullptr, *X2 = nullptr;
     size_t rho_spec_n = 0, X1_n = 0, X2_n = 0;
+    uint32_t *rhohl = nullptr;
+    size_t rhohl_n = 0;
+    int nsm = 152;
     float2 *Y1 = nullptr, *Y2 = nullptr;
     float *g = nullptr;
     uint32_t *bits = nullptr;
@@ -308,6 +324,8 @@ void free_tool(imf_handle h, Tool &t)
     dfree(h, t.er_chunks);
     dfree(h, t.er_chunk_start);
     dfree(h, t.er_runs);
+    dfree(h, t.d_taps);
+    dfree(h, t.d_bmat);
     t = Tool();
 }
 
@@ -390,12 +408,102 @@ void plan_erode(const std::vector<int32_t> &sh, const int K[3], std::vector<Erod
     }
 }
 
+// Greedy nearest-neighbour chain over the rotations (Frobenius distance), so that consecutive
+// orientations, and therefore every group of the direct path, have overlapping supports.
+std::vector<int> locality_order(const std::vector<double> &R, int n)
+{
+    std::vector<int> order;
+    std::vector<char> used(n, 0);
+    int cur = 0;
+    for (int step = 0; step < n; ++step) {
+        order.push_back(cur);
+        used[cur] = 1;
+        int best = -1;
+        double bd = 1e300;
+        for (int j = 0; j < n; ++j) {
+            if (used[j]) continue;
+            double d = 0;
+            for (int e = 0; e < 9; ++e) d += (R[9 * cur + e] - R[9 * j + e]) * (R[9 * cur + e] - R[9 * j + e]);
+            if (d < bd) { bd = d; best = j; }
+        }
+        if (best < 0) break;
+        cur = best;
+    }
+    return order;
+}
+
+constexpr size_t kDirectSmemLimit = 220 * 1024;
+
+// byte offset of element (row r, column k) in a K-major canonical tile with R rows
+inline size_t tc_kmajor(int r, int k, int R) { return (size_t)(k >> 3) * (R * 16) + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+// Groups of consecutive orientations, their union tap lists (linear offsets in the padded
+// copy of rho_O) and B matrices (BF16 0/1, K-major canonical layout, N rows).
+bool plan_direct(Tool &t, const int n[3], int vlo[3], int vhi[3], std::vector<int> &taps, std::vector<uint16_t> &bm)
+{
+    for (int c = 0; c < 3; ++c) {
+        t.dlo[c] = std::max(0, t.kmax[c] - vlo[c]);
+        const int hi = std::max(0, vhi[c] - t.kmin[c]);
+        t.dP[c] = n[c] + t.dlo[c] + hi;
+    }
+    const long PX = t.dP[0], PY = t.dP[1];
+    for (int G = std::min(256, (t.n_orient + 15) / 16 * 16); G >= 16; G -= 16) {
+        std::vector<int> gs, gk, gn;
+        std::vector<long> gto, gbo;
+        std::vector<int> tp;
+        std::vector<uint16_t> b;
+        bool fits = true;
+        double macs = 0;
+        for (int o0 = 0; o0 < t.n_orient && fits; o0 += G) {
+            const int nb = std::min(G, t.n_orient - o0);
+            const int N = (nb + 15) / 16 * 16;
+            std::vector<long> uni;
+            for (int i = o0; i < o0 + nb; ++i)
+                for (size_t m = 0; m < t.rt[i].size(); m += 3)
+                    uni.push_back(((long)t.rt[i][m + 2] * PY + t.rt[i][m + 1]) * PX + t.rt[i][m]);
+            std::sort(uni.begin(), uni.end());
+            uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
+            const int kpad = std::max(64, (int)((uni.size() + 63) / 64 * 64));
+            if (direct_smem_bytes(kpad, N) > kDirectSmemLimit) { fits = false; break; }
+            gs.push_back(o0);
+            gk.push_back(kpad);
+            gn.push_back(N);
+            gto.push_back((long)tp.size());
+            gbo.push_back((long)b.size());
+            for (int k = 0; k < kpad; ++k) tp.push_back(k < (int)uni.size() ? (int)uni[k] : 0);
+            const size_t b0 = b.size();
+            b.resize(b0 + (size_t)N * kpad, 0);
+            for (int i = o0; i < o0 + nb; ++i)
+                for (size_t m = 0; m < t.rt[i].size(); m += 3) {
+                    const long off = ((long)t.rt[i][m + 2] * PY + t.rt[i][m + 1]) * PX + t.rt[i][m];
+                    const int k = (int)(std::lower_bound(uni.begin(), uni.end(), off) - uni.begin());
+                    b[b0 + tc_kmajor(i - o0, k, N) / 2] = 0x3F80;    // BF16 1.0
+                }
+            const long tiles = (long)((t.win[0] + 127) / 128) * t.win[1] * t.win[2];
+            macs += 2.0 * tiles * 128.0 * N * kpad;
+        }
+        if (!fits) continue;
+        gs.push_back(t.n_orient);
+        t.dG = G;
+        t.grp_start = gs;
+        t.grp_kpad = gk;
+        t.grp_N = gn;
+        t.grp_tap_off = gto;
+        t.grp_b_off = gbo;
+        t.direct_macs = macs;
+        taps.swap(tp);
+        bm.swap(b);
+        return true;
+    }
+    return false;
+}
+
 imf_status ensure_work(imf_handle h)
 {
     const imf_options &op = h->opt;
     const long N = (long)op.nx * op.ny * op.nz;
-    size_t rs = 0, x1 = 0, x2 = 0, y1 = 0, y2 = 0, gn = 0, bn = 0;
-    int maxo = 1;
+    size_t rs = 0, x1 = 0, x2 = 0, y1 = 0, y2 = 0, gn = 0, bn = 0, hl = 0;
+    int maxo = 1, min_slots = 1;
     for (int i = 0; i < h->n_tools; ++i) {
         const Tool &t = h->tools[i];
         rs = std::max(rs, (size_t)t.P[2] * t.P[1] * t.Hs);
@@ -406,7 +514,12 @@ imf_status ensure_work(imf_handle h)
         gn = std::max(gn, (size_t)t.win[2] * t.win[1] * t.gpx);
         bn = std::max(bn, (size_t)t.win[2] * t.win[1] * t.wpr);
         maxo = std::max(maxo, t.n_orient);
+        if (t.path == IMF_BF16_DIRECT) {
+            hl = std::max(hl, (size_t)t.dP[0] * t.dP[1] * t.dP[2]);
+            min_slots = std::max(min_slots, std::min(t.dG, t.n_orient));
+        }
     }
+    if (hl > h->rhohl_n) { dfree(h, h->rhohl); h->rhohl_n = 0; TRY(dalloc(h, &h->rhohl, hl)); h->rhohl_n = hl; }
     if (!h->f) {
         TRY(dalloc(h, &h->f, (size_t)N));
         h->awords = (op.nx + 31) / 32;
@@ -418,7 +531,7 @@ imf_status ensure_work(imf_handle h)
     if (x1 > h->X1_n) { dfree(h, h->X1, h->X1_n); TRY(dalloc(h, &h->X1, x1)); h->X1_n = x1; }
     if (x2 > h->X2_n) { dfree(h, h->X2, h->X2_n); TRY(dalloc(h, &h->X2, x2)); h->X2_n = x2; }
     int want = op.orient_batch > 0 ? op.orient_batch : 16;
-    want = std::min(want, maxo);
+    want = std::max(std::min(want, maxo), min_slots);
     // per orientation slot: Y1, Y2, g, free bits and its share of the near-threshold list
     const size_t per_slot = y1 * 8 + y2 * 8 + gn * 4 + bn * 4 + (gn / 32 + 1) * sizeof(int2);
     if (op.hbm_budget_bytes) {
@@ -427,7 +540,9 @@ imf_status ensure_work(imf_handle h)
                            (size_t)h->flag_cap * sizeof(int2);
         const size_t fixed = (size_t)(1 << 16) * sizeof(int2);
         const long fit = (long)((have + cur > fixed ? have + cur - fixed : 0) / std::max<size_t>(per_slot, 1));
-        if (fit < 1) return fail(h, IMF_ERR_BUDGET, "one orientation slot needs %zu bytes; budget has %zu", per_slot, have + cur);
+        if (fit < min_slots)
+            return fail(h, IMF_ERR_BUDGET, "%d orientation slots need %zu bytes; budget has %zu", min_slots,
+                        per_slot * min_slots, have + cur);
         want = (int)std::min<long>(want, fit);
     }
     if (y1 > h->Y1_n || y2 > h->Y2_n || gn > h->g_n || bn > h->bits_n || want != h->slots) {
@@ -538,6 +653,7 @@ void imf_destroy(imf_handle h)
     if (h->used_stream) cudaStreamSynchronize(h->last_stream);
     for (auto &t : h->tools) free_tool(h, t);
     dfree(h, h->rho_spec, h->rho_spec_n);
+    dfree(h, h->rhohl);
     dfree(h, h->X1, h->X1_n);
     dfree(h, h->X2, h->X2_n);
     dfree(h, h->Y1, h->Y1_n * h->slots);
@@ -599,8 +715,20 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
     t.size_T = nT;
     t.theta = h->opt.theta_rel * (double)nT;
 
-    // --- rotate and resample on the device (Alg. 1 Rotate)
+    // --- orientation order: nearest-neighbour chain (groups of the direct path stay compact);
+    // results never depend on it, only the grouping of device work does
     std::vector<double> R(9 * (size_t)n_orient);
+    for (int i = 0; i < n_orient; ++i) quat_to_R(quats + 4 * i, &R[9 * i]);
+    t.perm = locality_order(R, n_orient);
+    t.iperm.assign(n_orient, 0);
+    std::vector<double> qint(4 * (size_t)n_orient);
+    for (int i = 0; i < n_orient; ++i) {
+        t.iperm[t.perm[i]] = i;
+        for (int c = 0; c < 4; ++c) qint[4 * i + c] = quats[4 * t.perm[i] + c];
+    }
+    quats = qint.data();
+
+    // --- rotate and resample on the device (Alg. 1 Rotate)
     std::vector<int> box(6 * (size_t)n_orient);
     std::vector<long> boff(n_orient + 1, 0);
     long maxb = 0;
@@ -766,6 +894,23 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
         (st = upload(h, &t.er_chunks, chunks)) || (st = upload(h, &t.er_chunk_start, chst)) ||
         (st = upload(h, &t.er_runs, eruns)))
         return bail(st);
+    // --- direct tensor-core path: groups, union taps, B matrices
+    const int prec = h->opt.precision;
+    if (prec != IMF_FP32_FFT) {
+        std::vector<int> taps;
+        std::vector<uint16_t> bm;
+        t.dir_ok = plan_direct(t, n, vlo, vhi, taps, bm);
+        if (t.dir_ok && ((st = upload(h, &t.d_taps, taps)) || (st = upload(h, &t.d_bmat, bm)))) return bail(st);
+    }
+    if (prec == IMF_BF16_DIRECT && !t.dir_ok)
+        return bail(fail(h, IMF_ERR_INVALID_ARG, "tool too large for the direct tensor-core path"));
+    t.path = prec == IMF_BF16_DIRECT ? IMF_BF16_DIRECT : IMF_FP32_FFT;
+    if (prec == IMF_BF16_DIRECT) {
+        t.set = true;
+        if (tool_id == h->n_tools) h->n_tools++;
+        return IMF_OK;
+    }
+
     // --- tool spectra: conj(FFT(1_RT)) / Ptot (reflection as conjugation, Alg. 1 footnote)
     const size_t per = (size_t)t.P[2] * t.P[1] * t.Hs;
     t.spec_bytes = per * n_orient * sizeof(float2);
@@ -790,8 +935,49 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
     dfree(h, dense, dn); dfree(h, s1, per); dfree(h, s2, per);
     if (st != IMF_OK) return bail(st);
     if (e != cudaSuccess) return bail(fail(h, IMF_ERR_CUDA, "tool spectrum: %s", cudaGetErrorString(e)));
+    t.has_spec = true;
     t.set = true;
     if (tool_id == h->n_tools) h->n_tools++;
+    return IMF_OK;
+}
+
+// near-threshold re-check, sweep and minimum over sharp points for one orientation batch
+imf_status tail_batch(imf_handle h, const Tool &t, const float *rho, const uint8_t *fix, int o0, int nb, cudaStream_t s)
+{
+    const imf_options &op = h->opt;
+    int *fcount = h->dev_small + 1;
+    const long gso = (long)t.win[2] * t.win[1] * t.gpx;
+    const long bso = (long)t.win[2] * t.win[1] * t.wpr;
+    if (op.recheck) {
+        RecheckArgs a{};
+        a.flags = h->flags; a.count = fcount; a.cap = h->flag_cap; a.rho = rho; a.fix = fix;
+        a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.rt_off = t.rt_off; a.rt_start = t.rt_start;
+        a.wx = t.win[0]; a.wy = t.win[1]; a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2];
+        a.g = h->g; a.g_sy = t.gpx; a.g_sz = (long)t.win[1] * t.gpx; a.g_so = gso;
+        a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
+        a.theta = t.theta; a.orient_base = o0;
+        Launch L(h, KID_RECHECK, s);
+        launch_recheck_blocks(a, 152 * 8, s);
+    }
+    {
+        SweepArgs a{};
+        a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
+        a.iv = t.iv; a.iv_start = t.iv_start; a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.awords = h->awords;
+        a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2]; a.orient_base = o0; a.nb = nb; a.A = h->A;
+        Launch L(h, KID_SWEEP, s);
+        launch_sweep2(a, s);
+    }
+    {
+        Erode2Args a{};
+        a.g = h->g; a.g_so = gso; a.gpx = t.gpx; a.gpy = t.win[1];
+        a.wx = t.win[0]; a.wy = t.win[1]; a.wz = t.win[2];
+        a.chunks = t.er_chunks; a.chunk_start = t.er_chunk_start; a.runs = t.er_runs;
+        a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.orient_base = o0; a.nb = nb; a.f = h->f;
+        Launch L(h, KID_ERODE, s);
+        launch_erode2(a, t.erode_smem, s);
+    }
+    h->last_batch_base = o0;
+    h->last_batch_n = nb;
     return IMF_OK;
 }
 
@@ -804,6 +990,9 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
     if (!h->f || !h->A || !h->dev_small || !h->flags || !h->Y1 || !h->Y2 || !h->g || !h->bits || !h->rho_spec ||
         !h->X1 || !h->X2 || h->slots < 1)
         return fail(h, IMF_ERR_OOM, "work buffers are not allocated");
+    for (int ti = 0; ti < h->n_tools; ++ti)
+        if (h->tools[ti].path == IMF_BF16_DIRECT && (!h->rhohl || h->slots < std::min(h->tools[ti].dG, h->tools[ti].n_orient)))
+            return fail(h, IMF_ERR_OOM, "direct-path buffers are not allocated");
     h->last_stream = s;
     h->used_stream = true;
     int *status = h->dev_small, *fcount = h->dev_small + 1;
@@ -817,6 +1006,38 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
     CU(cudaMemsetAsync(h->dev_small + 4, 0, sizeof(int), s));
     for (int ti = 0; ti < h->n_tools; ++ti) {
         const Tool &t = h->tools[ti];
+        const long gso_ = (long)t.win[2] * t.win[1] * t.gpx;
+        const long bso_ = (long)t.win[2] * t.win[1] * t.wpr;
+        if (t.path == IMF_BF16_DIRECT) {
+            {
+                Launch L(h, KID_RHO_HL, s);
+                launch_rho_hl(rho, fix, op.nx, op.ny, op.nz, t.dlo[0], t.dlo[1], t.dlo[2], t.dP[0], t.dP[1], t.dP[2],
+                              h->rhohl, s);
+            }
+            for (size_t gi = 0; gi + 1 < t.grp_start.size(); ++gi) {
+                const int o0 = t.grp_start[gi], nb = t.grp_start[gi + 1] - o0;
+                if (op.recheck) CU(cudaMemsetAsync(fcount, 0, sizeof(int), s));
+                {
+                    DirectArgs a{};
+                    a.rhohl = h->rhohl; a.PX = t.dP[0]; a.PY = t.dP[1];
+                    a.lox = t.dlo[0]; a.loy = t.dlo[1]; a.loz = t.dlo[2];
+                    a.tapoff = t.d_taps + t.grp_tap_off[gi]; a.kpad = t.grp_kpad[gi];
+                    a.bmat = t.d_bmat + t.grp_b_off[gi]; a.N = t.grp_N[gi]; a.nb = nb;
+                    a.wx = t.win[0]; a.wy = t.win[1]; a.wz = t.win[2];
+                    a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2]; a.ntiles_x = (t.win[0] + 127) / 128;
+                    a.g = h->g; a.g_sy = t.gpx; a.g_sz = (long)t.win[1] * t.gpx; a.g_so = gso_;
+                    a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso_;
+                    a.theta = (float)t.theta; a.band = (float)t.band; a.flag = op.recheck;
+                    a.flags = h->flags; a.flag_count = fcount; a.flag_total = h->dev_small + 4;
+                    a.flag_cap = h->flag_cap; a.status = status; a.orient_base = o0;
+                    Launch L(h, KID_DIRECT, s);
+                    launch_direct(a, h->nsm, s);
+                }
+                TRY(tail_batch(h, t, rho, fix, o0, nb, s));
+                h->last_tool = ti;
+            }
+            continue;
+        }
         TRY(forward_real_3d(h, t, rho, fix, op.nx, op.ny, op.nz, h->X1, h->X2, h->rho_spec, 1.f, 0, s));
         const long y1so = (long)t.win[2] * t.P[1] * t.Hs;
         const long y2so = (long)t.win[2] * t.win[1] * t.Hs;
@@ -856,34 +1077,7 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
                 Launch L(h, KID_IRFFT_THRESH, s);
                 launch_irfft_threshold(a, nb, s);
             }
-            if (op.recheck) {
-                RecheckArgs a{};
-                a.flags = h->flags; a.count = fcount; a.cap = h->flag_cap; a.rho = rho; a.fix = fix;
-                a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.rt_off = t.rt_off; a.rt_start = t.rt_start;
-                a.wx = t.win[0]; a.wy = t.win[1]; a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2];
-                a.g = h->g; a.g_sy = t.gpx; a.g_sz = (long)t.win[1] * t.gpx; a.g_so = gso;
-                a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
-                a.theta = t.theta; a.orient_base = o0;
-                Launch L(h, KID_RECHECK, s);
-                launch_recheck_blocks(a, 152 * 8, s);
-            }
-            {
-                SweepArgs a{};
-                a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
-                a.iv = t.iv; a.iv_start = t.iv_start; a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.awords = h->awords;
-                a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2]; a.orient_base = o0; a.nb = nb; a.A = h->A;
-                Launch L(h, KID_SWEEP, s);
-                launch_sweep2(a, s);
-            }
-            {
-                Erode2Args a{};
-                a.g = h->g; a.g_so = gso; a.gpx = t.gpx; a.gpy = t.win[1];
-                a.wx = t.win[0]; a.wy = t.win[1]; a.wz = t.win[2];
-                a.chunks = t.er_chunks; a.chunk_start = t.er_chunk_start; a.runs = t.er_runs;
-                a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.orient_base = o0; a.nb = nb; a.f = h->f;
-                Launch L(h, KID_ERODE, s);
-                launch_erode2(a, t.erode_smem, s);
-            }
+            TRY(tail_batch(h, t, rho, fix, o0, nb, s));
             h->last_batch_base = o0;
             h->last_batch_n = nb;
             h->last_tool = ti;
@@ -1047,10 +1241,76 @@ imf_status imf_autotune(imf_handle h, const float *rho_omega, const uint8_t *fix
     if (st != IMF_OK) return st;
     h->opt.orient_batch = best_nb;
     TRY(ensure_work(h));
+    // collision path: time the direct tensor-core path against the FFT path where both exist
+    for (int ti = 0; ti < h->n_tools; ++ti) {
+        Tool &t = h->tools[ti];
+        if (!(t.dir_ok && t.has_spec) || h->opt.precision != IMF_AUTO) continue;
+        float ms[2] = {1e30f, 1e30f};
+        const int paths[2] = {IMF_FP32_FFT, IMF_BF16_DIRECT};
+        for (int p = 0; p < 2; ++p) {
+            t.path = paths[p];
+            imf_status s2 = imf_compute(h, rho_omega, fixture, imf_bar, secluded, nullptr, nullptr, cuda_stream);
+            if (s2 != IMF_OK) continue;
+            cudaEvent_t a0, a1;
+            cudaEventCreate(&a0);
+            cudaEventCreate(&a1);
+            cudaEventRecord(a0, s);
+            s2 = imf_compute(h, rho_omega, fixture, imf_bar, secluded, nullptr, nullptr, cuda_stream);
+            cudaEventRecord(a1, s);
+            if (cudaEventSynchronize(a1) == cudaSuccess && s2 == IMF_OK) cudaEventElapsedTime(&ms[p], a0, a1);
+            cudaEventDestroy(a0);
+            cudaEventDestroy(a1);
+        }
+        t.path = ms[1] < ms[0] ? IMF_BF16_DIRECT : IMF_FP32_FFT;
+        TRY(ensure_work(h));
+    }
     if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
     if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
     if (best) *best = best_nb;
     return IMF_OK;
+}
+
+imf_status imf_set_path(imf_handle h, int tool_id, int path)
+{
+    if (!h || tool_id < 0 || tool_id >= h->n_tools || !h->tools[tool_id].set) return IMF_ERR_INVALID_ARG;
+    Tool &t = h->tools[tool_id];
+    if (path == IMF_BF16_DIRECT && !t.dir_ok)
+        return fail(h, IMF_ERR_INVALID_ARG, "the direct path is not available for tool %d", tool_id);
+    if (path == IMF_FP32_FFT && !t.has_spec)
+        return fail(h, IMF_ERR_INVALID_ARG, "no FFT spectra for tool %d (created with IMF_BF16_DIRECT)", tool_id);
+    if (path != IMF_BF16_DIRECT && path != IMF_FP32_FFT) return IMF_ERR_INVALID_ARG;
+    if (h->used_stream) CU(cudaStreamSynchronize(h->last_stream));
+    t.path = path;
+    if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    return IMF_OK;
+}
+
+imf_status imf_selftest_mma(int N, int K, const uint16_t *A, const uint16_t *B, float *D)
+{
+    if (!A || !B || !D) return IMF_ERR_INVALID_ARG;
+    uint16_t *dA = nullptr, *dB = nullptr;
+    float *dD = nullptr;
+    int *dst = nullptr;
+    int hst = 0;
+    imf_status st = IMF_OK;
+    if (cudaMalloc(&dA, (size_t)128 * K * 2) != cudaSuccess || cudaMalloc(&dB, (size_t)N * K * 2) != cudaSuccess ||
+        cudaMalloc(&dD, (size_t)128 * N * 4) != cudaSuccess || cudaMalloc(&dst, sizeof(int)) != cudaSuccess) {
+        st = IMF_ERR_OOM;
+    } else {
+        cudaMemcpy(dA, A, (size_t)128 * K * 2, cudaMemcpyHostToDevice);
+        cudaMemcpy(dB, B, (size_t)N * K * 2, cudaMemcpyHostToDevice);
+        cudaMemset(dst, 0, sizeof(int));
+        if (run_mma_selftest(dA, dB, dD, N, K, dst, 0) != 0) st = IMF_ERR_INVALID_ARG;
+        else if (cudaDeviceSynchronize() != cudaSuccess) st = IMF_ERR_CUDA;
+        else {
+            cudaMemcpy(D, dD, (size_t)128 * N * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(&hst, dst, sizeof(int), cudaMemcpyDeviceToHost);
+            if (hst) st = (imf_status)hst;
+        }
+    }
+    cudaFree(dA); cudaFree(dB); cudaFree(dD); cudaFree(dst);
+    return st;
 }
 
 imf_status imf_sync_status(imf_handle h)
@@ -1083,7 +1343,7 @@ imf_status imf_get_tool_info(imf_handle h, int tool_id, imf_tool_info *out)
     out->n_rt = t.n_rt;
     out->n_rk = t.n_rk;
     out->n_sharp = t.n_sh;
-    out->path = IMF_FP32_FFT;
+    out->path = t.path;
     out->spectra_bytes = t.spec_bytes;
     return IMF_OK;
 }
@@ -1093,7 +1353,8 @@ imf_status imf_get_offsets(imf_handle h, int tool_id, int orient, int which, int
     if (!h || !n || tool_id < 0 || tool_id >= h->n_tools || !h->tools[tool_id].set) return IMF_ERR_INVALID_ARG;
     const Tool &t = h->tools[tool_id];
     if (orient < 0 || orient >= t.n_orient || which < 0 || which > 2) return IMF_ERR_INVALID_ARG;
-    const std::vector<int32_t> &v = which == 0 ? t.rt[orient] : which == 1 ? t.rk[orient] : t.sh[orient];
+    const int io = t.iperm[orient];
+    const std::vector<int32_t> &v = which == 0 ? t.rt[io] : which == 1 ? t.rk[io] : t.sh[io];
     *n = (long)v.size() / 3;
     if (out) {
         if (cap < *n) return fail(h, IMF_ERR_INVALID_ARG, "capacity %ld < %ld", cap, *n);
@@ -1114,7 +1375,7 @@ imf_status imf_get_last_g(imf_handle h, int slot, float *g_out, long cap, int *o
     if (!h || h->last_tool < 0 || slot < 0 || slot >= h->last_batch_n) return IMF_ERR_INVALID_ARG;
     const Tool &t = h->tools[h->last_tool];
     const long n = (long)t.win[2] * t.win[1] * t.gpx;
-    if (orient_out) *orient_out = h->last_batch_base + slot;
+    if (orient_out) *orient_out = t.perm[h->last_batch_base + slot];
     if (!g_out) return IMF_OK;
     if (cap < n) return fail(h, IMF_ERR_INVALID_ARG, "capacity %ld < %ld", cap, n);
     if (h->used_stream) CU(cudaStreamSynchronize(h->last_stream));

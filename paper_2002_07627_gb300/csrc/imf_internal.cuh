@@ -172,6 +172,35 @@ struct Erode2Args {
 };
 void launch_erode2(const Erode2Args &a, size_t smem, cudaStream_t s);
 
+// Direct collision convolution on the tensor cores (direct_tc.cu).
+struct DirectArgs {
+    const uint32_t *rhohl;       // padded rho_O as (hi | lo << 16) BF16 pairs
+    int PX, PY;                  // padded pitches
+    int lox, loy, loz;           // padding before the grid along x, y, z
+    const int *tapoff;           // union taps of the group as linear offsets in the padded array
+    int kpad;                    // taps, padded to a multiple of 64 (padding taps have B = 0)
+    const uint16_t *bmat;        // B [N x kpad] BF16 0/1 in the K-major canonical layout
+    int N, nb;                   // MMA N (multiple of 16) and orientations in the group
+    int wx, wy, wz, kx, ky, kz;  // translation window and kmax (t = window index - kmax)
+    int ntiles_x;                // ceil(wx / 128)
+    float *g;
+    long g_sy, g_sz, g_so;
+    uint32_t *bits;
+    long b_sy, b_sz, b_so;
+    float theta, band;
+    int flag;
+    int2 *flags;
+    int *flag_count, *flag_total;
+    int flag_cap;
+    int *status;
+    int orient_base;
+};
+size_t direct_smem_bytes(int kpad, int N);
+void launch_rho_hl(const float *rho, const uint8_t *fix, int nx, int ny, int nz, int lox, int loy, int loz, int PX,
+                   int PY, int PZ, uint32_t *out, cudaStream_t s);
+void launch_direct(const DirectArgs &a, int nsm, cudaStream_t s);
+int run_mma_selftest(const uint16_t *A, const uint16_t *B, float *D, int N, int K, int *status, cudaStream_t s);
+
 void launch_fill_f32(float *p, float v, long n, cudaStream_t s);
 void launch_max_omega0(const float *f, const uint8_t *fix, long n, unsigned *maxbits, cudaStream_t s);
 struct FinalizeArgs {
