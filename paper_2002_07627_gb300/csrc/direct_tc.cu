@@ -8,10 +8,11 @@
 // orientations of the group, accumulating in TMEM (FP32). rho_O enters as two BF16 terms
 // rho_O = hi + lo (the binary tool indicator is exact in BF16), so D = A_hi B^T + A_lo B^T and the
 // input error is below 2^-16 of rho_O. B is loaded once per block by a bulk (TMA) copy in
-// the K-major canonical layout; A is built in shared memory, chunk by chunk, by four producer
-// warps from a padded copy of rho_O that holds (hi, lo) in one 32-bit word; one thread issues
-// the MMAs; the same four warps read D back with tcgen05.ld and write g, the free bits and the
-// near-threshold list in the layout of the FFT path. Every mbarrier wait is bounded; on a
+// the K-major canonical layout; A is built in shared memory, chunk by chunk, by eight producer
+// warps (two threads per tile row, half a chunk each) from a padded copy of rho_O that holds
+// (hi, lo) in one 32-bit word; one thread issues the MMAs; the same eight warps read D back
+// with tcgen05.ld (warp w reads TMEM lanes 32 (w mod 4) .. + 31 and half of the columns) and
+// write g, the free bits and the near-threshold list in the layout of the FFT path. Every mbarrier wait is bounded; on a
 // timeout the block records IMF_ERR_TIMEOUT, stops, and still frees its TMEM.
 #include <cfloat>
 #include <cuda_bf16.h>
@@ -25,7 +26,8 @@ namespace {
 
 constexpr int kDM = 128;          // translations per tile (MMA M)
 constexpr int kDKC = 64;          // taps per chunk
-constexpr int kDThreads = 160;    // 4 producer / epilogue warps + 1 MMA warp
+constexpr int kDProd = 256;       // 8 producer / epilogue warps: two threads per tile row
+constexpr int kDThreads = kDProd + 32;   // + 1 MMA warp
 constexpr uint32_t kStageBytes = kDM * kDKC * 2;   // one BF16 operand chunk
 
 __device__ __forceinline__ uint16_t bf16_bits_rn(float x)
@@ -61,7 +63,7 @@ __global__ void rho_hl_kernel(const float *rho, const uint8_t *fix, int nx, int 
 // ---------------------------------------------------------------------------------------
 // the direct kernel
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kDThreads, 1) direct_corr_kernel(DirectArgs a)
+__global__ void __launch_bounds__(kDThreads, 2) direct_corr_kernel(DirectArgs a)
 {
     extern __shared__ __align__(1024) uint8_t dsm[];
     const uint32_t bbytes = (uint32_t)a.kpad * a.N * 2;
@@ -80,23 +82,23 @@ __global__ void __launch_bounds__(kDThreads, 1) direct_corr_kernel(DirectArgs a)
 
     if (threadIdx.x == 0) {
         s_abort = 0;
-        tc::mbar_init(&full[0], 128);
-        tc::mbar_init(&full[1], 128);
+        tc::mbar_init(&full[0], kDProd);
+        tc::mbar_init(&full[1], kDProd);
         tc::mbar_init(&empty[0], 1);
         tc::mbar_init(&empty[1], 1);
         tc::mbar_init(bload, 1);
         tc::mbar_init(dfull, 1);
-        tc::mbar_init(dempty, 128);
+        tc::mbar_init(dempty, kDProd);
         tc::mbar_init(bars + 7, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == 4) tc::tmem_alloc(tmem_slot, ncols);
+    if (warp == 8) tc::tmem_alloc(tmem_slot, ncols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 4) {
+    if (warp == 8) {
         // ------------------------------------------------------------- MMA issuer
         if (lane == 0) {
             tc::mbar_expect_tx(bload, bbytes);
@@ -141,7 +143,8 @@ __global__ void __launch_bounds__(kDThreads, 1) direct_corr_kernel(DirectArgs a)
         __syncwarp();
     } else {
         // ------------------------------------------------------- producers / epilogue
-        const int m = threadIdx.x;                  // row of the tile = TMEM lane
+        const int m = threadIdx.x & (kDM - 1);      // row of the tile = TMEM lane
+        const int half = threadIdx.x >> 7;          // which half of each chunk / of the columns
         long gc = 0;
         int tcount = 0;
         bool ok = true;
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(kDThreads, 1) direct_corr_kernel(DirectArgs a)
                 uint8_t *Ahi = Ast + (2 * s) * kStageBytes, *Alo = Ahi + kStageBytes;
                 const int *taps = a.tapoff + c * kDKC;
 #pragma unroll 4
-                for (int kk = 0; kk < kDKC; kk += 2) {
+                for (int kk = half * (kDKC / 2); kk < (half + 1) * (kDKC / 2); kk += 2) {
                     const uint32_t w0 = __ldg(a.rhohl + pbase + __ldg(taps + kk));
                     const uint32_t w1 = __ldg(a.rhohl + pbase + __ldg(taps + kk + 1));
                     const uint32_t off = tc::kmajor_offset(m, kk, kDM);
@@ -173,11 +176,12 @@ __global__ void __launch_bounds__(kDThreads, 1) direct_corr_kernel(DirectArgs a)
             if (!ok) break;
             if (!(ok = tc::mbar_wait(dfull, tcount & 1))) break;
             tc::fence_after();
-            // epilogue: D row m, columns = orientations of the group
+            // epilogue: D row m, this warp's half of the columns (= orientations of the group)
             const bool valid = x < a.wx;
-            for (int n0 = 0; n0 < a.N; n0 += 8) {
+            const int q = warp & 3;
+            for (int n0 = half * (a.N / 2); n0 < (half + 1) * (a.N / 2); n0 += 8) {
                 float v[8];
-                tc::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)n0, v);
+                tc::tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)n0, v);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int n = n0 + j;
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(kDThreads, 1) direct_corr_kernel(DirectArgs a)
                     if (valid) g[x] = gv;
                     const unsigned fb = __ballot_sync(0xffffffffu, valid && gv <= a.theta);
                     uint32_t *bw = a.bits + (long)n * a.b_so + (long)z * a.b_sz + (long)y * a.b_sy;
-                    if (lane == 0 && xs * kDM + warp * 32 < a.wx) bw[(xs * kDM + warp * 32) >> 5] = fb;
+                    if (lane == 0 && xs * kDM + q * 32 < a.wx) bw[(xs * kDM + q * 32) >> 5] = fb;
                     if (a.flag) {
                         const bool near = valid && fabsf(gv - a.theta) <= a.band;
                         const unsigned nm = __ballot_sync(0xffffffffu, near);
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(kDThreads, 1) direct_corr_kernel(DirectArgs a)
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 4) tc::tmem_dealloc(tmem, ncols);
+    if (warp == 8) tc::tmem_dealloc(tmem, ncols);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -305,7 +309,7 @@ void launch_direct(const DirectArgs &a, int nsm, cudaStream_t s)
     const size_t smem = direct_smem_bytes(a.kpad, a.N);
     cudaFuncSetAttribute(direct_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int ntiles = a.ntiles_x * a.wy * a.wz;
-    const int grid = ntiles < nsm ? ntiles : nsm;
+    const int grid = ntiles < 2 * nsm ? ntiles : 2 * nsm;
     direct_corr_kernel<<<grid, kDThreads, smem, s>>>(a);
 }
 
