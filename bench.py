@@ -201,6 +201,18 @@ def oracle_cores():
     return int(n) if n else os.cpu_count()
 
 
+def reduce_max(value: float, device) -> float:
+    """Maximum of `value` over all ranks (the step time of a weak-scaling run is the slowest
+    rank's); the identity without torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -381,11 +393,8 @@ def run_ours(args):
         times = timed_steps(args.steps)
     imf.sync()
     launches = imf.stats().launches - l0
-    total_ms = sum(times)
+    total_ms = reduce_max(sum(times), dev)
     if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
     value = ws * nG * n_orient / (ms_per_step * 1e-3)
@@ -458,11 +467,7 @@ def run_ours(args):
                                       ob.data_ptr(), osec.data_ptr(), None, None, stream.cuda_stream)
             et.append(time.perf_counter() - t0)
             assert st == 0, imf.lib.imf_last_error(imf.h)
-        e_s = statistics.mean(et)
-        if ws > 1:
-            t = torch.tensor([e_s], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_s = float(t.item())
+        e_s = reduce_max(statistics.mean(et), dev)
         e2e = {"value": ws * nG * n_orient / e_s, "unit": UNIT, "h2d_bytes_per_step": nG * 4 + (nG if hf is not None else 0),
                "d2h_bytes_per_step": nG * 4 + nG, "entry_point": "imf_compute_host (pinned host buffers)"}
 
