@@ -162,13 +162,21 @@ __global__ void __launch_bounds__(kDThreads, 2) direct_corr_kernel(DirectArgs a)
                 if (*((volatile int *)&s_abort)) { ok = false; break; }
                 uint8_t *Ahi = Ast + (2 * s) * kStageBytes, *Alo = Ahi + kStageBytes;
                 const int *taps = a.tapoff + c * kDKC;
-#pragma unroll 4
-                for (int kk = half * (kDKC / 2); kk < (half + 1) * (kDKC / 2); kk += 2) {
-                    const uint32_t w0 = __ldg(a.rhohl + pbase + __ldg(taps + kk));
-                    const uint32_t w1 = __ldg(a.rhohl + pbase + __ldg(taps + kk + 1));
+                // 8 consecutive taps per step: one 16-byte store per operand (a warp writes 512
+                // contiguous bytes of the canonical layout, no bank conflicts)
+#pragma unroll
+                for (int kk = half * (kDKC / 2); kk < (half + 1) * (kDKC / 2); kk += 8) {
+                    uint32_t w[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) w[e] = __ldg(a.rhohl + pbase + __ldg(taps + kk + e));
+                    uint4 vh, vl;
+                    vh.x = (w[0] & 0xffffu) | (w[1] << 16); vl.x = (w[0] >> 16) | (w[1] & 0xffff0000u);
+                    vh.y = (w[2] & 0xffffu) | (w[3] << 16); vl.y = (w[2] >> 16) | (w[3] & 0xffff0000u);
+                    vh.z = (w[4] & 0xffffu) | (w[5] << 16); vl.z = (w[4] >> 16) | (w[5] & 0xffff0000u);
+                    vh.w = (w[6] & 0xffffu) | (w[7] << 16); vl.w = (w[6] >> 16) | (w[7] & 0xffff0000u);
                     const uint32_t off = tc::kmajor_offset(m, kk, kDM);
-                    *(uint32_t *)(Ahi + off) = (w0 & 0xffffu) | (w1 << 16);
-                    *(uint32_t *)(Alo + off) = (w0 >> 16) | (w1 & 0xffff0000u);
+                    *(uint4 *)(Ahi + off) = vh;
+                    *(uint4 *)(Alo + off) = vl;
                 }
                 tc::fence_async_smem();
                 tc::mbar_arrive(&full[s]);

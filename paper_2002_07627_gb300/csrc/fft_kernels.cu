@@ -18,20 +18,37 @@ namespace {
 // Stockham stages over a tile of W interleaved pencils (element (w, j) at w + j * sj);
 // W is a power of two so q -> (w, jb) is a mask and a shift, and jb / Ns uses the plan's
 // exact reciprocal.
+template <int S, int R, int LOGW>
+__device__ __forceinline__ void stage_loop(const float2 *src, float2 *dst, int L, int Ns, int sj, const float2 *tw,
+                                           unsigned mul, int step)
+{
+    constexpr int W = 1 << LOGW;
+    const int nb = (L / R) << LOGW;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+        const int w = q & (W - 1), jb = q >> LOGW;
+        stockham_bfly<S, R>(src, dst, w, jb, L, Ns, 1, sj, tw, (int)fast_div((unsigned)jb, mul), step);
+    }
+}
+
+// Stockham stages over a tile of W interleaved pencils (element (w, j) at w + j * sj);
+// W is a power of two so q -> (w, jb) is a mask and a shift, jb / Ns uses the plan's exact
+// reciprocal, and the radix dispatch happens once per stage.
 template <int S, int LOGW>
 __device__ void run_stages(const FftPlan &plan, float2 *&src, float2 *&dst, int sj, const float2 *tw)
 {
-    constexpr int W = 1 << LOGW;
     const int L = plan.L;
     int Ns = 1;
     for (int s = 0; s < plan.nrad; ++s) {
         const int R = plan.rad[s];
-        const int nb = (L / R) << LOGW;
         const unsigned mul = plan.mul[s];
         const int step = plan.step[s];
-        for (int q = threadIdx.x; q < nb; q += blockDim.x) {
-            const int w = q & (W - 1), jb = q >> LOGW;
-            stockham_dispatch<S>(R, src, dst, w, jb, L, Ns, 1, sj, tw, (int)fast_div((unsigned)jb, mul), step);
+        switch (R) {
+        case 2: stage_loop<S, 2, LOGW>(src, dst, L, Ns, sj, tw, mul, step); break;
+        case 3: stage_loop<S, 3, LOGW>(src, dst, L, Ns, sj, tw, mul, step); break;
+        case 4: stage_loop<S, 4, LOGW>(src, dst, L, Ns, sj, tw, mul, step); break;
+        case 5: stage_loop<S, 5, LOGW>(src, dst, L, Ns, sj, tw, mul, step); break;
+        case 7: stage_loop<S, 7, LOGW>(src, dst, L, Ns, sj, tw, mul, step); break;
+        default: stage_loop<S, 8, LOGW>(src, dst, L, Ns, sj, tw, mul, step); break;
         }
         __syncthreads();
         float2 *t = src; src = dst; dst = t;

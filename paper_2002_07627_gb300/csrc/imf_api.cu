@@ -255,6 +255,41 @@ int next_smooth(int n)
     return n;
 }
 
+// Relative cost of one length-L pass: L times the summed per-point cost of its radix stages
+// (radix-8 and radix-4 butterflies are the cheapest per point, 7 and 5 the dearest).
+double fft_cost(int L)
+{
+    FftPlan p;
+    if (!make_plan(L, &p)) return 1e300;
+    double c = 0;
+    for (int s = 0; s < p.nrad; ++s) {
+        switch (p.rad[s]) {
+        case 8: c += 1.0; break;
+        case 4: c += 0.9; break;
+        case 2: c += 0.8; break;
+        case 3: c += 1.0; break;
+        case 5: c += 1.25; break;
+        default: c += 1.45; break;
+        }
+    }
+    return L * c;
+}
+
+// FFT plan choice: among smooth lengths from the minimum up to 12 % above it, the cheapest
+// by fft_cost (a padded transform is correct for any length at or above the minimum).
+int best_smooth(int n)
+{
+    const int n0 = next_smooth(n);
+    int best = n0;
+    double bc = fft_cost(n0);
+    for (int m = n0 + 1; m <= n0 + n0 / 8; ++m) {
+        if (!is_smooth(m)) continue;
+        const double c = fft_cost(m);
+        if (c < bc) { bc = c; best = m; }
+    }
+    return best;
+}
+
 // R from the unit quaternion (w, x, y, z), normalised first; row major, v = R u.
 void quat_to_R(const double *q, double *R)
 {
@@ -831,10 +866,10 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
             return fail(h, IMF_ERR_INVALID_ARG, "rotated tool offsets exceed +-511 voxels");
         }
     }
-    t.M = next_smooth((req[0] + 1) / 2);
+    t.M = best_smooth((req[0] + 1) / 2);
     t.P[0] = 2 * t.M;
-    t.P[1] = next_smooth(req[1]);
-    t.P[2] = next_smooth(req[2]);
+    t.P[1] = best_smooth(req[1]);
+    t.P[2] = best_smooth(req[2]);
     t.Hx = t.M + 1;
     t.Hs = (t.Hx + 1) & ~1;
     t.gpx = (t.win[0] + 3) & ~3;
