@@ -85,17 +85,23 @@ __global__ void __launch_bounds__(kErThreads, 2) erode2_kernel(Erode2Args a)
             __syncthreads();
             // asynchronous fill, one warp per tile row; cells outside the window (read only by
             // outputs beyond the grid, which are masked) are zero-filled
+            const bool xin = gx0 + txh <= a.wx;
             for (int r = warp; r < nrow; r += kErThreads / 32) {
                 const int iy = r % tyh, iz = r / tyh;
                 const int gy = gy0 + iy, gz = gz0 + iz;
                 const bool rowok = gy < a.wy && gz < a.wz;
-                const float *src = g + ((long)gz * a.gpy + gy) * a.gpx;
+                const float *src = g + ((long)gz * a.gpy + gy) * a.gpx + gx0;
                 const uint32_t drow = sbase + 4u * (uint32_t)(iz * pz + iy * py);
-                for (int ix = lane; ix < txh; ix += 32) {
-                    const int gx = gx0 + ix;
-                    const bool ok = rowok && gx < a.wx;
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(drow + 4u * ix),
-                                 "l"(ok ? src + gx : g), "r"(ok ? 4 : 0));
+                if (rowok && xin) {
+                    // whole row inside the window: plain 4-byte copies
+                    for (int ix = lane; ix < txh; ix += 32)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(drow + 4u * ix), "l"(src + ix));
+                } else {
+                    for (int ix = lane; ix < txh; ix += 32) {
+                        const bool ok = rowok && gx0 + ix < a.wx;
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(drow + 4u * ix),
+                                     "l"(ok ? src + ix : g), "r"(ok ? 4 : 0));
+                    }
                 }
             }
             for (int q = threadIdx.x; q < nrun; q += kErThreads) sruns[q] = a.runs[run0 + q];
