@@ -71,6 +71,9 @@ typedef struct {
     double recheck_band;     /* band half-width in voxel volumes; <= 0 picks a default         */
     int orient_batch;        /* orientations per batch of device work; 0 = 16 (fewer if budget) */
     size_t hbm_budget_bytes; /* cap on library-owned device memory; 0 = no cap (App. B)        */
+    int erode_groups;        /* orientation groups per tile of the minimum over sharp points
+                                (work-unit granularity only; the result does not depend on it);
+                                0 = chosen from the grid and the SM count                      */
 } imf_options;
 
 /* Fill *opt with the defaults above (grid 0x0x0, which imf_create rejects). */

@@ -32,7 +32,7 @@ class ImfOptions(ctypes.Structure):
                 ("voxel", ctypes.c_double), ("lambda_", ctypes.c_double), ("tau", ctypes.c_double),
                 ("theta_rel", ctypes.c_double), ("precision", ctypes.c_int), ("recheck", ctypes.c_int),
                 ("recheck_band", ctypes.c_double), ("orient_batch", ctypes.c_int),
-                ("hbm_budget_bytes", ctypes.c_size_t)]
+                ("hbm_budget_bytes", ctypes.c_size_t), ("erode_groups", ctypes.c_int)]
 
 
 class ImfToolInfo(ctypes.Structure):
@@ -139,7 +139,7 @@ class Imf:
     """One design grid on the current CUDA device; mirrors the C ABI one-to-one."""
 
     def __init__(self, shape_zyx, lam=0.01, tau=0.5, theta_rel=0.01, precision=IMF_AUTO, recheck=True,
-                 recheck_band=0.0, orient_batch=0, hbm_budget_bytes=0, voxel=1.0):
+                 recheck_band=0.0, orient_batch=0, hbm_budget_bytes=0, voxel=1.0, erode_groups=0):
         self.lib = load()
         opt = ImfOptions()
         self.lib.imf_default_options(ctypes.byref(opt))
@@ -148,6 +148,7 @@ class Imf:
         opt.voxel, opt.lambda_, opt.tau, opt.theta_rel = voxel, lam, tau, theta_rel
         opt.precision, opt.recheck, opt.recheck_band = precision, int(recheck), recheck_band
         opt.orient_batch, opt.hbm_budget_bytes = orient_batch, hbm_budget_bytes
+        opt.erode_groups = erode_groups
         self.shape = (nz, ny, nx)
         self.opt = opt
         h = ctypes.c_void_p()

@@ -10,6 +10,12 @@
 // the shared-memory budget; the run descriptors of a chunk are staged next to the tile. The
 // row pitch is odd and the plane pitch is chosen so that the 32 lanes of a warp (8 rows x 4
 // planes) read 32 different banks.
+//
+// The orientations of a launch may be split into groups, one block per (tile, group), so that
+// the grid holds several waves of short units and the uneven cost of the tiles (pruned tiles
+// finish early) does not leave SMs idle at the end. Groups of one tile then merge into f with
+// an integer atomic minimum, which orders non-negative floats (every g >= 0; -0 is mapped to +0
+// first) exactly as the float minimum does, so the result does not depend on the split.
 #include <cfloat>
 
 #include "imf_internal.cuh"
@@ -54,7 +60,10 @@ __global__ void __launch_bounds__(kErThreads, 2) erode2_kernel(Erode2Args a)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // warp = tx (8) x tz_hi (2); lane = ty (8) x tz_lo (4)
     const int ty = lane & 7, tz = ((warp >> 3) << 2) | (lane >> 3), tx = warp & 7;
-    const int X0 = blockIdx.x * kErTX, Y0 = blockIdx.y * kErTY, Z0 = blockIdx.z * kErTZ;
+    const int tiles_z = (a.nz + kErTZ - 1) / kErTZ;
+    const int grp = blockIdx.z / tiles_z;
+    const int X0 = blockIdx.x * kErTX, Y0 = blockIdx.y * kErTY, Z0 = (blockIdx.z - grp * tiles_z) * kErTZ;
+    const int ob0 = grp * a.nb / a.ngroups, ob1 = (grp + 1) * a.nb / a.ngroups;
     const int y = Y0 + ty, z = Z0 + tz;
     float *frow = a.f + ((long)z * a.ny + y) * a.nx;
     // the running minimum starts from f; outputs outside the grid start at 0 so that they
@@ -66,7 +75,7 @@ __global__ void __launch_bounds__(kErThreads, 2) erode2_kernel(Erode2Args a)
         acc[j] = (y < a.ny && z < a.nz && x < a.nx) ? frow[x] : 0.f;
     }
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tile);
-    for (int ob = 0; ob < a.nb; ++ob) {
+    for (int ob = ob0; ob < ob1; ++ob) {
         const int og = a.orient_base + ob;
         const float *g = a.g + ob * a.g_so;
         // gamma_R >= 0, so outputs whose minimum is already 0 are final: skip work when a whole
@@ -129,10 +138,18 @@ __global__ void __launch_bounds__(kErThreads, 2) erode2_kernel(Erode2Args a)
         }
     }
     if (y < a.ny && z < a.nz) {
+        if (a.ngroups == 1) {
 #pragma unroll
-        for (int j = 0; j < kErXT; ++j) {
-            const int x = X0 + tx * kErXT + j;
-            if (x < a.nx) frow[x] = acc[j];
+            for (int j = 0; j < kErXT; ++j) {
+                const int x = X0 + tx * kErXT + j;
+                if (x < a.nx) frow[x] = acc[j];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kErXT; ++j) {
+                const int x = X0 + tx * kErXT + j;
+                if (x < a.nx) atomicMin(reinterpret_cast<unsigned int *>(frow + x), __float_as_uint(__fadd_rn(acc[j], 0.f)));
+            }
         }
     }
 }
@@ -143,8 +160,16 @@ void launch_erode2(const Erode2Args &a, size_t smem, cudaStream_t s)
 {
     // the static descriptor table counts against the default 48 KB, so always raise the limit
     cudaFuncSetAttribute(erode2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid((a.nx + kErTX - 1) / kErTX, (a.ny + kErTY - 1) / kErTY, (a.nz + kErTZ - 1) / kErTZ);
+    dim3 grid((a.nx + kErTX - 1) / kErTX, (a.ny + kErTY - 1) / kErTY, ((a.nz + kErTZ - 1) / kErTZ) * a.ngroups);
     erode2_kernel<<<grid, kErThreads, smem, s>>>(a);
+}
+
+int erode2_blocks_per_sm(size_t smem)
+{
+    cudaFuncSetAttribute(erode2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, erode2_kernel, kErThreads, smem) != cudaSuccess) n = 1;
+    return n < 1 ? 1 : n;
 }
 
 } // namespace imf

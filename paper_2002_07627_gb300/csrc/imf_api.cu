@@ -61,6 +61,7 @@ struct Tool {
     int *er_chunk_start = nullptr;
     int2 *er_runs = nullptr;
     size_t erode_smem = 0;
+    int erode_bps = 1;                   // resident erosion blocks per SM
     long n_rt = 0, n_rk = 0, n_sh = 0;
     std::vector<int> perm, iperm;        // internal orientation order -> caller's index, and back
     int path = IMF_FP32_FFT;             // collision path in use
@@ -662,6 +663,7 @@ void imf_default_options(imf_options *opt)
     opt->recheck_band = 0.0;
     opt->orient_batch = 0;
     opt->hbm_budget_bytes = 0;
+    opt->erode_groups = 0;
 }
 
 imf_status imf_create(const imf_options *opt, imf_handle *out)
@@ -675,6 +677,7 @@ imf_status imf_create(const imf_options *opt, imf_handle *out)
         !(opt->voxel > 0))
         return IMF_ERR_INVALID_ARG;
     if (opt->precision < IMF_AUTO || opt->precision > IMF_BF16_DIRECT) return IMF_ERR_INVALID_ARG;
+    if (opt->erode_groups < 0) return IMF_ERR_INVALID_ARG;
     imf_handle h = new (std::nothrow) imf_handle_s();
     if (!h) return IMF_ERR_OOM;
     h->opt = *opt;
@@ -914,6 +917,13 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
         return fail(h, IMF_ERR_INVALID_ARG, "sharp-point set too wide for the tiled minimum (%zu bytes of tile)",
                     t.erode_smem);
     }
+    {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+            h->nsm = n;
+    }
+    t.erode_bps = erode2_blocks_per_sm(t.erode_smem);
     st = IMF_OK;
     auto bail = [&](imf_status s2) { free_tool(h, t); return s2; };
     twiddles(t.M, t.M, t.M, tw);
@@ -1008,6 +1018,12 @@ imf_status tail_batch(imf_handle h, const Tool &t, const float *rho, const uint8
         a.wx = t.win[0]; a.wy = t.win[1]; a.wz = t.win[2];
         a.chunks = t.er_chunks; a.chunk_start = t.er_chunk_start; a.runs = t.er_runs;
         a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.orient_base = o0; a.nb = nb; a.f = h->f;
+        // enough (tile, orientation group) units for about six waves of resident blocks
+        const long tiles = (long)((op.nx + kErTX - 1) / kErTX) * ((op.ny + kErTY - 1) / kErTY) *
+                           ((op.nz + kErTZ - 1) / kErTZ);
+        const long slots = (long)t.erode_bps * h->nsm;
+        int G = op.erode_groups > 0 ? op.erode_groups : (int)((6 * slots + tiles - 1) / tiles);
+        a.ngroups = std::max(1, std::min(G, nb));
         Launch L(h, KID_ERODE, s);
         launch_erode2(a, t.erode_smem, s);
     }

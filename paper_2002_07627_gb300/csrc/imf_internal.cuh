@@ -168,9 +168,11 @@ struct Erode2Args {
     const int2 *runs;            // (shared-memory offset, length)
     int nx, ny, nz;
     int orient_base, nb;
+    int ngroups;                 // orientation groups per tile (blockIdx.z = group * tiles_z + tile z)
     float *f;
 };
 void launch_erode2(const Erode2Args &a, size_t smem, cudaStream_t s);
+int erode2_blocks_per_sm(size_t smem);
 
 // Direct collision convolution on the tensor cores (direct_tc.cu).
 struct DirectArgs {

@@ -260,3 +260,17 @@ def test_recheck_off_stays_inside_the_contract():
     ref = oracle.imf(d)
     got = run_gpu(d, recheck=False)
     check_against_oracle(d, got, ref)
+
+
+def test_orientation_groups_of_the_minimum_do_not_change_the_result():
+    """The minimum over sharp points may split a launch's orientations into groups that merge
+    into f with an integer atomic minimum; every split gives bit-identical f, f_bar and Gamma,
+    including one group per orientation and more groups than orientations."""
+    d = _small3d(seed=4, n=(37, 45, 70), n_orient=11)
+    base = run_gpu(d, erode_groups=1, orient_batch=8)
+    ref = oracle.imf(d)
+    check_against_oracle(d, base, ref)
+    for g in (2, 3, 8, 40, 0):
+        got = run_gpu(d, erode_groups=g, orient_batch=8)
+        for k in ("f", "fbar", "secluded", "accessible"):
+            assert np.array_equal(got[k], base[k]), (g, k)
