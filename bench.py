@@ -351,7 +351,8 @@ def run_ours(args):
     nG = int(np.prod(shape))
     n_orient = sum(len(t.quats) for t in d.tools)
     prec = {"auto": 0, "fft": 1, "direct": 2}[args.precision]
-    imf = binding.Imf(shape, orient_batch=args.orient_batch, precision=prec, erode_groups=args.erode_groups)
+    imf = binding.Imf(shape, orient_batch=args.orient_batch, precision=prec, erode_groups=args.erode_groups,
+                      fft_stages_only=args.fft_stages_only)
     imf.set_tools(d.tools)
     info = imf.tool_info(0)
     rho = torch.from_numpy(d.rho).to(dev)
@@ -529,6 +530,8 @@ def main():
     ap.add_argument("--orient-batch", type=int, default=0, help="orientations per device batch (0: library default)")
     ap.add_argument("--erode-groups", type=int, default=0,
                     help="orientation groups per tile of the minimum over sharp points (0: library default)")
+    ap.add_argument("--fft-stages-only", action="store_true",
+                    help="radix-stage FFT passes everywhere (comparison with the two-pass register FFT)")
     ap.add_argument("--precision", choices=["auto", "fft", "direct"], default="fft",
                     help="collision path: FP32 FFT, BF16-hi/lo tcgen05 direct, or autotuned")
     ap.add_argument("--batch-designs", type=int, default=64)

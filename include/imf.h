@@ -74,6 +74,8 @@ typedef struct {
     int erode_groups;        /* orientation groups per tile of the minimum over sharp points
                                 (work-unit granularity only; the result does not depend on it);
                                 0 = chosen from the grid and the SM count                      */
+    int fft_stages_only;     /* 1: every FFT pass uses radix stages (2..8) even where a two-pass
+                                register split exists (comparisons and tests); 0 = default    */
 } imf_options;
 
 /* Fill *opt with the defaults above (grid 0x0x0, which imf_create rejects). */

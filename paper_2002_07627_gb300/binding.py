@@ -32,7 +32,8 @@ class ImfOptions(ctypes.Structure):
                 ("voxel", ctypes.c_double), ("lambda_", ctypes.c_double), ("tau", ctypes.c_double),
                 ("theta_rel", ctypes.c_double), ("precision", ctypes.c_int), ("recheck", ctypes.c_int),
                 ("recheck_band", ctypes.c_double), ("orient_batch", ctypes.c_int),
-                ("hbm_budget_bytes", ctypes.c_size_t), ("erode_groups", ctypes.c_int)]
+                ("hbm_budget_bytes", ctypes.c_size_t), ("erode_groups", ctypes.c_int),
+                ("fft_stages_only", ctypes.c_int)]
 
 
 class ImfToolInfo(ctypes.Structure):
@@ -107,6 +108,19 @@ def host_fft(x: np.ndarray, sign: int = -1) -> np.ndarray:
     return out[..., 0].astype(np.float64) + 1j * out[..., 1]
 
 
+def host_fft2(x: np.ndarray, sign: int = -1):
+    """Run the kernels' two-pass register transform on the CPU (host emulation, tests only).
+    Returns (spectrum, (A, B)) or raises ValueError when the length has no supported split."""
+    L = ctypes.CDLL(HOSTLIB)
+    L.imf_host_fft2.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    a = np.ascontiguousarray(np.stack([x.real, x.imag], -1).astype(np.float32))
+    out = np.zeros_like(a)
+    rc = L.imf_host_fft2(len(x), sign, a.ctypes.data, out.ctypes.data)
+    if rc < 0:
+        raise ValueError(f"no two-pass split for length {len(x)}")
+    return out[..., 0].astype(np.float64) + 1j * out[..., 1], (rc // 100, rc % 100)
+
+
 class ImfError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -139,7 +153,7 @@ class Imf:
     """One design grid on the current CUDA device; mirrors the C ABI one-to-one."""
 
     def __init__(self, shape_zyx, lam=0.01, tau=0.5, theta_rel=0.01, precision=IMF_AUTO, recheck=True,
-                 recheck_band=0.0, orient_batch=0, hbm_budget_bytes=0, voxel=1.0, erode_groups=0):
+                 recheck_band=0.0, orient_batch=0, hbm_budget_bytes=0, voxel=1.0, erode_groups=0, fft_stages_only=False):
         self.lib = load()
         opt = ImfOptions()
         self.lib.imf_default_options(ctypes.byref(opt))
@@ -149,6 +163,7 @@ class Imf:
         opt.precision, opt.recheck, opt.recheck_band = precision, int(recheck), recheck_band
         opt.orient_batch, opt.hbm_budget_bytes = orient_batch, hbm_budget_bytes
         opt.erode_groups = erode_groups
+        opt.fft_stages_only = int(fft_stages_only)
         self.shape = (nz, ny, nx)
         self.opt = opt
         h = ctypes.c_void_p()

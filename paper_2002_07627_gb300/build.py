@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libimf.so")
 HOSTLIB = os.path.join(BUILD, "libimf_hosttest.so")
 
-CUDA_SOURCES = ["imf_api.cu", "fft_kernels.cu", "imf_kernels.cu", "erode.cu", "direct_tc.cu", "noalloc.cu"]
+CUDA_SOURCES = ["imf_api.cu", "fft_kernels.cu", "fft2_kernels.cu", "imf_kernels.cu", "erode.cu", "direct_tc.cu", "noalloc.cu"]
 HOST_TEST_SOURCES = ["hosttest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

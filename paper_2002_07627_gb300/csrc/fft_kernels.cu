@@ -10,6 +10,7 @@
 // measure g together with the bit mask of collision-free translations (threshold of
 // Eq. eq_conv_D) and the list of translations whose g lies within the re-check band.
 #include "imf_internal.cuh"
+#include "threshold_row.cuh"
 
 namespace imf {
 
@@ -206,49 +207,10 @@ template <int LOGW> __global__ void __launch_bounds__(kThreads) irfft_threshold_
     __syncthreads();
     float2 *src = buf0, *dst = buf1;
     run_stages<1, LOGW>(a.plan, src, dst, ld, twM);
-    // g[i] = Re z[i/2] (i even) or Im z[i/2] (i odd), clamped at 0 (g >= 0 exactly)
-    const int nwords = (a.nout + 31) >> 5;
-    float *g = a.g + o * a.g_so;
-    uint32_t *bits = a.bits + o * a.b_so;
     for (int w = warp; w < W; w += nwarp) {
         const int r = r0 + w;
         if (r >= a.rows) break;  // warp-uniform
-        const int y = r % a.rows_y, z = r / a.rows_y;
-        float *grow = g + z * a.g_sz + y * a.g_sy;
-        uint32_t *brow = bits + z * a.b_sz + y * a.b_sy;
-        for (int q = 0; q < nwords; ++q) {
-            const int i = q * 32 + lane;
-            const bool valid = i < a.nout;
-            float gv = 0.f;
-            if (valid) {
-                const float2 zz = src[(i >> 1) * ld + w];
-                gv = fmaxf((i & 1) ? zz.y : zz.x, 0.f);
-                grow[i] = gv;
-            }
-            const unsigned freeb = __ballot_sync(0xffffffffu, valid && gv <= a.theta);
-            if (lane == 0) brow[q] = freeb;
-            if (a.flag) {
-                const bool near = valid && fabsf(gv - a.theta) <= a.band;
-                const unsigned nm = __ballot_sync(0xffffffffu, near);
-                if (nm) {
-                    int base = 0;
-                    if (lane == 0) {
-                        base = atomicAdd(a.flag_count, __popc(nm));
-                        atomicAdd(a.flag_total, __popc(nm));
-                    }
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (near) {
-                        const int slot = base + __popc(nm & ((1u << lane) - 1u));
-                        if (slot < a.flag_cap) {
-                            const long lin = ((long)z * a.rows_y + y) * a.nout + i;
-                            a.flags[slot] = make_int2(a.orient_base + (int)o, (int)lin);
-                        } else {
-                            atomicExch(a.status, kDevOverflow);
-                        }
-                    }
-                }
-            }
-        }
+        threshold_row(a, src + w, ld, o, r, lane);
     }
 }
 
@@ -271,6 +233,10 @@ size_t x_smem(int M, int W) { return (size_t)(2 * (M + 1) * (W + 1) + 2 * M + 1)
 
 void launch_axis_fft(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s)
 {
+    if (a.A2 > 0) {
+        launch_axis2(sign, a, nbatch, norient, s);
+        return;
+    }
     const size_t smem = (size_t)(2 * kAxisW * a.plan.L + a.plan.L) * sizeof(float2);
     dim3 grid((a.nx + kAxisW - 1) / kAxisW, nbatch, norient);
     if (sign < 0) {
@@ -294,6 +260,10 @@ void launch_rfft_fwd(const RfftArgs &a, cudaStream_t s)
 
 void launch_irfft_threshold(const IrfftArgs &a, int norient, cudaStream_t s)
 {
+    if (a.A2 > 0) {
+        launch_irfft2_threshold(a, norient, s);
+        return;
+    }
     const int lw = x_log_rows(a.M), W = 1 << lw;
     const size_t smem = x_smem(a.M, W);
     dim3 grid((a.rows + W - 1) / W, 1, norient);

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "imf.h"
+#include "fft2.cuh"
 #include "imf_internal.cuh"
 
 using namespace imf;
@@ -48,6 +49,7 @@ struct Tool {
     int P[3] = {1, 1, 1}, M = 1, Hx = 2, Hs = 2;
     int win[3] = {1, 1, 1}, gpx = 4, wpr = 3;
     FftPlan plM{}, ply{}, plz{};
+    int sM[2] = {0, 0}, sy[2] = {0, 0}, sz[2] = {0, 0};  // two-pass splits (A, B), or 0
     float2 *twM = nullptr, *twP = nullptr, *twy = nullptr, *twz = nullptr;
     float2 *spec = nullptr;
     size_t spec_bytes = 0;
@@ -257,9 +259,13 @@ int next_smooth(int n)
 }
 
 // Relative cost of one length-L pass: L times the summed per-point cost of its radix stages
-// (radix-8 and radix-4 butterflies are the cheapest per point, 7 and 5 the dearest).
+// (radix-8 and radix-4 butterflies are the cheapest per point, 7 and 5 the dearest), or a
+// flat per-point cost for lengths the two-pass register transform handles.
 double fft_cost(int L)
 {
+    int A = 0, B = 0;
+    // a length with a two-pass split crosses shared memory once and runs unrolled DFTs
+    if (fft2::choose_split(L, &A, &B)) return L * 1.1;
     FftPlan p;
     if (!make_plan(L, &p)) return 1e300;
     double c = 0;
@@ -629,6 +635,7 @@ imf_status forward_real_3d(imf_handle h, const Tool &t, const float *src, const 
         a.in = X1; a.in_sb = (long)ny * t.Hs; a.in_sl = t.Hs;
         a.out = X2; a.out_sb = (long)t.P[1] * t.Hs; a.out_sl = t.Hs;
         a.nx = t.Hx; a.lin = ny; a.j0 = 0; a.lout = t.P[1]; a.scale = 1.f; a.tw = t.twy; a.plan = t.ply;
+        a.A2 = t.sy[0]; a.B2 = t.sy[1];
         Launch L(h, KID_AXIS_FWD, s);
         launch_axis_fft(-1, a, nz, 1, s);
     }
@@ -638,6 +645,7 @@ imf_status forward_real_3d(imf_handle h, const Tool &t, const float *src, const 
         a.out = out; a.out_sb = t.Hs; a.out_sl = (long)t.P[1] * t.Hs;
         a.nx = t.Hx; a.lin = nz; a.j0 = 0; a.lout = t.P[2]; a.scale = scale; a.conj_out = conj_out;
         a.tw = t.twz; a.plan = t.plz;
+        a.A2 = t.sz[0]; a.B2 = t.sz[1];
         Launch L(h, KID_AXIS_FWD, s);
         launch_axis_fft(-1, a, t.P[1], 1, s);
     }
@@ -664,6 +672,7 @@ void imf_default_options(imf_options *opt)
     opt->orient_batch = 0;
     opt->hbm_budget_bytes = 0;
     opt->erode_groups = 0;
+    opt->fft_stages_only = 0;
 }
 
 imf_status imf_create(const imf_options *opt, imf_handle *out)
@@ -877,6 +886,10 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
     t.Hs = (t.Hx + 1) & ~1;
     t.gpx = (t.win[0] + 3) & ~3;
     t.wpr = (t.win[0] + 31) / 32 + 2;
+    const bool split = !h->opt.fft_stages_only;
+    if (!split || !fft2::choose_split(t.M, &t.sM[0], &t.sM[1])) t.sM[0] = t.sM[1] = 0;
+    if (!split || !fft2::choose_split(t.P[1], &t.sy[0], &t.sy[1])) t.sy[0] = t.sy[1] = 0;
+    if (!split || !fft2::choose_split(t.P[2], &t.sz[0], &t.sz[1])) t.sz[0] = t.sz[1] = 0;
     if (!make_plan(t.M, &t.plM) || !make_plan(t.P[1], &t.ply) || !make_plan(t.P[2], &t.plz)) {
         free_tool(h, t);
         return fail(h, IMF_ERR_INVALID_ARG, "no FFT plan for %d x %d x %d", t.P[0], t.P[1], t.P[2]);
@@ -1104,6 +1117,7 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
                 a.mul = h->rho_spec; a.mul_so = 0; a.mul_sb = t.Hs; a.mul_sl = (long)t.P[1] * t.Hs;
                 a.out = h->Y1; a.out_so = y1so; a.out_sb = t.Hs; a.out_sl = (long)t.P[1] * t.Hs;
                 a.nx = t.Hx; a.lin = t.P[2]; a.j0 = 0; a.lout = t.win[2]; a.scale = 1.f; a.tw = t.twz; a.plan = t.plz;
+                a.A2 = t.sz[0]; a.B2 = t.sz[1];
                 Launch L(h, KID_AXIS_INV_MUL, s);
                 launch_axis_fft(1, a, t.P[1], nb, s);
             }
@@ -1112,6 +1126,7 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
                 a.in = h->Y1; a.in_so = y1so; a.in_sb = (long)t.P[1] * t.Hs; a.in_sl = t.Hs;
                 a.out = h->Y2; a.out_so = y2so; a.out_sb = (long)t.win[1] * t.Hs; a.out_sl = t.Hs;
                 a.nx = t.Hx; a.lin = t.P[1]; a.j0 = 0; a.lout = t.win[1]; a.scale = 1.f; a.tw = t.twy; a.plan = t.ply;
+                a.A2 = t.sy[0]; a.B2 = t.sy[1];
                 Launch L(h, KID_AXIS_INV, s);
                 launch_axis_fft(1, a, t.win[2], nb, s);
             }
@@ -1125,6 +1140,7 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
                 a.flags = h->flags; a.flag_count = fcount; a.flag_total = h->dev_small + 4; a.flag_cap = h->flag_cap;
                 a.status = status;
                 a.orient_base = o0; a.M = t.M; a.twM = t.twM; a.twP = t.twP; a.plan = t.plM;
+                a.A2 = t.sM[0]; a.B2 = t.sM[1];
                 Launch L(h, KID_IRFFT_THRESH, s);
                 launch_irfft_threshold(a, nb, s);
             }

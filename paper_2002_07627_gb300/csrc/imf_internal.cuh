@@ -33,6 +33,7 @@ struct AxisArgs {
     int conj_out;
     const float2 *tw;            // exp(-2 pi i m / L), m < L
     FftPlan plan;
+    int A2, B2;                  // two-pass split L = A2 B2 (fft2.cuh), or 0: Stockham stages
 };
 
 // Real-to-complex FFT along x (rows of a real grid), packed as a half-length complex FFT.
@@ -72,11 +73,17 @@ struct IrfftArgs {
     int M;
     const float2 *twM, *twP;
     FftPlan plan;
+    int A2, B2;                  // two-pass split M = A2 B2 (fft2.cuh), or 0: Stockham stages
 };
 
 void launch_axis_fft(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s);
 void launch_rfft_fwd(const RfftArgs &a, cudaStream_t s);
 void launch_irfft_threshold(const IrfftArgs &a, int norient, cudaStream_t s);
+// two-pass register variants (fft2_kernels.cu); the dispatchers above call them when A2 > 0
+void launch_axis2(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s);
+void launch_irfft2_threshold(const IrfftArgs &a, int norient, cudaStream_t s);
+size_t axis2_smem(int L);
+size_t irfft2_smem(int M, int A, int B);
 
 // ---------------------------------------------------------------------------------------
 // IMF kernels

@@ -41,6 +41,44 @@ def test_host_fft_matches_numpy(lib, L):
     assert np.max(np.abs(inv - np.fft.ifft(x) * L)) < 2e-6 * scale * max(1.0, np.log2(L))
 
 
+_SPLIT_SIZES = (2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16)
+_SPLIT_LENGTHS = sorted({a * b for a in _SPLIT_SIZES for b in _SPLIT_SIZES if a >= b})
+
+
+@pytest.mark.parametrize("L", _SPLIT_LENGTHS)
+def test_host_two_pass_fft_matches_numpy(lib, L):
+    """The two-pass register transform (every length A B with A, B in the supported set) agrees
+    with numpy's FFT in both directions, and its split is the balanced one with A >= B."""
+    rng = np.random.default_rng(1000 + L)
+    x = rng.normal(size=L) + 1j * rng.normal(size=L)
+    fwd, (A, B) = binding.host_fft2(x, -1)
+    inv, _ = binding.host_fft2(x, +1)
+    assert A * B == L and A >= B and A in _SPLIT_SIZES and B in _SPLIT_SIZES
+    assert A == min(a for a in _SPLIT_SIZES if L % a == 0 and L // a in _SPLIT_SIZES and a >= L // a)
+    scale = np.sqrt(L) * np.abs(x).max()
+    assert np.max(np.abs(fwd - np.fft.fft(x))) < 2e-6 * scale * max(1.0, np.log2(L))
+    assert np.max(np.abs(inv - np.fft.ifft(x) * L)) < 2e-6 * scale * max(1.0, np.log2(L))
+
+
+def test_host_two_pass_fft_single_tones(lib):
+    """A unit impulse at n0 transforms to exp(-+2 pi i n0 k / L) exactly up to rounding: pins
+    the sign convention and the index maps n = n1 + B n2, k = k2 + A k1 separately."""
+    for L in (96, 168, 192, 150, 210):
+        for n0 in (0, 1, 7, L - 1):
+            x = np.zeros(L, complex)
+            x[n0] = 1.0
+            k = np.arange(L)
+            for sign in (-1, 1):
+                got, _ = binding.host_fft2(x, sign)
+                assert np.max(np.abs(got - np.exp(sign * 2j * np.pi * n0 * k / L))) < 4e-6
+
+
+def test_host_two_pass_fft_rejects_unsplittable_lengths(lib):
+    for L in (11, 13 * 4, 17 * 2, 7 * 7 * 7, 512):
+        with pytest.raises(ValueError):
+            binding.host_fft2(np.ones(L, complex))
+
+
 def test_host_fft_rejects_rough_lengths(lib):
     with pytest.raises(ValueError):
         binding.host_fft(np.ones(11, complex))

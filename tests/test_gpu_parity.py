@@ -274,3 +274,16 @@ def test_orientation_groups_of_the_minimum_do_not_change_the_result():
         got = run_gpu(d, erode_groups=g, orient_batch=8)
         for k in ("f", "fbar", "secluded", "accessible"):
             assert np.array_equal(got[k], base[k]), (g, k)
+
+
+@pytest.mark.parametrize("stages_only", [False, True])
+def test_both_fft_variants_match_oracle(stages_only):
+    """The two-pass register FFT (default where the padded lengths split into factors <= 16)
+    and the radix-stage FFT (forced) both meet the contract on a ragged grid, per orientation
+    for g and the free bits and in full for f, f_bar and Gamma."""
+    d = _small3d(seed=7, n=(29, 38, 45), n_orient=6)
+    ref = oracle.imf(d, keep=True)
+    got = run_gpu(d, orient_batch=4, fft_stages_only=stages_only)
+    check_against_oracle(d, got, ref)
+    info = got["imf"].tool_info(0)
+    assert all(p <= 256 for p in info.P)      # both variants run the same padded lengths
