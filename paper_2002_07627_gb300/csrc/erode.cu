@@ -58,8 +58,10 @@ __global__ void __launch_bounds__(kErThreads, 2) erode2_kernel(Erode2Args a)
     extern __shared__ float tile[];
     __shared__ int2 sruns[kErMaxRunsPerChunk];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // warp = tx (8) x tz_hi (2); lane = ty (8) x tz_lo (4)
-    const int ty = lane & 7, tz = ((warp >> 3) << 2) | (lane >> 3), tx = warp & 7;
+    // lane = ty_lo (8) x tz_lo (4); warp = tx (kErTX / kErXT) x ty_hi (kErTY / 8) x tz_hi
+    constexpr int NXT = kErTX / kErXT, NYH = kErTY / 8;
+    static_assert(NXT * NYH * (kErTZ / 4) * 32 == kErThreads, "erosion block shape");
+    const int tx = warp % NXT, ty = ((warp / NXT) % NYH) * 8 + (lane & 7), tz = (warp / (NXT * NYH)) * 4 + (lane >> 3);
     const int tiles_z = (a.nz + kErTZ - 1) / kErTZ;
     const int grp = blockIdx.z / tiles_z;
     const int X0 = blockIdx.x * kErTX, Y0 = blockIdx.y * kErTY, Z0 = (blockIdx.z - grp * tiles_z) * kErTZ;
