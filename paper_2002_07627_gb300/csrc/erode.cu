@@ -53,7 +53,7 @@ template <int L> __device__ __forceinline__ void run_group(const int2 *sruns, in
     for (int q = q0; q < q1; ++q) run_min<L>(tb + sruns[q].x, acc);
 }
 
-__global__ void __launch_bounds__(kErThreads, 2) erode2_kernel(Erode2Args a)
+__global__ void __launch_bounds__(kErThreads, kErBlocksPerSM) erode2_kernel(Erode2Args a)
 {
     extern __shared__ float tile[];
     __shared__ int2 sruns[kErMaxRunsPerChunk];

@@ -373,7 +373,6 @@ void free_tool(imf_handle h, Tool &t)
 
 // Runs along x of the sharp points of one orientation, grouped in dz-chunks whose g tile fits
 // `budget` bytes of shared memory (see erode.cu for the tile layout).
-constexpr size_t kErodeBudget = 104 * 1024;
 
 bool bank_free(int P, int Q)
 {
