@@ -131,9 +131,8 @@ inline bool choose_split(int L, int *A, int *B)
 
 // Pass-1 arithmetic of one thread: A-point DFT of v (the samples x[n1 + B n2], n2 < A), then
 // v[k2] *= w_L^{S n1 k2} from tw[m] = exp(-2 pi i m / L) (n1 k2 < L needs no reduction).
-template <int S, int A> __host__ __device__ __forceinline__ void pass1(float2 *v, int n1, const float2 *tw)
+template <int S, int A> __host__ __device__ __forceinline__ void twiddle(float2 *v, int n1, const float2 *tw)
 {
-    dft_reg<S, A>(v);
     if (n1 == 0) return;
 #pragma unroll
     for (int k2 = 1; k2 < A; ++k2) {
@@ -141,6 +140,11 @@ template <int S, int A> __host__ __device__ __forceinline__ void pass1(float2 *v
         if (S > 0) t.y = -t.y;
         v[k2] = c_mul(v[k2], t);
     }
+}
+template <int S, int A> __host__ __device__ __forceinline__ void pass1(float2 *v, int n1, const float2 *tw)
+{
+    dft_reg<S, A>(v);
+    twiddle<S, A>(v, n1, tw);
 }
 
 // Calls f(std::integral_constant<int, n>) for a supported size n (uniform branch).

@@ -44,16 +44,18 @@ template <int S> __global__ void __launch_bounds__(kT2) axis2_kernel(AxisArgs a,
         ok = b < nbatch;
     }
     for (int i = threadIdx.x; i < L; i += kT2) tw[i] = a.tw[i];
-    __syncthreads();
     const long o = blockIdx.z;
-    // pass 1: slot p = n1 < B loads x[n1 + B n2] (times the pointwise factor), A-point DFT,
-    // twiddle; tile element (n1, k2) of pencil w at (n1 A + k2) W + w
-    if (p < B && ok) {
-        const float2 *in = a.in + o * a.in_so + b * a.in_sb + c;
-        const float2 *mul = a.mul ? a.mul + o * a.mul_so + b * a.mul_sb + c : nullptr;
-        fft2::with_size(A, [&](auto AA) {
-            constexpr int NA = decltype(AA)::value;
-            float2 v[NA];
+    // pass 1: slot p = n1 < B loads x[n1 + B n2] (times the pointwise factor) and runs the
+    // A-point DFT while the twiddle table is still being staged; after the barrier it applies
+    // the twiddles and stores tile element (n1, k2) of pencil w at (n1 A + k2) W + w. Every
+    // thread enters (the size is uniform), so the barrier inside is reached by all.
+    const bool act1 = p < B && ok;
+    const float2 *in = a.in + o * a.in_so + b * a.in_sb + c;
+    const float2 *mul = a.mul ? a.mul + o * a.mul_so + b * a.mul_sb + c : nullptr;
+    fft2::with_size(A, [&](auto AA) {
+        constexpr int NA = decltype(AA)::value;
+        float2 v[NA];
+        if (act1) {
             if (mul) {
                 float2 m[NA];
 #pragma unroll
@@ -75,11 +77,15 @@ template <int S> __global__ void __launch_bounds__(kT2) axis2_kernel(AxisArgs a,
                     v[n2] = j < a.lin ? in[(long)j * a.in_sl] : make_float2(0.f, 0.f);
                 }
             }
-            fft2::pass1<S, NA>(v, p, tw);
+            fft2::dft_reg<S, NA>(v);
+        }
+        __syncthreads();
+        if (act1) {
+            fft2::twiddle<S, NA>(v, p, tw);
 #pragma unroll
             for (int k2 = 0; k2 < NA; ++k2) tile[(p * NA + k2) * kW2 + w] = v[k2];
-        });
-    }
+        }
+    });
     __syncthreads();
     // pass 2: slot p = k2 < A, B-point DFT over n1; X[k2 + A k1] -> out[j - j0] if in window
     if (p < A && ok) {
