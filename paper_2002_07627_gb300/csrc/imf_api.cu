@@ -57,8 +57,6 @@ struct Tool {
     int *rt_start = nullptr;
     int4 *iv = nullptr;
     int *iv_start = nullptr;
-    int *sh_lin = nullptr;
-    int *sh_start = nullptr;
     ErodeChunk *er_chunks = nullptr;
     int *er_chunk_start = nullptr;
     int2 *er_runs = nullptr;
@@ -361,8 +359,6 @@ void free_tool(imf_handle h, Tool &t)
     dfree(h, t.rt_start, (size_t)t.n_orient + 1);
     dfree(h, t.iv, (size_t)0);
     dfree(h, t.iv_start, (size_t)t.n_orient + 1);
-    dfree(h, t.sh_lin, (size_t)t.n_sh);
-    dfree(h, t.sh_start, (size_t)t.n_orient + 1);
     dfree(h, t.er_chunks);
     dfree(h, t.er_chunk_start);
     dfree(h, t.er_runs);
@@ -899,7 +895,7 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
     // --- device tables
     std::vector<float2> tw;
     std::vector<uint32_t> rto;
-    std::vector<int> rts(n_orient + 1, 0), ivst(n_orient + 1, 0), shs(n_orient + 1, 0), shl;
+    std::vector<int> rts(n_orient + 1, 0), ivst(n_orient + 1, 0);
     std::vector<int4> ivv;
     for (int i = 0; i < n_orient; ++i) {
         for (size_t m = 0; m < t.rt[i].size(); m += 3)
@@ -908,14 +904,11 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
         rts[i + 1] = (int)rto.size();
         for (size_t m = 0; m < ivs[i].size(); m += 4) ivv.push_back(make_int4(ivs[i][m], ivs[i][m + 1], ivs[i][m + 2], ivs[i][m + 3]));
         ivst[i + 1] = (int)ivv.size();
-        for (size_t m = 0; m < t.sh[i].size(); m += 3)
-            shl.push_back((int)(((long)t.sh[i][m + 2] * t.win[1] + t.sh[i][m + 1]) * t.gpx + t.sh[i][m]));
-        shs[i + 1] = (int)shl.size();
+        t.n_sh += (long)t.sh[i].size() / 3;
     }
     t.n_rt = (long)rto.size();
     t.n_rk = 0;
     for (auto &v : t.rk) t.n_rk += (long)v.size() / 3;
-    t.n_sh = (long)shl.size();
     std::vector<ErodeChunk> chunks;
     std::vector<int2> eruns;
     std::vector<int> chst(n_orient + 1, 0);
@@ -947,7 +940,7 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
     twiddles(t.P[2], t.P[2], t.P[2], tw);
     if ((st = upload(h, &t.twz, tw))) return bail(st);
     if ((st = upload(h, &t.rt_off, rto)) || (st = upload(h, &t.rt_start, rts)) || (st = upload(h, &t.iv, ivv)) ||
-        (st = upload(h, &t.iv_start, ivst)) || (st = upload(h, &t.sh_lin, shl)) || (st = upload(h, &t.sh_start, shs)) ||
+        (st = upload(h, &t.iv_start, ivst)) ||
         (st = upload(h, &t.er_chunks, chunks)) || (st = upload(h, &t.er_chunk_start, chst)) ||
         (st = upload(h, &t.er_runs, eruns)))
         return bail(st);

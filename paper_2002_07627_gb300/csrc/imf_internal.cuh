@@ -140,18 +140,6 @@ struct SweepArgs {
 void launch_sweep(const SweepArgs &a, cudaStream_t s);
 void launch_sweep2(const SweepArgs &a, cudaStream_t s);
 
-struct ErodeArgs {
-    const float *g;
-    long g_so;
-    int gpx, gpy;                // window pitch (x) and rows per z-plane
-    const int *sh_lin;           // linear window offsets of the sharp points, all orientations
-    const int *sh_start;         // n_orient + 1
-    int nx, ny, nz;
-    int kx, ky, kz;
-    int orient_base, nb;
-    float *f;                    // running minimum over orientations and tools
-};
-void launch_erode(const ErodeArgs &a, cudaStream_t s);
 
 // Tiled minimum over sharp points. A block owns kErTX x kErTY x kErTZ outputs (kErXT
 // consecutive x per thread; 1024 threads, one block per SM); the sharp points of an

@@ -297,28 +297,6 @@ __global__ void __launch_bounds__(256) recheck_blocks_kernel(RecheckArgs a)
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// Minimum over sharp points (Eq. eq_imf_2): gamma_R(x) = min_k g_R(x - k), folded into the
-// running minimum over orientations and tools (Eq. eq_imf_5).
-// ---------------------------------------------------------------------------------------
-__global__ void erode_kernel(ErodeArgs a)
-{
-    const long n = (long)a.nx * a.ny * a.nz;
-    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
-        const int x = (int)(idx % a.nx);
-        const int y = (int)((idx / a.nx) % a.ny);
-        const int z = (int)(idx / ((long)a.nx * a.ny));
-        const long base = ((long)(z + a.kz) * a.gpy + (y + a.ky)) * a.gpx + (x + a.kx);
-        float m = a.f[idx];
-        for (int ob = 0; ob < a.nb; ++ob) {
-            const int og = a.orient_base + ob;
-            const float *g = a.g + ob * a.g_so + base;
-            for (int k = a.sh_start[og]; k < a.sh_start[og + 1]; ++k) m = fminf(m, g[-(long)a.sh_lin[k]]);
-        }
-        a.f[idx] = m;
-    }
-}
-
 __global__ void fill_f32_kernel(float *p, float v, long n)
 {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) p[i] = v;
@@ -425,11 +403,6 @@ void launch_recheck_blocks(const RecheckArgs &a, int max_points, cudaStream_t s)
 void launch_sweep(const SweepArgs &a, cudaStream_t s)
 {
     sweep_kernel<<<blocks_for((long)a.awords * a.ny * a.nz), kThreads, 0, s>>>(a);
-}
-
-void launch_erode(const ErodeArgs &a, cudaStream_t s)
-{
-    erode_kernel<<<blocks_for((long)a.nx * a.ny * a.nz), kThreads, 0, s>>>(a);
 }
 
 void launch_fill_f32(float *p, float v, long n, cudaStream_t s)
