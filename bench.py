@@ -162,16 +162,16 @@ def algorithmic_bytes(kernel, info, shape, nb):
     return None
 
 
-def traffic_record(kernel):
-    """dram bytes per launch of `kernel` from the committed ncu summary, if the kernel source is
-    unchanged since the capture (else None)."""
+def traffic_record(kernel, workload):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if it was captured on
+    this workload and the kernel source is unchanged since the capture (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
     rec = d.get(kernel)
-    if not rec:
+    if not rec or rec.get("workload") != workload:
         return None
     src = os.path.join(ROOT, rec["source"])
     if not os.path.exists(src):
@@ -427,7 +427,7 @@ def run_ours(args):
         peak = 152 * 128 * smax * 1e6 / 1e12
         ach = comps / avg_s / 1e12
         roof = {"kernel": dname, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tcomparisons/s",
-                "frac": ach / peak, "traffic": traffic_record(dname),
+                "frac": ach / peak, "traffic": traffic_record(dname, args.workload),
                 "peak_source": f"152 SMs x 128 lanes x {smax:.0f} MHz (unit counts and clock)",
                 "algorithmic_comparisons_per_launch": comps, "avg_launch_ms": dms / dcnt,
                 "note": "outputs already at 0 skip later orientations; they count as done"}
@@ -438,12 +438,12 @@ def run_ours(args):
         flops = 2.0 * info.n_rt * wx * wy * wz / max(1, dcnt / args.steps)
         ach = flops / avg_s / 1e12
         roof = {"kernel": dname, "bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
-                "frac": ach / bf16, "traffic": traffic_record(dname), "peak_source": f"bf16 burst, {peak_src}",
+                "frac": ach / bf16, "traffic": traffic_record(dname, args.workload), "peak_source": f"bf16 burst, {peak_src}",
                 "algorithmic_flops_per_launch": flops, "avg_launch_ms": dms / dcnt}
     elif abytes is not None:
         ach = abytes / avg_s / 1e9
         roof = {"kernel": dname, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": traffic_record(dname), "peak_source": peak_src,
+                "frac": ach / hbm, "traffic": traffic_record(dname, args.workload), "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": dms / dcnt}
     kernel_share = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                     for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}
