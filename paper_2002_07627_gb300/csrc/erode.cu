@@ -95,24 +95,45 @@ __global__ void __launch_bounds__(kErThreads, kErBlocksPerSM) erode2_kernel(Erod
             const int run0 = ch.run0, nrun = ch.run1 - ch.run0;
             __syncthreads();
             // asynchronous fill, one warp per tile row; cells outside the window (read only by
-            // outputs beyond the grid, which are masked) are zero-filled
+            // outputs beyond the grid, which are masked) are zero-filled. Rows are short (a few
+            // copies per lane), so the row position advances without division and each lane's
+            // copies of a row are unrolled four at a time.
             const bool xin = gx0 + txh <= a.wx;
-            for (int r = warp; r < nrow; r += kErThreads / 32) {
-                const int iy = r % tyh, iz = r / tyh;
-                const int gy = gy0 + iy, gz = gz0 + iz;
-                const bool rowok = gy < a.wy && gz < a.wz;
-                const float *src = g + ((long)gz * a.gpy + gy) * a.gpx + gx0;
-                const uint32_t drow = sbase + 4u * (uint32_t)(iz * pz + iy * py);
+            constexpr int NW = kErThreads / 32;
+            int iy = warp % tyh, iz = warp / tyh;
+            // row pointers advance by NW rows per step (and by one plane minus tyh rows per wrap)
+            const long gstep = (long)NW * a.gpx, gwrap = (long)a.gpy * a.gpx - (long)tyh * a.gpx;
+            const uint32_t dstep = 4u * (uint32_t)(NW * py), dwrap = 4u * (uint32_t)(pz - tyh * py);
+            const float *src = g + ((long)(gz0 + iz) * a.gpy + (gy0 + iy)) * a.gpx + gx0;
+            uint32_t drow = sbase + 4u * (uint32_t)(iz * pz + iy * py);
+            for (int r = warp; r < nrow; r += NW) {
+                const bool rowok = gy0 + iy < a.wy && gz0 + iz < a.wz;
                 if (rowok && xin) {
                     // whole row inside the window: plain 4-byte copies
-                    for (int ix = lane; ix < txh; ix += 32)
-                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(drow + 4u * ix), "l"(src + ix));
+                    for (int ix0 = lane; ix0 < txh; ix0 += 128) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int ix = ix0 + 32 * k;
+                            if (ix < txh)
+                                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(drow + 4u * ix),
+                                             "l"(src + ix));
+                        }
+                    }
                 } else {
                     for (int ix = lane; ix < txh; ix += 32) {
                         const bool ok = rowok && gx0 + ix < a.wx;
                         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(drow + 4u * ix),
                                      "l"(ok ? src + ix : g), "r"(ok ? 4 : 0));
                     }
+                }
+                iy += NW;
+                src += gstep;
+                drow += dstep;
+                while (iy >= tyh) {
+                    iy -= tyh;
+                    ++iz;
+                    src += gwrap;
+                    drow += dwrap;
                 }
             }
             for (int q = threadIdx.x; q < nrun; q += kErThreads) sruns[q] = a.runs[run0 + q];
