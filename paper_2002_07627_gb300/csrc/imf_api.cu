@@ -24,6 +24,7 @@
 #include "imf.h"
 #include "fft2.cuh"
 #include "imf_internal.cuh"
+#include "erode_plan.h"
 
 using namespace imf;
 
@@ -365,84 +366,6 @@ void free_tool(imf_handle h, Tool &t)
     dfree(h, t.d_taps);
     dfree(h, t.d_bmat);
     t = Tool();
-}
-
-// Runs along x of the sharp points of one orientation, grouped in dz-chunks whose g tile fits
-// `budget` bytes of shared memory (see erode.cu for the tile layout).
-
-bool bank_free(int P, int Q)
-{
-    bool seen[32] = {false};
-    for (int tz = 0; tz < 4; ++tz)
-        for (int ty = 0; ty < 8; ++ty) {
-            const int b = ((tz * Q + ty * P) % 32 + 32) % 32;
-            if (seen[b]) return false;
-            seen[b] = true;
-        }
-    return true;
-}
-
-void plan_erode(const std::vector<int32_t> &sh, const int K[3], std::vector<ErodeChunk> &chunks,
-                std::vector<int2> &runs, size_t &smem_max)
-{
-    if (sh.empty()) return;
-    int kmn[3] = {1 << 30, 1 << 30, 1 << 30}, kmx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
-    std::map<std::pair<int, int>, std::vector<int>> rows;   // (dz, dy) -> dx
-    for (size_t m = 0; m < sh.size(); m += 3) {
-        for (int c = 0; c < 3; ++c) { kmn[c] = std::min(kmn[c], sh[m + c]); kmx[c] = std::max(kmx[c], sh[m + c]); }
-        rows[{sh[m + 2], sh[m + 1]}].push_back(sh[m]);
-    }
-    struct Run { int dz, dy, a, L; };
-    std::vector<Run> rr;
-    for (auto &kv : rows) {
-        auto &v = kv.second;
-        std::sort(v.begin(), v.end());
-        size_t i = 0;
-        while (i < v.size()) {
-            size_t j = i;
-            while (j + 1 < v.size() && v[j + 1] == v[j] + 1) ++j;
-            for (int a0 = v[i]; a0 <= v[j]; a0 += kErMaxL)
-                rr.push_back({kv.first.first, kv.first.second, a0, std::min(kErMaxL, v[j] - a0 + 1)});
-            i = j + 1;
-        }
-    }
-    const int Ex = kmx[0] - kmn[0] + 1, Ey = kmx[1] - kmn[1] + 1;
-    const int txh = kErTX + Ex - 1, tyh = kErTY + Ey - 1;
-    const int P = txh | 1;
-    int Q = tyh * P;
-    while (!bank_free(P, Q)) ++Q;
-    int planes = (int)(kErodeBudget / (4 * (size_t)Q));
-    int dzc = planes - kErTZ + 1;
-    if (dzc < 1) dzc = 1;
-    for (int hi = kmx[2]; hi >= kmn[2]; hi -= dzc) {
-        const int lo = std::max(kmn[2], hi - dzc + 1);
-        std::vector<int2> cr;
-        for (const Run &r : rr) {
-            if (r.dz < lo || r.dz > hi) continue;
-            const int off = (hi - r.dz) * Q + (kmx[1] - r.dy) * P + (kmx[0] - (r.a + r.L - 1));
-            cr.push_back(make_int2(off, r.L));
-        }
-        if (cr.empty()) continue;
-        std::stable_sort(cr.begin(), cr.end(), [](const int2 &x, const int2 &y) { return x.y < y.y; });
-        for (size_t b = 0; b < cr.size(); b += kErMaxRunsPerChunk) {
-            const size_t e = std::min(cr.size(), b + (size_t)kErMaxRunsPerChunk);
-            ErodeChunk ch{};
-            ch.run0 = (int)runs.size();
-            for (size_t i = b; i < e; ++i) runs.push_back(cr[i]);
-            ch.run1 = (int)runs.size();
-            ch.lend[0] = 0;
-            for (int L = 1; L <= kErMaxL; ++L) {
-                int c = ch.lend[L - 1];
-                while (ch.run0 + c < ch.run1 && runs[ch.run0 + c].y == L) ++c;
-                ch.lend[L] = c;
-            }
-            ch.txh = txh; ch.tyh = tyh; ch.tzh = kErTZ + (hi - lo);
-            ch.pitch_y = P; ch.pitch_z = Q;
-            ch.ox = K[0] - kmx[0]; ch.oy = K[1] - kmx[1]; ch.oz = K[2] - hi;
-            chunks.push_back(ch);
-        }
-        smem_max = std::max(smem_max, (size_t)(kErTZ + (hi - lo)) * Q * sizeof(float));
-    }
 }
 
 // Greedy nearest-neighbour chain over the rotations (Frobenius distance), so that consecutive

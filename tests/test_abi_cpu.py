@@ -8,7 +8,7 @@ import os
 import numpy as np
 import pytest
 
-from paper_2002_07627_gb300 import binding, build
+from paper_2002_07627_gb300 import binding, build, synth
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -115,3 +115,76 @@ def test_stage_reciprocals_are_exact(lib):
     L.imf_host_check_div.restype = ctypes.c_long
     # every stage divisor up to the longest plan, for every butterfly index the kernels use
     assert L.imf_host_check_div(4096, 1 << 20) == 0
+
+
+def _host_plan(sh, K):
+    import ctypes
+    from paper_2002_07627_gb300 import build
+    L = ctypes.CDLL(build.HOSTLIB)
+    sh = np.ascontiguousarray(np.asarray(sh, np.int32).reshape(-1, 3))
+    Ka = np.ascontiguousarray(np.asarray(K, np.int32))
+    consts = np.zeros(7, np.int64)
+    L.imf_host_erode_constants(consts.ctypes.data_as(ctypes.c_void_p))
+    chunks = np.zeros((4096, 28), np.int32)
+    runs = np.zeros((1 << 16, 2), np.int32)
+    smem = ctypes.c_long(0)
+    nruns = ctypes.c_int(0)
+    L.imf_host_plan_erode.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_long),
+                                      ctypes.POINTER(ctypes.c_int)]
+    n = L.imf_host_plan_erode(sh.ctypes.data, len(sh), Ka.ctypes.data, len(chunks), chunks.ctypes.data, len(runs),
+                              runs.ctypes.data, ctypes.byref(smem), ctypes.byref(nruns))
+    assert n >= 0
+    return chunks[:n], runs[:nruns.value], smem.value, dict(zip(["tx", "ty", "tz", "xt", "maxl", "budget", "maxruns"],
+                                                                  consts.tolist()))
+
+
+def _plan_cases():
+    from oracle.ref import resample_tool
+    cases = []
+    big = synth.cylinder_tool(3, 20, 8, 16, synth.fibonacci_quats(64))
+    for i in (0, 7, 23, 41, 63):
+        cases.append(resample_tool(big, big.quats[i])["sharp"])
+    small = synth.cylinder_tool(2, 6, 4, 6, np.random.default_rng(5).normal(size=(3, 4)))
+    for q in small.quats:
+        cases.append(resample_tool(small, q)["sharp"])
+    planar = synth.planar_tool(n_orient=8)
+    cases.append(resample_tool(planar, planar.quats[3])["sharp"])
+    long_x = synth.box_tool(ext=(37, 3, 2))                 # runs longer than the 16-sample limit
+    cases.append(resample_tool(long_x, np.array([1.0, 0, 0, 0]))["sharp"])
+    return cases
+
+
+@pytest.mark.parametrize("case", range(10))
+def test_erosion_plan_covers_every_sharp_point_once_within_the_tile(lib, case):
+    """The plan of the tiled minimum over sharp points (Eq. eq_imf_2), decoded with only the
+    window origin K and each chunk's tile origin: its runs cover every sharp point exactly once,
+    sit in length groups of at most 16, every thread position reads inside its chunk's tile,
+    the tile fits the budget and the 32 lanes of a warp (8 rows x 4 planes) hit 32 banks."""
+    sh = np.asarray(_plan_cases()[case], np.int64)
+    rng = np.random.default_rng(case)
+    K = sh.max(0) + rng.integers(0, 5, size=3)      # any window origin at or beyond the largest offset
+    chunks, runs, smem, c = _host_plan(sh, K)
+    covered = []
+    nxt = c["tx"] // c["xt"]
+    for ch in chunks:
+        run0, run1, txh, tyh, tzh, P, Q, ox, oy, oz = ch[:10]
+        lend = ch[10:27]
+        assert P % 2 == 1 and P >= txh and Q >= tyh * P
+        banks = {(tz * Q + ty * P) % 32 for tz in range(4) for ty in range(8)}
+        assert len(banks) == 32
+        assert tzh * Q * 4 <= max(c["budget"], c["tz"] * Q * 4) and tzh * Q * 4 <= smem
+        assert 0 < run1 - run0 <= c["maxruns"] and lend[0] == 0 and lend[c["maxl"]] == run1 - run0
+        for Lr in range(1, c["maxl"] + 1):
+            seg = runs[run0 + lend[Lr - 1]: run0 + lend[Lr]]
+            assert np.all(seg[:, 1] == Lr)
+        for off, Lr in runs[run0:run1]:
+            iz, rem = divmod(int(off), int(Q))
+            iy, ix = divmod(rem, int(P))
+            # the reads of the thread farthest from the block origin stay in the tile
+            assert ix + (nxt - 1) * c["xt"] + c["xt"] + Lr - 2 <= txh - 1
+            assert iy + c["ty"] - 1 <= tyh - 1 and iz + c["tz"] - 1 <= tzh - 1
+            kz, ky, kx_last = K[2] - oz - iz, K[1] - oy - iy, K[0] - ox - ix
+            covered += [(kx, ky, kz) for kx in range(kx_last - Lr + 1, kx_last + 1)]
+    assert len(covered) == len(sh)
+    assert sorted(covered) == sorted(map(tuple, sh.tolist()))
