@@ -352,7 +352,7 @@ def run_ours(args):
     n_orient = sum(len(t.quats) for t in d.tools)
     prec = {"auto": 0, "fft": 1, "direct": 2}[args.precision]
     imf = binding.Imf(shape, orient_batch=args.orient_batch, precision=prec, erode_groups=args.erode_groups,
-                      fft_stages_only=args.fft_stages_only)
+                      fft_stages_only=args.fft_stages_only, accessible_by_sweep=args.accessible_by_sweep)
     imf.set_tools(d.tools)
     info = imf.tool_info(0)
     rho = torch.from_numpy(d.rho).to(dev)
@@ -362,13 +362,14 @@ def run_ours(args):
     info = imf.tool_info(0)
     fbar = torch.empty_like(rho)
     sec = torch.empty(shape, dtype=torch.uint8, device=dev)
+    acc_step = torch.empty(shape, dtype=torch.uint8, device=dev)   # the accessible set, every step
     sens0 = torch.from_numpy(np.random.default_rng(rank).normal(size=shape).astype(np.float32)).to(dev)
     sens = sens0.clone()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        imf.compute(rho, fix, fbar, sec, stream=stream)
+        imf.compute(rho, fix, fbar, sec, accessible=acc_step, stream=stream)
         imf.penalize(sens, rho, fbar, sec, fix, w_acc=0.5, stream=stream)
 
     def timed_steps(k):
@@ -455,22 +456,23 @@ def run_ours(args):
         hf = torch.from_numpy(d.fixture).pin_memory() if d.fixture is not None else None
         ob = torch.empty(shape, dtype=torch.float32).pin_memory()
         osec = torch.empty(shape, dtype=torch.uint8).pin_memory()
+        oacc = torch.empty(shape, dtype=torch.uint8).pin_memory()
         lib = imf.lib
         for _ in range(2):
             lib.imf_compute_host(imf.h, hr.data_ptr(), hf.data_ptr() if hf is not None else None, ob.data_ptr(),
-                                 osec.data_ptr(), None, None, stream.cuda_stream)
+                                 osec.data_ptr(), None, oacc.data_ptr(), stream.cuda_stream)
         et = []
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st = lib.imf_compute_host(imf.h, hr.data_ptr(), hf.data_ptr() if hf is not None else None,
-                                      ob.data_ptr(), osec.data_ptr(), None, None, stream.cuda_stream)
+                                      ob.data_ptr(), osec.data_ptr(), None, oacc.data_ptr(), stream.cuda_stream)
             et.append(time.perf_counter() - t0)
             assert st == 0, imf.lib.imf_last_error(imf.h)
         e_s = reduce_max(statistics.mean(et), dev)
         e2e = {"value": ws * nG * n_orient / e_s, "unit": UNIT, "h2d_bytes_per_step": nG * 4 + (nG if hf is not None else 0),
-               "d2h_bytes_per_step": nG * 4 + nG, "entry_point": "imf_compute_host (pinned host buffers)"}
+               "d2h_bytes_per_step": nG * 4 + 2 * nG, "entry_point": "imf_compute_host (pinned host buffers)"}
 
     if rank != 0:
         if ws > 1:
@@ -489,9 +491,13 @@ def run_ours(args):
     pts = [np.array(np.unravel_index(np.argmax(np.where(om0, f, -1)), shape))[::-1]]
     for _ in range(args.error_points - 1):
         pts.append(np.array([rng.integers(0, shape[2]), rng.integers(0, shape[1]), rng.integers(0, shape[0])]))
-    fo, _ = oracle.point_query(d.rho, d.fixture, d.tools, np.array(pts))
+    fo, Ao = oracle.point_query(d.rho, d.fixture, d.tools, np.array(pts))
     M = float(f[pts[0][2], pts[0][1], pts[0][0]])
     err = max(abs(float(f[z, y, x]) - fv) for (x, y, z), fv in zip(pts, fo)) / max(M, 1e-30)
+    a_np = acc.cpu().numpy()
+    theta = 0.01 * float(sum(((t.holder != 0) | (t.cutter != 0)).sum() for t in d.tools[:1]))
+    acc_mismatch = sum(int(a_np[z, y, x] != av) for (x, y, z), fv, av in zip(pts, fo, Ao)
+                       if om0[z, y, x] and abs(fv - theta) > 1e-3 * theta / 0.01)
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -505,9 +511,14 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": dict(workload_config(args.workload, d), l2="256 MiB buffer written between timed steps",
                           fft_grid=list(info.P), translation_window=list(info.win),
-                          collision_path={1: "fp32_fft", 2: "bf16_direct_tcgen05"}[imf.tool_info(0).path]),
+                          collision_path={1: "fp32_fft", 2: "bf16_direct_tcgen05"}[imf.tool_info(0).path],
+                          accessible=("sweep of the free translations by the cutter (Eq. eq_conv_A)"
+                                      if args.accessible_by_sweep or len(d.tools) > 1
+                                      or any(getattr(t, "sharp", None) is not None for t in d.tools)
+                                      else "A = [f <= theta]: sharp points = the whole cutter (App. A)")),
            "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
-           "imf_error": {"max_abs_over_max_f": err, "points": len(pts), "vs": "FP64 oracle point queries"},
+           "imf_error": {"max_abs_over_max_f": err, "points": len(pts), "vs": "FP64 oracle point queries",
+                         "accessible_mismatches": acc_mismatch},
            "near_threshold_rechecked": int(flagged),
            "roofline": roof, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": int(launches), "clocks": clk.summary()}
@@ -530,6 +541,8 @@ def main():
     ap.add_argument("--orient-batch", type=int, default=0, help="orientations per device batch (0: library default)")
     ap.add_argument("--erode-groups", type=int, default=0,
                     help="orientation groups per tile of the minimum over sharp points (0: library default)")
+    ap.add_argument("--accessible-by-sweep", action="store_true",
+                    help="build the accessible set by the sweep even where A = [f <= theta] is exact")
     ap.add_argument("--fft-stages-only", action="store_true",
                     help="radix-stage FFT passes everywhere (comparison with the two-pass register FFT)")
     ap.add_argument("--precision", choices=["auto", "fft", "direct"], default="fft",

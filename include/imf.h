@@ -76,6 +76,11 @@ typedef struct {
                                 0 = chosen from the grid and the SM count                      */
     int fft_stages_only;     /* 1: every FFT pass uses radix stages (2..8) even where a two-pass
                                 register split exists (comparisons and tests); 0 = default    */
+    int accessible_by_sweep; /* the accessible output of imf_compute: 0 = with one tool whose
+                                sharp points are its whole cutter, A = [f <= theta] (exact:
+                                both say "some cutter point lies on a free translation"; the
+                                route of App. A), else the sweep of Eq. eq_conv_A; 1 = always
+                                the sweep                                                      */
 } imf_options;
 
 /* Fill *opt with the defaults above (grid 0x0x0, which imf_create rejects). */

@@ -33,7 +33,7 @@ class ImfOptions(ctypes.Structure):
                 ("theta_rel", ctypes.c_double), ("precision", ctypes.c_int), ("recheck", ctypes.c_int),
                 ("recheck_band", ctypes.c_double), ("orient_batch", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("erode_groups", ctypes.c_int),
-                ("fft_stages_only", ctypes.c_int)]
+                ("fft_stages_only", ctypes.c_int), ("accessible_by_sweep", ctypes.c_int)]
 
 
 class ImfToolInfo(ctypes.Structure):
@@ -153,7 +153,8 @@ class Imf:
     """One design grid on the current CUDA device; mirrors the C ABI one-to-one."""
 
     def __init__(self, shape_zyx, lam=0.01, tau=0.5, theta_rel=0.01, precision=IMF_AUTO, recheck=True,
-                 recheck_band=0.0, orient_batch=0, hbm_budget_bytes=0, voxel=1.0, erode_groups=0, fft_stages_only=False):
+                 recheck_band=0.0, orient_batch=0, hbm_budget_bytes=0, voxel=1.0, erode_groups=0, fft_stages_only=False,
+                 accessible_by_sweep=False):
         self.lib = load()
         opt = ImfOptions()
         self.lib.imf_default_options(ctypes.byref(opt))
@@ -164,6 +165,7 @@ class Imf:
         opt.orient_batch, opt.hbm_budget_bytes = orient_batch, hbm_budget_bytes
         opt.erode_groups = erode_groups
         opt.fft_stages_only = int(fft_stages_only)
+        opt.accessible_by_sweep = int(accessible_by_sweep)
         self.shape = (nz, ny, nx)
         self.opt = opt
         h = ctypes.c_void_p()

@@ -66,6 +66,7 @@ struct Tool {
     long n_rt = 0, n_rk = 0, n_sh = 0;
     std::vector<int> perm, iperm;        // internal orientation order -> caller's index, and back
     int path = IMF_FP32_FFT;             // collision path in use
+    bool sharp_is_cutter = true;         // sharp points = every cutter voxel (no proper subset)
     bool has_spec = false;               // FFT spectra built
     // direct tensor-core path
     bool dir_ok = false;
@@ -128,6 +129,7 @@ struct imf_handle_s {
     cudaGraphExec_t graph_exec = nullptr;
     // debug
     bool keep_g = false;
+    bool run_sweep = true;      // this compute builds A by the sweep (else A = [f <= theta])
     int last_batch_base = -1, last_batch_n = 0, last_tool = -1;
 };
 
@@ -666,6 +668,8 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
         nT += T[i];
     }
     if (nK == 0) return fail(h, IMF_ERR_INVALID_ARG, "empty cutter");
+    bool sharp_all = true;
+    for (long i = 0; i < tv; ++i) sharp_all = sharp_all && S[i] == K[i];
     for (int i = 0; i < n_orient; ++i) {
         const double *q = quats + 4 * i;
         const double nn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
@@ -679,6 +683,7 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
     t.n_orient = n_orient;
     t.size_T = nT;
     t.theta = h->opt.theta_rel * (double)nT;
+    t.sharp_is_cutter = sharp_all;
 
     // --- orientation order: nearest-neighbour chain (groups of the direct path stay compact);
     // results never depend on it, only the grouping of device work does
@@ -932,7 +937,7 @@ imf_status tail_batch(imf_handle h, const Tool &t, const float *rho, const uint8
         Launch L(h, KID_RECHECK, s);
         launch_recheck_blocks(a, 152 * 8, s);
     }
-    {
+    if (h->run_sweep) {
         SweepArgs a{};
         a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
         a.iv = t.iv; a.iv_start = t.iv_start; a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.awords = h->awords;
@@ -980,7 +985,11 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
         Launch L(h, KID_INIT, s);
         launch_fill_f32(h->f, INFINITY, N, s);
     }
-    CU(cudaMemsetAsync(h->A, 0, sizeof(uint32_t) * (size_t)op.nz * op.ny * h->awords, s));
+    // the accessible output: from the minimum when that is exact (one tool, sharp points = the
+    // whole cutter), else by the sweep; neither when the caller does not ask for it
+    const bool acc_from_f = acc && !op.accessible_by_sweep && h->n_tools == 1 && h->tools[0].sharp_is_cutter;
+    h->run_sweep = acc && !acc_from_f;
+    if (h->run_sweep) CU(cudaMemsetAsync(h->A, 0, sizeof(uint32_t) * (size_t)op.nz * op.ny * h->awords, s));
     CU(cudaMemsetAsync(maxbits, 0, sizeof(unsigned), s));
     CU(cudaMemsetAsync(h->dev_small + 4, 0, sizeof(int), s));
     for (int ti = 0; ti < h->n_tools; ++ti) {
@@ -1074,6 +1083,7 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
         a.f = h->f; a.rho = rho; a.fix = fix; a.A = h->A; a.nx = op.nx; a.ny = op.ny; a.nz = op.nz;
         a.awords = h->awords; a.maxbits = maxbits; a.lambda = op.lambda; a.tau = op.tau;
         a.fbar = fbar; a.secluded = sec; a.raw = raw; a.acc = acc;
+        a.acc_from_f = acc_from_f; a.theta = (float)h->tools[0].theta;
         Launch L(h, KID_FINALIZE, s);
         launch_finalize(a, s);
     }

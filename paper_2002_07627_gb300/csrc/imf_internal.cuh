@@ -220,6 +220,8 @@ struct FinalizeArgs {
     uint8_t *secluded;
     float *raw;
     uint8_t *acc;
+    int acc_from_f;              // acc = [f <= theta] instead of the swept bits A
+    float theta;
 };
 void launch_finalize(const FinalizeArgs &a, cudaStream_t s);
 void launch_absmax_omega0(const float *v, const uint8_t *fix, long n, unsigned *maxbits, cudaStream_t s);

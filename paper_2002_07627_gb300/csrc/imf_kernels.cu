@@ -348,10 +348,17 @@ __global__ void finalize_kernel(FinalizeArgs a)
         a.secluded[idx] = (uint8_t)(B && !((double)a.rho[idx] > a.tau));
         if (a.raw) a.raw[idx] = f;
         if (a.acc) {
-            const int x = (int)(idx % a.nx);
-            const long row = idx / a.nx;
-            const uint32_t w = a.A[row * a.awords + (x >> 5)];
-            a.acc[idx] = (uint8_t)(!fixc && ((w >> (x & 31)) & 1u));
+            if (a.acc_from_f) {
+                // sharp points = the whole cutter, one tool: some cutter point lies on a free
+                // translation iff the minimum over sharp points is <= theta (Eq. eq_imf_2 vs
+                // Eq. eq_conv_A; the FP32 comparison of the free bits)
+                a.acc[idx] = (uint8_t)(!fixc && f <= a.theta);
+            } else {
+                const int x = (int)(idx % a.nx);
+                const long row = idx / a.nx;
+                const uint32_t w = a.A[row * a.awords + (x >> 5)];
+                a.acc[idx] = (uint8_t)(!fixc && ((w >> (x & 31)) & 1u));
+            }
         }
     }
 }

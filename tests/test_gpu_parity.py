@@ -361,3 +361,28 @@ def test_both_fft_variants_match_oracle(stages_only):
     check_against_oracle(d, got, ref)
     info = got["imf"].tool_info(0)
     assert all(p <= 256 for p in info.P)      # both variants run the same padded lengths
+
+
+def test_accessible_from_the_minimum_equals_the_sweep():
+    """With one tool whose sharp points are its whole cutter, the library reads A off the
+    minimum, A = [f <= theta] (App. A); the sweep of Eq. eq_conv_A (forced) must give the same
+    set except where f lies within FP32 rounding of theta, and both meet the contract against
+    the oracle. A sharp-point subset (or a second tool) falls back to the sweep by itself."""
+    for seed, n in ((3, (31, 40, 47)), (8, (20, 26, 33))):
+        d = _small3d(seed=seed, n=n, n_orient=7)
+        ref = oracle.imf(d)
+        a = run_gpu(d, orient_batch=4)
+        b = run_gpu(d, orient_batch=4, accessible_by_sweep=True)
+        check_against_oracle(d, a, ref)
+        check_against_oracle(d, b, ref)
+        theta = 0.01 * float(((d.tools[0].holder != 0) | (d.tools[0].cutter != 0)).sum())
+        assert np.array_equal(a["f"], b["f"])
+        differ = a["accessible"] != b["accessible"]
+        assert not np.any(differ & (np.abs(a["f"] - theta) > 1e-5 * theta))
+        assert b["imf"].stats().launches > a["imf"].stats().launches   # the sweep ran only in b
+    # sharp subset: the default path sweeps and agrees with the oracle
+    d = _small3d(seed=5, n=(25, 30, 35), n_orient=5)
+    sharp = np.zeros_like(d.tools[0].cutter)
+    sharp[: sharp.shape[0] // 2] = 1
+    d.tools[0].sharp = sharp
+    check_against_oracle(d, run_gpu(d, orient_batch=4), oracle.imf(d))
