@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kT2) irfft2_threshold_kernel(IrfftArgs a)
     for (int ww = warp; ww < R; ww += kT2 / 32) {
         const int rr = r0 + ww;
         if (rr >= a.rows) break;  // warp-uniform
-        threshold_row(a, tile + ww * ld, 1, o, rr, lane);
+        threshold_row_any(a, tile + ww * ld, 1, o, rr, lane);
     }
 }
 

@@ -210,7 +210,7 @@ template <int LOGW> __global__ void __launch_bounds__(kThreads) irfft_threshold_
     for (int w = warp; w < W; w += nwarp) {
         const int r = r0 + w;
         if (r >= a.rows) break;  // warp-uniform
-        threshold_row(a, src + w, ld, o, r, lane);
+        threshold_row_any(a, src + w, ld, o, r, lane);
     }
 }
 

@@ -1065,6 +1065,7 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
                 a.status = status;
                 a.orient_base = o0; a.M = t.M; a.twM = t.twM; a.twP = t.twP; a.plan = t.plM;
                 a.A2 = t.sM[0]; a.B2 = t.sM[1];
+                a.write_bits = h->run_sweep || h->keep_g;
                 Launch L(h, KID_IRFFT_THRESH, s);
                 launch_irfft_threshold(a, nb, s);
             }

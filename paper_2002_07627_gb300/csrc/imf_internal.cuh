@@ -74,6 +74,7 @@ struct IrfftArgs {
     const float2 *twM, *twP;
     FftPlan plan;
     int A2, B2;                  // two-pass split M = A2 B2 (fft2.cuh), or 0: Stockham stages
+    int write_bits;              // store the free bits (the sweep or a debug copy reads them)
 };
 
 void launch_axis_fft(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s);
