@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(kT2) irfft2_threshold_kernel(IrfftArgs a)
         }
     }
     __syncthreads();
-    // pass 2 (every thread enters: the size is uniform and the barrier inside is reached by all)
+    // pass 2 (every thread enters: the size is uniform and the barriers inside are reached by all)
+    const int lane = threadIdx.x & 31;
     {
         const int w = threadIdx.x / A, p = threadIdx.x - w * A;
         const bool act = w < R && r0 + w < a.rows;
@@ -172,6 +173,30 @@ __global__ void __launch_bounds__(kT2) irfft2_threshold_kernel(IrfftArgs a)
                 for (int n1 = 0; n1 < NB; ++n1) u[n1] = line[n1 * Ap + p];
                 fft2::dft_reg<1, NB>(u);
             }
+            if (!a.write_bits) {
+                // thread (row w, k2 = p) holds z[p + A k1]: g[2j] = Re, g[2j+1] = Im for
+                // j = p + A k1, clamped at 0, written straight from registers (consecutive
+                // lanes, consecutive j), near-threshold translations listed for the re-check
+                int y = 0, z = 0;
+                if (act) {
+                    y = (r0 + w) % a.rows_y;
+                    z = (r0 + w) / a.rows_y;
+                }
+                float *grow = a.g + o * a.g_so + z * a.g_sz + y * a.g_sy;
+                const long lrow = ((long)z * a.rows_y + y) * a.nout;
+#pragma unroll
+                for (int k1 = 0; k1 < NB; ++k1) {
+                    const int i0 = 2 * (p + A * k1);
+                    const bool v0 = act && i0 < a.nout, v1 = act && i0 + 1 < a.nout;
+                    const float g0 = fmaxf(u[k1].x, 0.f), g1 = fmaxf(u[k1].y, 0.f);
+                    if (v1) *reinterpret_cast<float2 *>(grow + i0) = make_float2(g0, g1);
+                    else if (v0) grow[i0] = g0;
+                    if (a.flag)
+                        record_near(a, o, lrow + i0, v0 && fabsf(g0 - a.theta) <= a.band,
+                                    v1 && fabsf(g1 - a.theta) <= a.band, lane);
+                }
+                return;
+            }
             __syncthreads();
             if (act) {
 #pragma unroll
@@ -179,12 +204,13 @@ __global__ void __launch_bounds__(kT2) irfft2_threshold_kernel(IrfftArgs a)
             }
         });
     }
+    if (!a.write_bits) return;   // uniform: the outputs are written
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5;
     for (int ww = warp; ww < R; ww += kT2 / 32) {
         const int rr = r0 + ww;
         if (rr >= a.rows) break;  // warp-uniform
-        threshold_row_any(a, tile + ww * ld, 1, o, rr, lane);
+        threshold_row<true>(a, tile + ww * ld, 1, o, rr, lane);
     }
 }
 
