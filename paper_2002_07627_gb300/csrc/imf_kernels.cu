@@ -330,18 +330,19 @@ __global__ void max_omega0_kernel(const float *f, const uint8_t *fix, long n, un
     if (threadIdx.x == 0) atomicMax(maxbits, __float_as_uint(m));
 }
 
-// Alg. 1 tail: f_bar = f / M (FP64), B = [f_bar > lambda], f_bar <- f_bar B,
-// Gamma = Omega_0 [rho <= tau] B; outputs on fixture cells are 0.
+// Alg. 1 tail: f_bar = f / M (FP64, as f times the FP64 reciprocal of M: within one FP64 ulp of
+// the quotient, and FP64 division per voxel is slow on this part), B = [f_bar > lambda],
+// f_bar <- f_bar B, Gamma = Omega_0 [rho <= tau] B; outputs on fixture cells are 0.
 __global__ void finalize_kernel(FinalizeArgs a)
 {
     const long n = (long)a.nx * a.ny * a.nz;
     const float Mf = __uint_as_float(*a.maxbits);
-    const double M = (double)Mf;
     const bool ok = Mf > 0.f && Mf <= FLT_MAX;
+    const double invM = ok ? 1.0 / (double)Mf : 0.0;
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
         const float f = a.f[idx];
         const bool fixc = a.fix && a.fix[idx];
-        double fb = (ok && !fixc) ? (double)f / M : 0.0;
+        double fb = (ok && !fixc) ? (double)f * invM : 0.0;
         const bool B = fb > a.lambda;
         if (!B) fb = 0.0;
         a.fbar[idx] = (float)fb;
