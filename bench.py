@@ -132,8 +132,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes(kernel, info, shape, nb):
-    """Bytes a launch must move at minimum (per launch, nb orientations), by kernel class."""
+def algorithmic_bytes(kernel, info, shape, nb, bits=True):
+    """Bytes a launch must move at minimum (per launch, nb orientations), by kernel class; `bits`:
+    the inverse x pass also stores the free bits (only the sweep route reads them)."""
     Px, Py, Pz = info.P
     Hx = Px // 2 + 1
     Wx, Wy, Wz = info.win
@@ -146,7 +147,7 @@ def algorithmic_bytes(kernel, info, shape, nb):
     if kernel == "fft_y_inv":
         return nb * (Wz * Py * Hx * 8 + Wz * Wy * Hx * 8)
     if kernel == "irfft_x_threshold":
-        return nb * (Wz * Wy * Hx * 8 + Wz * Wy * Wx * 4 + Wz * Wy * bitsw)
+        return nb * (Wz * Wy * Hx * 8 + Wz * Wy * Wx * 4 + (Wz * Wy * bitsw if bits else 0))
     if kernel == "erode_min":
         return nb * Wz * Wy * Wx * 4 + 2 * nG * 4
     if kernel == "sweep_dilate":
@@ -411,7 +412,9 @@ def run_ours(args):
     dom = max(((k, v) for k, v in kt.items()), key=lambda kv: kv[1][0])
     dname, (dms, dcnt) = dom
     nb = max(1.0, n_orient * args.steps / max(1, kt.get("fft_z_inv_mul", (0, 1))[1]))
-    abytes = algorithmic_bytes(dname, info, shape, nb)
+    sweep_route = args.accessible_by_sweep or len(d.tools) > 1 or any(getattr(t, "sharp", None) is not None
+                                                                      for t in d.tools)
+    abytes = algorithmic_bytes(dname, info, shape, nb, bits=sweep_route)
     hbm, bf16, peak_src = measured_peaks()
     roof = None
     avg_s = dms / dcnt * 1e-3
