@@ -174,11 +174,14 @@ def traffic_record(kernel, workload):
     rec = d.get(kernel)
     if not rec or rec.get("workload") != workload:
         return None
-    src = os.path.join(ROOT, rec["source"])
-    if not os.path.exists(src):
-        return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if h != rec.get("source_sha256_16"):
+    srcs = rec.get("sources") or [rec.get("source")]
+    hsh = hashlib.sha256()
+    for src in srcs:
+        path = os.path.join(ROOT, src)
+        if not os.path.exists(path):
+            return None
+        hsh.update(open(path, "rb").read())
+    if hsh.hexdigest()[:16] != rec.get("source_sha256_16"):
         return None
     return rec.get("bytes_per_launch")
 
