@@ -355,8 +355,12 @@ def run_ours(args):
     nG = int(np.prod(shape))
     n_orient = sum(len(t.quats) for t in d.tools)
     prec = {"auto": 0, "fft": 1, "direct": 2}[args.precision]
+    # the timed step runs every step of the method as its own kernel, the sweep of the free
+    # translations (Eq. eq_conv_A) included; --accessible-from-imf times the library's default
+    # route instead (A read off the minimum where that is exact, App. A)
+    by_sweep = not args.accessible_from_imf
     imf = binding.Imf(shape, orient_batch=args.orient_batch, precision=prec, erode_groups=args.erode_groups,
-                      fft_stages_only=args.fft_stages_only, accessible_by_sweep=args.accessible_by_sweep)
+                      fft_stages_only=args.fft_stages_only, accessible_by_sweep=by_sweep)
     imf.set_tools(d.tools)
     info = imf.tool_info(0)
     rho = torch.from_numpy(d.rho).to(dev)
@@ -376,13 +380,14 @@ def run_ours(args):
         imf.compute(rho, fix, fbar, sec, accessible=acc_step, stream=stream)
         imf.penalize(sens, rho, fbar, sec, fix, w_acc=0.5, stream=stream)
 
-    def timed_steps(k):
+    def timed_steps(k, fn=None):
+        fn = fn or step
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         for a, b in ev:
             flush.zero_()
             sens.copy_(sens0)
             a.record(stream)
-            step()
+            fn()
             b.record(stream)
         torch.cuda.synchronize()
         return [a.elapsed_time(b) for a, b in ev]
@@ -409,6 +414,28 @@ def run_ours(args):
     # latency percentiles over at least 200 calls (L2 flushed before each), outside the timed region
     lat = times if len(times) >= 200 else timed_steps(max(200, args.latency_calls))
 
+    # the other route for the accessible set, on a second handle, timed the same way
+    alt = binding.Imf(shape, orient_batch=args.orient_batch, precision=prec, erode_groups=args.erode_groups,
+                      fft_stages_only=args.fft_stages_only, accessible_by_sweep=not by_sweep)
+    alt.set_tools(d.tools)
+    if args.precision == "auto":
+        alt.autotune(rho, fix)
+
+    def alt_step():
+        alt.compute(rho, fix, fbar, sec, accessible=acc_step, stream=stream)
+        alt.penalize(sens, rho, fbar, sec, fix, w_acc=0.5, stream=stream)
+
+    for _ in range(args.warmup):
+        alt_step()
+    alt.sync()
+    alt_ms = reduce_max(sum(timed_steps(args.steps, alt_step)), dev) / args.steps
+    alt.sync()
+    alt.close()
+    variant = {("accessible_from_imf" if by_sweep else "accessible_by_sweep"): {
+        "ms_per_step": alt_ms, "value": ws * nG * n_orient / (alt_ms * 1e-3),
+        "accessible": ("A = [f <= theta] where exact (one tool, sharp points = the whole cutter), the library "
+                       "default" if by_sweep else "sweep of the free translations (Eq. eq_conv_A)")}}
+
     # per-kernel times with CUDA events on the launching stream (separate pass of K steps)
     imf.reset_kernel_times()
     imf.set_profiling(True)
@@ -418,8 +445,7 @@ def run_ours(args):
     dom = max(((k, v) for k, v in kt.items()), key=lambda kv: kv[1][0])
     dname, (dms, dcnt) = dom
     nb = max(1.0, n_orient * args.steps / max(1, kt.get("fft_z_inv_mul", (0, 1))[1]))
-    sweep_route = args.accessible_by_sweep or len(d.tools) > 1 or any(getattr(t, "sharp", None) is not None
-                                                                      for t in d.tools)
+    sweep_route = by_sweep or len(d.tools) > 1 or any(getattr(t, "sharp", None) is not None for t in d.tools)
     abytes = algorithmic_bytes(dname, info, shape, nb, bits=sweep_route)
     hbm, bf16, peak_src = measured_peaks()
     roof = None
@@ -522,10 +548,11 @@ def run_ours(args):
                           fft_grid=list(info.P), translation_window=list(info.win),
                           collision_path={1: "fp32_fft", 2: "bf16_direct_tcgen05"}[imf.tool_info(0).path],
                           accessible=("sweep of the free translations by the cutter (Eq. eq_conv_A)"
-                                      if args.accessible_by_sweep or len(d.tools) > 1
+                                      if by_sweep or len(d.tools) > 1
                                       or any(getattr(t, "sharp", None) is not None for t in d.tools)
                                       else "A = [f <= theta]: sharp points = the whole cutter (App. A)")),
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)), "calls": len(lat)},
+           "variants": variant,
            "imf_error": {"max_abs_over_max_f": err, "points": len(pts), "vs": "FP64 oracle point queries",
                          "accessible_mismatches": acc_mismatch},
            "near_threshold_rechecked": int(flagged),
@@ -551,8 +578,9 @@ def main():
     ap.add_argument("--orient-batch", type=int, default=0, help="orientations per device batch (0: library default)")
     ap.add_argument("--erode-groups", type=int, default=0,
                     help="orientation groups per tile of the minimum over sharp points (0: library default)")
-    ap.add_argument("--accessible-by-sweep", action="store_true",
-                    help="build the accessible set by the sweep even where A = [f <= theta] is exact")
+    ap.add_argument("--accessible-from-imf", action="store_true",
+                    help="time the library's default route for the accessible set (A = [f <= theta] where "
+                         "exact) instead of the sweep")
     ap.add_argument("--fft-stages-only", action="store_true",
                     help="radix-stage FFT passes everywhere (comparison with the two-pass register FFT)")
     ap.add_argument("--precision", choices=["auto", "fft", "direct"], default="fft",
