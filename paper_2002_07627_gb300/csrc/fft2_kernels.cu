@@ -123,6 +123,10 @@ __global__ void __launch_bounds__(kT2) irfft2_threshold_kernel(IrfftArgs a)
     const int A = a.A2, B = a.B2, M = a.M, Ap = A | 1, R = kT2 / A;
     const int ld = max(M, B * Ap) + 1;
     float2 *tile = sm, *twM = sm + R * ld, *twP = twM + M;
+    // free flags of the block's rows, one byte per translation; rows of fp >= 2 M >= nout bytes,
+    // 16-byte aligned
+    const int fp = (2 * M + 31) & ~31;
+    uint8_t *sflag = reinterpret_cast<uint8_t *>(sm + ((R * ld + 2 * M + 2) & ~1));
     for (int i = threadIdx.x; i < M; i += kT2) twM[i] = a.twM[i];
     for (int i = threadIdx.x; i <= M; i += kT2) twP[i] = a.twP[i];
     __syncthreads();
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(kT2) irfft2_threshold_kernel(IrfftArgs a)
         }
     }
     __syncthreads();
-    // pass 2 (every thread enters: the size is uniform and the barriers inside are reached by all)
+    // pass 2 (every thread enters the uniform size dispatch; inactive threads store nothing)
     const int lane = threadIdx.x & 31;
     {
         const int w = threadIdx.x / A, p = threadIdx.x - w * A;
@@ -173,44 +177,57 @@ __global__ void __launch_bounds__(kT2) irfft2_threshold_kernel(IrfftArgs a)
                 for (int n1 = 0; n1 < NB; ++n1) u[n1] = line[n1 * Ap + p];
                 fft2::dft_reg<1, NB>(u);
             }
-            if (!a.write_bits) {
-                // thread (row w, k2 = p) holds z[p + A k1]: g[2j] = Re, g[2j+1] = Im for
-                // j = p + A k1, clamped at 0, written straight from registers (consecutive
-                // lanes, consecutive j), near-threshold translations listed for the re-check
-                int y = 0, z = 0;
-                if (act) {
-                    y = (r0 + w) % a.rows_y;
-                    z = (r0 + w) / a.rows_y;
-                }
-                float *grow = a.g + o * a.g_so + z * a.g_sz + y * a.g_sy;
-                const long lrow = ((long)z * a.rows_y + y) * a.nout;
-#pragma unroll
-                for (int k1 = 0; k1 < NB; ++k1) {
-                    const int i0 = 2 * (p + A * k1);
-                    const bool v0 = act && i0 < a.nout, v1 = act && i0 + 1 < a.nout;
-                    const float g0 = fmaxf(u[k1].x, 0.f), g1 = fmaxf(u[k1].y, 0.f);
-                    if (v1) *reinterpret_cast<float2 *>(grow + i0) = make_float2(g0, g1);
-                    else if (v0) grow[i0] = g0;
-                    if (a.flag)
-                        record_near(a, o, lrow + i0, v0 && fabsf(g0 - a.theta) <= a.band,
-                                    v1 && fabsf(g1 - a.theta) <= a.band, lane);
-                }
-                return;
-            }
-            __syncthreads();
+            // thread (row w, k2 = p) holds z[p + A k1]: g[2j] = Re, g[2j+1] = Im for j = p + A k1,
+            // clamped at 0, written straight from registers (consecutive lanes, consecutive j);
+            // the free flags g <= theta go to shared memory as bytes and near-threshold
+            // translations are listed for the re-check
+            int y = 0, z = 0;
             if (act) {
+                y = (r0 + w) % a.rows_y;
+                z = (r0 + w) / a.rows_y;
+            }
+            float *grow = a.g + o * a.g_so + z * a.g_sz + y * a.g_sy;
+            const long lrow = ((long)z * a.rows_y + y) * a.nout;
 #pragma unroll
-                for (int k1 = 0; k1 < NB; ++k1) line[p + A * k1] = u[k1];
+            for (int k1 = 0; k1 < NB; ++k1) {
+                const int i0 = 2 * (p + A * k1);
+                const bool v0 = act && i0 < a.nout, v1 = act && i0 + 1 < a.nout;
+                const float g0 = fmaxf(u[k1].x, 0.f), g1 = fmaxf(u[k1].y, 0.f);
+                if (v1) *reinterpret_cast<float2 *>(grow + i0) = make_float2(g0, g1);
+                else if (v0) grow[i0] = g0;
+                if (a.write_bits && v0)
+                    *reinterpret_cast<uint16_t *>(sflag + w * fp + i0) =
+                        (uint16_t)((g0 <= a.theta ? 1u : 0u) | (v1 && g1 <= a.theta ? 0x100u : 0u));
+                if (a.flag)
+                    record_near(a, o, lrow + i0, v0 && fabsf(g0 - a.theta) <= a.band,
+                                v1 && fabsf(g1 - a.theta) <= a.band, lane);
             }
         });
     }
-    if (!a.write_bits) return;   // uniform: the outputs are written
+    if (!a.write_bits) return;   // uniform
     __syncthreads();
-    const int warp = threadIdx.x >> 5;
-    for (int ww = warp; ww < R; ww += kT2 / 32) {
-        const int rr = r0 + ww;
-        if (rr >= a.rows) break;  // warp-uniform
-        threshold_row<true>(a, tile + ww * ld, 1, o, rr, lane);
+    // one free-bit word (32 translations along x) per thread, packed from its 32 flag bytes:
+    // for a 4-byte group v with bytes b_i in {0, 1}, the multiplier 0x01020408 = 2^24 + 2^17 +
+    // 2^10 + 2^3 moves byte i (bit 8 i) to bit 24 + i and every cross term to a distinct bit
+    // below 24 (no carries); bytes past nout are masked off
+    const int nwq = (a.nout + 31) >> 5;
+    for (int i = threadIdx.x; i < R * nwq; i += kT2) {
+        const int ww = i / nwq, q = i - ww * nwq, rr = r0 + ww;
+        if (rr >= a.rows) break;   // later i only have larger rows
+        const uint4 *fw = reinterpret_cast<const uint4 *>(sflag + ww * fp + 32 * q);
+        uint32_t word = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint4 v = fw[h];
+            const uint32_t g4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                word |= (((g4[k] & 0x01010101u) * 0x01020408u) >> 24 & 0xfu) << (16 * h + 4 * k);
+        }
+        const int rem = a.nout - 32 * q;
+        if (rem < 32) word &= (1u << rem) - 1u;
+        const int y = rr % a.rows_y, z = rr / a.rows_y;
+        a.bits[o * a.b_so + z * a.b_sz + y * a.b_sy + q] = word;
     }
 }
 
@@ -225,7 +242,10 @@ size_t axis2_smem(int L) { return (size_t)(L * kW2 + L) * sizeof(float2); }
 
 size_t irfft2_smem(int M, int A, int B)
 {
-    return (size_t)((kT2 / A) * (std::max(M, B * (A | 1)) + 1) + 2 * M + 1) * sizeof(float2);
+    // R rows of flag bytes (the window has at most 2 M translations along x, rows padded to 32
+    // bytes) after the tables, starting on a 16-byte boundary
+    const int R = kT2 / A, ld = std::max(M, B * (A | 1)) + 1, fp = (2 * M + 31) & ~31;
+    return (size_t)(((R * ld + 2 * M + 2) & ~1) + (R * fp + 7) / 8) * sizeof(float2);
 }
 
 void launch_axis2(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s)

@@ -33,12 +33,12 @@ namespace {
 enum KernelId {
     KID_ROTATE, KID_SPEC, KID_RFFT_FWD, KID_AXIS_FWD, KID_AXIS_INV_MUL, KID_AXIS_INV, KID_IRFFT_THRESH,
     KID_RECHECK, KID_SWEEP, KID_ERODE, KID_INIT, KID_MAX, KID_FINALIZE, KID_ABSMAX, KID_PENALIZE, KID_RHO_HL,
-    KID_DIRECT, KID_COUNT
+    KID_DIRECT, KID_SWEEP_LEVELS, KID_COUNT
 };
 const char *kKernelNames[KID_COUNT] = {
     "rotate_resample", "tool_spectrum", "rfft_x_fwd", "fft_axis_fwd", "fft_z_inv_mul", "fft_y_inv",
     "irfft_x_threshold", "recheck_near_threshold", "sweep_dilate", "erode_min", "init", "max_omega0",
-    "finalize", "absmax_omega0", "penalize", "rho_hi_lo", "direct_corr_tcgen05"};
+    "finalize", "absmax_omega0", "penalize", "rho_hi_lo", "direct_corr_tcgen05", "sweep_levels"};
 
 struct Tool {
     bool set = false;
@@ -56,8 +56,8 @@ struct Tool {
     size_t spec_bytes = 0;
     uint32_t *rt_off = nullptr;
     int *rt_start = nullptr;
-    int4 *iv = nullptr;
-    int *iv_start = nullptr;
+    int4 *sw_pairs = nullptr;            // sweep run descriptors (SweepArgs::pairs), all orientations
+    int *sw_start = nullptr;
     ErodeChunk *er_chunks = nullptr;
     int *er_chunk_start = nullptr;
     int2 *er_runs = nullptr;
@@ -360,8 +360,8 @@ void free_tool(imf_handle h, Tool &t)
     dfree(h, t.spec, t.spec_bytes / sizeof(float2));
     dfree(h, t.rt_off, (size_t)t.n_rt);
     dfree(h, t.rt_start, (size_t)t.n_orient + 1);
-    dfree(h, t.iv, (size_t)0);
-    dfree(h, t.iv_start, (size_t)t.n_orient + 1);
+    dfree(h, t.sw_pairs, (size_t)0);
+    dfree(h, t.sw_start, (size_t)t.n_orient + 1);
     dfree(h, t.er_chunks);
     dfree(h, t.er_chunk_start);
     dfree(h, t.er_runs);
@@ -495,10 +495,10 @@ imf_status ensure_work(imf_handle h)
     int want = op.orient_batch > 0 ? op.orient_batch : 16;
     want = std::max(std::min(want, maxo), min_slots);
     // per orientation slot: Y1, Y2, g, free bits and its share of the near-threshold list
-    const size_t per_slot = y1 * 8 + y2 * 8 + gn * 4 + bn * 4 + (gn / 32 + 1) * sizeof(int2);
+    const size_t per_slot = y1 * 8 + y2 * 8 + gn * 4 + bn * 4 * kSweepLevels + (gn / 32 + 1) * sizeof(int2);
     if (op.hbm_budget_bytes) {
         const size_t have = op.hbm_budget_bytes > h->owned_bytes ? op.hbm_budget_bytes - h->owned_bytes : 0;
-        const size_t cur = (size_t)h->slots * (h->Y1_n * 8 + h->Y2_n * 8 + h->g_n * 4 + h->bits_n * 4) +
+        const size_t cur = (size_t)h->slots * (h->Y1_n * 8 + h->Y2_n * 8 + h->g_n * 4 + h->bits_n * 4 * kSweepLevels) +
                            (size_t)h->flag_cap * sizeof(int2);
         const size_t fixed = (size_t)(1 << 16) * sizeof(int2);
         const long fit = (long)((have + cur > fixed ? have + cur - fixed : 0) / std::max<size_t>(per_slot, 1));
@@ -522,8 +522,8 @@ imf_status ensure_work(imf_handle h)
         TRY(dalloc(h, &h->Y1, h->Y1_n * want));
         TRY(dalloc(h, &h->Y2, h->Y2_n * want));
         TRY(dalloc(h, &h->g, h->g_n * want));
-        TRY(dalloc(h, &h->bits, h->bits_n * want));
-        CU(cudaMemset(h->bits, 0, h->bits_n * want * sizeof(uint32_t)));
+        TRY(dalloc(h, &h->bits, h->bits_n * want * kSweepLevels));   // free bits and their dilation levels
+        CU(cudaMemset(h->bits, 0, h->bits_n * want * kSweepLevels * sizeof(uint32_t)));
         CU(cudaMemset(h->g, 0, h->g_n * want * sizeof(float)));
         h->slots = want;
     }
@@ -626,7 +626,7 @@ void imf_destroy(imf_handle h)
     dfree(h, h->Y1, h->Y1_n * h->slots);
     dfree(h, h->Y2, h->Y2_n * h->slots);
     dfree(h, h->g, h->g_n * h->slots);
-    dfree(h, h->bits, h->bits_n * h->slots);
+    dfree(h, h->bits, h->bits_n * h->slots * kSweepLevels);
     dfree(h, h->f, 0);
     dfree(h, h->A, 0);
     dfree(h, h->flags, (size_t)h->flag_cap);
@@ -830,7 +830,21 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
             rto.push_back((uint32_t)(t.rt[i][m] + 512) | ((uint32_t)(t.rt[i][m + 1] + 512) << 10) |
                           ((uint32_t)(t.rt[i][m + 2] + 512) << 20));
         rts[i + 1] = (int)rto.size();
-        for (size_t m = 0; m < ivs[i].size(); m += 4) ivv.push_back(make_int4(ivs[i][m], ivs[i][m + 1], ivs[i][m + 2], ivs[i][m + 3]));
+        // cutter run [a, b] at (dy, dz): sliding OR of length L at shift s = kx - b >= 0 from
+        // level j with 2^j <= L <= 2^(j+1) (runs are at most 32 long), windows s and s + L - 2^j
+        for (size_t m = 0; m < ivs[i].size(); m += 4) {
+            const int a0 = ivs[i][m], b0 = ivs[i][m + 1], dy = ivs[i][m + 2], dz = ivs[i][m + 3];
+            const int L = b0 - a0 + 1;
+            int j = 0;
+            while (j < kSweepLevels - 1 && (2 << j) <= L) ++j;
+            const int sa = t.kmax[0] - b0, sb = sa + L - (1 << j);
+            const long row = (long)(t.kmax[2] - dz) * t.win[1] * t.wpr + (long)(t.kmax[1] - dy) * t.wpr;
+            if (row + (sa >> 5) > 0x7fffffffL) {
+                free_tool(h, t);
+                return fail(h, IMF_ERR_INVALID_ARG, "translation window too large for the sweep descriptors");
+            }
+            ivv.push_back(make_int4((int)(row + (sa >> 5)), (sb >> 5) - (sa >> 5), (sa & 31) | ((sb & 31) << 8), j));
+        }
         ivst[i + 1] = (int)ivv.size();
         t.n_sh += (long)t.sh[i].size() / 3;
     }
@@ -867,8 +881,8 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
     if ((st = upload(h, &t.twy, tw))) return bail(st);
     twiddles(t.P[2], t.P[2], t.P[2], tw);
     if ((st = upload(h, &t.twz, tw))) return bail(st);
-    if ((st = upload(h, &t.rt_off, rto)) || (st = upload(h, &t.rt_start, rts)) || (st = upload(h, &t.iv, ivv)) ||
-        (st = upload(h, &t.iv_start, ivst)) ||
+    if ((st = upload(h, &t.rt_off, rto)) || (st = upload(h, &t.rt_start, rts)) || (st = upload(h, &t.sw_pairs, ivv)) ||
+        (st = upload(h, &t.sw_start, ivst)) ||
         (st = upload(h, &t.er_chunks, chunks)) || (st = upload(h, &t.er_chunk_start, chst)) ||
         (st = upload(h, &t.er_runs, eruns)))
         return bail(st);
@@ -938,12 +952,19 @@ imf_status tail_batch(imf_handle h, const Tool &t, const float *rho, const uint8
         launch_recheck_blocks(a, 152 * 8, s);
     }
     if (h->run_sweep) {
+        const long lstride = (long)h->bits_n * h->slots;
+        {
+            SweepLevelsArgs a{};
+            a.bits = h->bits; a.lstride = lstride; a.n = bso * nb; a.wpr = t.wpr;
+            Launch L(h, KID_SWEEP_LEVELS, s);
+            launch_sweep_levels(a, s);
+        }
         SweepArgs a{};
-        a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
-        a.iv = t.iv; a.iv_start = t.iv_start; a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.awords = h->awords;
-        a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2]; a.orient_base = o0; a.nb = nb; a.A = h->A;
+        a.bits = h->bits; a.lstride = lstride; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
+        a.pairs = t.sw_pairs; a.pair_start = t.sw_start; a.nx = op.nx; a.ny = op.ny; a.nz = op.nz;
+        a.awords = h->awords; a.orient_base = o0; a.nb = nb; a.A = h->A;
         Launch L(h, KID_SWEEP, s);
-        launch_sweep2(a, s);
+        launch_sweep(a, s);
     }
     {
         Erode2Args a{};

@@ -128,18 +128,30 @@ struct RecheckArgs {
 void launch_recheck(const RecheckArgs &a, cudaStream_t s);
 void launch_recheck_blocks(const RecheckArgs &a, int max_points, cudaStream_t s);
 
+// Free bits with their dilation levels: level j (0 .. kSweepLevels - 1) of every slot lives at
+// bits + j * lstride, word i of level j being the OR of the free bits i*32+t .. i*32+t+2^j-1.
+constexpr int kSweepLevels = 5;
+struct SweepLevelsArgs {
+    uint32_t *bits;              // level 0 of slot 0 (the free bits)
+    long lstride;                // words between levels
+    long n;                      // words of the batch's slots (rows of wpr words)
+    int wpr;
+};
 struct SweepArgs {
-    const uint32_t *bits;
+    const uint32_t *bits;        // level 0 of slot 0; level j at + j * lstride
+    long lstride;
     long b_sy, b_sz, b_so;
-    const int4 *iv;              // cutter row intervals (a, b, dy, dz), all orientations
-    const int *iv_start;         // n_orient + 1
+    // per cutter run, one int4: x = window row offset (kz - dz) b_sz + (ky - dy) b_sy plus the
+    // word of the first shift s = kx - b, y = word distance to the second shift s + L - 2^j,
+    // z = (s & 31) | ((s + L - 2^j) & 31) << 8, w = level j = min(4, floor(log2 L))
+    const int4 *pairs;
+    const int *pair_start;       // n_orient + 1
     int nx, ny, nz, awords;
-    int kx, ky, kz;
     int orient_base, nb;
     uint32_t *A;                 // accessible bits [nz][ny][awords], OR-accumulated
 };
+void launch_sweep_levels(const SweepLevelsArgs &a, cudaStream_t s);
 void launch_sweep(const SweepArgs &a, cudaStream_t s);
-void launch_sweep2(const SweepArgs &a, cudaStream_t s);
 
 
 // Tiled minimum over sharp points. A block owns kErTX x kErTY x kErTZ outputs (kErXT

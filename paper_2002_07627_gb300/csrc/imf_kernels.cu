@@ -126,69 +126,41 @@ __global__ void recheck_kernel(RecheckArgs a)
 
 // ---------------------------------------------------------------------------------------
 // Sweep (Eq. eq_conv_A): A_R(x) = OR_{k in RK} free(x - k), on bit-packed rows. RK is a
-// union of runs [a, b] along x at fixed (dy, dz); a run contributes the sliding OR of
-// length b - a + 1 of one source row, computed on 64-bit windows by doubling shifts.
+// union of runs [a, b] along x at fixed (dy, dz) (at most 32 long); a run contributes the
+// sliding OR of length L = b - a + 1 of one source row. With the dilation levels
+// D_j(i) = OR_{t < 2^j} free(i + t) (D_0 = free), the sliding OR of length L at i is
+// D_j(i) | D_j(i + L - 2^j) for 2^j <= L <= 2^(j+1), so every run costs two 32-bit windows.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t bit_window(const uint32_t *row, int s)
-{
-    const int w0 = s >> 5, sh = s & 31;
-    uint64_t lo = (uint64_t)row[w0] | ((uint64_t)row[w0 + 1] << 32);
-    if (sh) lo = (lo >> sh) | ((uint64_t)row[w0 + 2] << (64 - sh));
-    return lo;
-}
 
-__device__ __forceinline__ uint32_t dilate_bits(uint64_t w, int L)
+// Levels 1..4 of the free bits of slots [0, nb): word i of level j at bits + j * lstride + i.
+// Bits past the end of a row count as 0; a row's window words only reach its padding words.
+__global__ void sweep_levels_kernel(SweepLevelsArgs a)
 {
-    uint64_t d = w;
-    int span = 1;
-    while (span * 2 <= L) {
-        d |= d >> span;
-        span *= 2;
-    }
-    if (span < L) d |= d >> (L - span);
-    return (uint32_t)d;
-}
-
-__global__ void sweep_kernel(SweepArgs a)
-{
-    const long total = (long)a.awords * a.ny * a.nz;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        const int q = (int)(t % a.awords);
-        const int y = (int)((t / a.awords) % a.ny);
-        const int z = (int)(t / ((long)a.awords * a.ny));
-        uint32_t acc = 0;
-        for (int ob = 0; ob < a.nb; ++ob) {
-            const int og = a.orient_base + ob;
-            const uint32_t *bits = a.bits + ob * a.b_so;
-            for (int m = a.iv_start[og]; m < a.iv_start[og + 1]; ++m) {
-                const int4 iv = a.iv[m];
-                const uint32_t *row = bits + (long)(z - iv.w + a.kz) * a.b_sz + (long)(y - iv.z + a.ky) * a.b_sy;
-                const int L = iv.y - iv.x + 1;
-                const int s0 = 32 * q + a.kx - iv.y;
-                for (int c0 = 0; c0 < L; c0 += 32) acc |= dilate_bits(bit_window(row, s0 + c0), min(32, L - c0));
-            }
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < a.n; i += (long)gridDim.x * blockDim.x) {
+        const int w = (int)(i % a.wpr);
+        const uint32_t lo = a.bits[i], hi = w + 1 < a.wpr ? a.bits[i + 1] : 0u;
+        uint64_t v = (uint64_t)lo | ((uint64_t)hi << 32);
+        // after the step with shift 2^(j-1), bit t < 32 of v is the OR of the source bits
+        // t .. t + 2^j - 1 (all below bit 64 for j <= 4)
+#pragma unroll
+        for (int j = 1; j < kSweepLevels; ++j) {
+            v |= v >> (1 << (j - 1));
+            a.bits[j * a.lstride + i] = (uint32_t)v;
         }
-        const int rem = a.nx - 32 * q;
-        if (rem < 32) acc &= (1u << rem) - 1u;
-        uint32_t *dst = a.A + ((long)z * a.ny + y) * a.awords + q;
-        *dst |= acc;
     }
 }
 
-// One thread per (output word, orientation of the batch); results are OR-ed into A. The
-// cutter runs of the orientation are staged in shared memory as (row offset, x shift,
-// length); a run reads the 64 source bits starting at its shift with two funnel shifts and
-// ORs the window of its length by doubling.
+// One thread per (output word, orientation of the batch); results are OR-ed into A. The run
+// descriptors of the orientation are staged in shared memory (see SweepArgs::pairs).
 constexpr int kSweepStage = 512;
 
-__global__ void __launch_bounds__(256) sweep2_kernel(SweepArgs a)
+__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a)
 {
-    __shared__ int4 siv[kSweepStage];
+    __shared__ int4 sp[kSweepStage];
     const long total = (long)a.awords * a.ny * a.nz;
     const int ob = blockIdx.y;
     const int og = a.orient_base + ob;
-    const uint32_t *bits = a.bits + ob * a.b_so;
-    const int m0 = a.iv_start[og], m1 = a.iv_start[og + 1];
+    const int m0 = a.pair_start[og], m1 = a.pair_start[og + 1];
     const long tstride = (long)gridDim.x * blockDim.x;
     for (long tb = (long)blockIdx.x * blockDim.x; tb < total; tb += tstride) {
         const long t = tb + threadIdx.x;
@@ -196,7 +168,8 @@ __global__ void __launch_bounds__(256) sweep2_kernel(SweepArgs a)
         const int q = live ? (int)(t % a.awords) : 0;
         const int y = live ? (int)((t / a.awords) % a.ny) : 0;
         const int z = live ? (int)(t / ((long)a.awords * a.ny)) : 0;
-        const uint32_t *base = bits + (long)z * a.b_sz + (long)y * a.b_sy;
+        // word q of the output row, in window coordinates of slot ob (run offsets added below)
+        const uint32_t *base = a.bits + ob * a.b_so + (long)z * a.b_sz + (long)y * a.b_sy + q;
         uint32_t *dstw = a.A + ((long)z * a.ny + y) * a.awords + q;
         const int rem = a.nx - 32 * q;
         const uint32_t full = rem < 32 ? (1u << rem) - 1u : 0xffffffffu;
@@ -206,29 +179,14 @@ __global__ void __launch_bounds__(256) sweep2_kernel(SweepArgs a)
         for (int c0 = m0; c0 < m1; c0 += kSweepStage) {
             const int cn = min(kSweepStage, m1 - c0);
             __syncthreads();
-            for (int i = threadIdx.x; i < cn; i += blockDim.x) {
-                const int4 iv = a.iv[c0 + i];     // (a, b, dy, dz)
-                siv[i] = make_int4((int)((long)(a.kz - iv.w) * a.b_sz + (long)(a.ky - iv.z) * a.b_sy),
-                                   a.kx - iv.y, iv.y - iv.x + 1, 0);
-            }
+            for (int i = threadIdx.x; i < cn; i += blockDim.x) sp[i] = a.pairs[c0 + i];
             __syncthreads();
             if (!live || (acc & full) == full) continue;
             for (int i = 0; i < cn; ++i) {
-                const int4 r = siv[i];
-                const uint32_t *row = base + r.x;
-                const int s0 = 32 * q + r.y;
-                const int w0 = s0 >> 5, sh = s0 & 31;
-                const uint32_t u0 = row[w0], u1 = row[w0 + 1], u2 = row[w0 + 2];
-                uint32_t lo = __funnelshift_r(u0, u1, sh), hi = __funnelshift_r(u1, u2, sh);
-                const int L = r.z;
-                int span = 1;
-                while (span * 2 <= L) {
-                    lo |= __funnelshift_r(lo, hi, span);
-                    hi |= hi >> span;
-                    span *= 2;
-                }
-                if (span < L) lo |= __funnelshift_r(lo, hi, L - span);
-                acc |= lo;
+                const int4 d = sp[i];
+                const uint32_t *p = base + (long)d.w * a.lstride + d.x;
+                const uint32_t u0 = p[0], u1 = p[1], v0 = p[d.y], v1 = p[d.y + 1];
+                acc |= __funnelshift_r(u0, u1, d.z & 31) | __funnelshift_r(v0, v1, d.z >> 8);
             }
         }
         if (live) {
@@ -396,21 +354,21 @@ void launch_recheck(const RecheckArgs &a, cudaStream_t s)
     recheck_kernel<<<152 * 8, kThreads, 0, s>>>(a);
 }
 
-void launch_sweep2(const SweepArgs &a, cudaStream_t s)
+void launch_sweep_levels(const SweepLevelsArgs &a, cudaStream_t s)
+{
+    sweep_levels_kernel<<<blocks_for(a.n, kThreads, 152 * 8), kThreads, 0, s>>>(a);
+}
+
+void launch_sweep(const SweepArgs &a, cudaStream_t s)
 {
     dim3 grid(blocks_for((long)a.awords * a.ny * a.nz, kThreads, 152 * 4), a.nb);
-    sweep2_kernel<<<grid, kThreads, 0, s>>>(a);
+    sweep_kernel<<<grid, kThreads, 0, s>>>(a);
 }
 
 void launch_recheck_blocks(const RecheckArgs &a, int max_points, cudaStream_t s)
 {
     int blocks = max_points < 1 ? 1 : (max_points > 152 * 8 ? 152 * 8 : max_points);
     recheck_blocks_kernel<<<blocks, 256, 0, s>>>(a);
-}
-
-void launch_sweep(const SweepArgs &a, cudaStream_t s)
-{
-    sweep_kernel<<<blocks_for((long)a.awords * a.ny * a.nz), kThreads, 0, s>>>(a);
 }
 
 void launch_fill_f32(float *p, float v, long n, cudaStream_t s)

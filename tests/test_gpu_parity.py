@@ -386,3 +386,20 @@ def test_accessible_from_the_minimum_equals_the_sweep():
     sharp[: sharp.shape[0] // 2] = 1
     d.tools[0].sharp = sharp
     check_against_oracle(d, run_gpu(d, orient_batch=4), oracle.imf(d))
+
+def test_sweep_of_long_cutter_runs_matches_oracle():
+    """Sweep of Eq. eq_conv_A with cutter runs along x of every length class: a 40-voxel cutter
+    laid along +x and -x (runs split at 32, so lengths 32 and 8 occur), tilted and upright
+    (runs of 1 .. 5). The sweep is forced; the accessible set must match the oracle exactly
+    away from the threshold, and so must the route that reads A off the minimum."""
+    c, s_ = np.cos(np.pi / 4), np.sin(np.pi / 4)
+    quats = np.array([[c, 0, s_, 0], [c, 0, -s_, 0], [1, 0, 0, 0], [np.cos(0.3), 0.2, np.sin(0.3), 0.1]])
+    quats /= np.linalg.norm(quats, axis=1, keepdims=True)
+    rho = synth.beam_density((90, 30, 26), n_beams=8, seed=11)
+    fix = synth.slab_fixture(rho.shape, 2, axis="z")
+    d = synth.Design(rho, fix, [synth.cylinder_tool(2, 40, 3, 4, quats)])
+    ref = oracle.imf(d)
+    got = run_gpu(d, orient_batch=3, accessible_by_sweep=True)
+    check_against_oracle(d, got, ref)
+    assert got["accessible"].any() and not got["accessible"].all()
+    check_against_oracle(d, run_gpu(d, orient_batch=3), ref)
