@@ -148,6 +148,8 @@ def algorithmic_bytes(kernel, info, shape, nb, bits=True):
         return nb * (Wz * Py * Hx * 8 + Wz * Wy * Hx * 8)
     if kernel == "irfft_x_threshold":
         return nb * (Wz * Wy * Hx * 8 + Wz * Wy * Wx * 4 + (Wz * Wy * bitsw if bits else 0))
+    if kernel == "fft_yx_inv_threshold":
+        return nb * (Wz * Py * Hx * 8 + Wz * Wy * Wx * 4 + (Wz * Wy * bitsw if bits else 0))
     if kernel == "erode_min":
         return nb * Wz * Wy * Wx * 4 + 2 * nG * 4
     if kernel == "sweep_dilate":

@@ -81,6 +81,10 @@ typedef struct {
                                 both say "some cutter point lies on a free translation"; the
                                 route of App. A), else the sweep of Eq. eq_conv_A; 1 = always
                                 the sweep                                                      */
+    int separate_yx_passes;  /* 1: the inverse y and x passes run as two kernels with the y
+                                output in HBM; 0 = one kernel per z-plane that keeps the plane
+                                in shared memory, wherever it fits (same arithmetic, same
+                                results)                                                       */
 } imf_options;
 
 /* Fill *opt with the defaults above (grid 0x0x0, which imf_create rejects). */

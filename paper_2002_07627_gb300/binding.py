@@ -33,7 +33,8 @@ class ImfOptions(ctypes.Structure):
                 ("theta_rel", ctypes.c_double), ("precision", ctypes.c_int), ("recheck", ctypes.c_int),
                 ("recheck_band", ctypes.c_double), ("orient_batch", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("erode_groups", ctypes.c_int),
-                ("fft_stages_only", ctypes.c_int), ("accessible_by_sweep", ctypes.c_int)]
+                ("fft_stages_only", ctypes.c_int), ("accessible_by_sweep", ctypes.c_int),
+                ("separate_yx_passes", ctypes.c_int)]
 
 
 class ImfToolInfo(ctypes.Structure):
@@ -154,7 +155,7 @@ class Imf:
 
     def __init__(self, shape_zyx, lam=0.01, tau=0.5, theta_rel=0.01, precision=IMF_AUTO, recheck=True,
                  recheck_band=0.0, orient_batch=0, hbm_budget_bytes=0, voxel=1.0, erode_groups=0, fft_stages_only=False,
-                 accessible_by_sweep=False):
+                 accessible_by_sweep=False, separate_yx_passes=False):
         self.lib = load()
         opt = ImfOptions()
         self.lib.imf_default_options(ctypes.byref(opt))
@@ -166,6 +167,7 @@ class Imf:
         opt.erode_groups = erode_groups
         opt.fft_stages_only = int(fft_stages_only)
         opt.accessible_by_sweep = int(accessible_by_sweep)
+        opt.separate_yx_passes = int(separate_yx_passes)
         self.shape = (nz, ny, nx)
         self.opt = opt
         h = ctypes.c_void_p()

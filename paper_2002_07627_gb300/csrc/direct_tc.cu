@@ -133,12 +133,12 @@ __global__ void __launch_bounds__(kDThreads, 2) direct_corr_kernel(DirectArgs a)
                 if (ok) tc::mma_commit(dfull);
             }
             if (!ok) {
-                atomicExch(a.status, 4);
+                atomicExch(a.status, kDevTimeout);
                 atomicExch(&s_abort, 1);
             }
             // drain: every MMA this thread issued has completed before TMEM is freed
             tc::mma_commit(bars + 7);
-            if (!tc::mbar_wait(bars + 7, 0)) atomicExch(a.status, 4);
+            if (!tc::mbar_wait(bars + 7, 0)) atomicExch(a.status, kDevTimeout);
         }
         __syncwarp();
     } else {
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kDThreads, 2) direct_corr_kernel(DirectArgs a)
             tc::mbar_arrive(dempty);
         }
         if (!ok) {
-            atomicExch(a.status, 4);
+            atomicExch(a.status, kDevTimeout);
             atomicExch(&s_abort, 1);
         }
     }
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(128, 1) mma_selftest_kernel(const uint16_t *A,
             for (int j = 0; j < 8; ++j) D[(warp * 32 + lane) * N + n0 + j] = v[j];
         }
     } else if (threadIdx.x == 0) {
-        *status = 4;
+        *status = kDevTimeout;
     }
     tc::fence_before();
     __syncthreads();

@@ -10,6 +10,7 @@
 
 #include "fft2.cuh"
 #include "imf_internal.cuh"
+#include "tc_primitives.cuh"
 #include "threshold_row.cuh"
 
 namespace imf {
@@ -109,112 +110,72 @@ template <int S> __global__ void __launch_bounds__(kT2) axis2_kernel(AxisArgs a,
     }
 }
 
-// Inverse x pass over R = 256 / A window rows per block: the half spectrum X[0..M] of a row is
-// packed into M complex samples Z[k] = (X[k] + conj X[M-k]) + i exp(+2 pi i k / P)
-// (X[k] - conj X[M-k]) as pass 1 loads it, the M-point inverse DFT runs in two passes, the
-// samples are written back to the row's shared-memory line in natural order and the threshold
-// epilogue reads them. Pass 1 gives row w the threads w B .. w B + B - 1 and pass 2 the threads
-// w A .. w A + A - 1, so the slots a pass does not need are whole idle warps. Row w's line
-// holds pass-1 element (n1, k2) at n1 Ap + k2 with Ap = A | 1 odd (stores of consecutive n1
-// fall in different bank pairs).
-__global__ void __launch_bounds__(kT2) irfft2_threshold_kernel(IrfftArgs a)
+// Pass-1 input of the inverse x pass for thread p of a row: the half spectrum X[0..M] of the
+// row (at `row`, global or shared memory) packed into the complex samples
+// Z[k] = (X[k] + conj X[M-k]) + i exp(+2 pi i k / P) (X[k] - conj X[M-k]), k = p + B n2.
+template <int NA>
+__device__ __forceinline__ void x_pack(const float2 *row, int p, int B, int M, const float2 *twP, float2 *v)
 {
-    extern __shared__ float2 sm[];
-    const int A = a.A2, B = a.B2, M = a.M, Ap = A | 1, R = kT2 / A;
-    const int ld = max(M, B * Ap) + 1;
-    float2 *tile = sm, *twM = sm + R * ld, *twP = twM + M;
-    // free flags of the block's rows, one byte per translation; rows of fp >= 2 M >= nout bytes,
-    // 16-byte aligned
-    const int fp = (2 * M + 31) & ~31;
-    uint8_t *sflag = reinterpret_cast<uint8_t *>(sm + ((R * ld + 2 * M + 2) & ~1));
-    for (int i = threadIdx.x; i < M; i += kT2) twM[i] = a.twM[i];
-    for (int i = threadIdx.x; i <= M; i += kT2) twP[i] = a.twP[i];
-    __syncthreads();
-    const int r0 = (int)blockIdx.x * R;
-    const long o = blockIdx.z;
-    {
-        const int w = threadIdx.x / B, p = threadIdx.x - w * B;
-        const int r = r0 + w;
-        if (w < R && r < a.rows) {
-            const int y = r % a.rows_y, z = r / a.rows_y;
-            const float2 *row = a.in + o * a.in_so + z * a.in_sz + y * a.in_sy;
-            float2 *line = tile + w * ld;
-            fft2::with_size(A, [&](auto AA) {
-                constexpr int NA = decltype(AA)::value;
-                float2 v[NA], xc[NA];
+    float2 xc[NA];
 #pragma unroll
-                for (int n2 = 0; n2 < NA; ++n2) {
-                    const int k = p + B * n2;
-                    v[n2] = row[k];
-                    xc[n2] = row[M - k];
-                }
-#pragma unroll
-                for (int n2 = 0; n2 < NA; ++n2) {
-                    const int k = p + B * n2;
-                    const float2 xk = v[n2], xcc = c_conj(xc[n2]);
-                    const float2 e = c_add(xk, xcc);
-                    const float2 od = c_mul(c_conj(twP[k]), c_sub(xk, xcc));
-                    v[n2] = c_add(e, c_mul_si<1>(od));
-                }
-                fft2::pass1<1, NA>(v, p, twM);
-#pragma unroll
-                for (int k2 = 0; k2 < NA; ++k2) line[p * Ap + k2] = v[k2];
-            });
-        }
+    for (int n2 = 0; n2 < NA; ++n2) {
+        const int k = p + B * n2;
+        v[n2] = row[k];
+        xc[n2] = row[M - k];
     }
-    __syncthreads();
-    // pass 2 (every thread enters the uniform size dispatch; inactive threads store nothing)
-    const int lane = threadIdx.x & 31;
-    {
-        const int w = threadIdx.x / A, p = threadIdx.x - w * A;
-        const bool act = w < R && r0 + w < a.rows;
-        float2 *line = tile + w * ld;
-        fft2::with_size(B, [&](auto BB) {
-            constexpr int NB = decltype(BB)::value;
-            float2 u[NB];
-            if (act) {
 #pragma unroll
-                for (int n1 = 0; n1 < NB; ++n1) u[n1] = line[n1 * Ap + p];
-                fft2::dft_reg<1, NB>(u);
-            }
-            // thread (row w, k2 = p) holds z[p + A k1]: g[2j] = Re, g[2j+1] = Im for j = p + A k1,
-            // clamped at 0, written straight from registers (consecutive lanes, consecutive j);
-            // the free flags g <= theta go to shared memory as bytes and near-threshold
-            // translations are listed for the re-check
-            int y = 0, z = 0;
-            if (act) {
-                y = (r0 + w) % a.rows_y;
-                z = (r0 + w) / a.rows_y;
-            }
-            float *grow = a.g + o * a.g_so + z * a.g_sz + y * a.g_sy;
-            const long lrow = ((long)z * a.rows_y + y) * a.nout;
-#pragma unroll
-            for (int k1 = 0; k1 < NB; ++k1) {
-                const int i0 = 2 * (p + A * k1);
-                const bool v0 = act && i0 < a.nout, v1 = act && i0 + 1 < a.nout;
-                const float g0 = fmaxf(u[k1].x, 0.f), g1 = fmaxf(u[k1].y, 0.f);
-                if (v1) *reinterpret_cast<float2 *>(grow + i0) = make_float2(g0, g1);
-                else if (v0) grow[i0] = g0;
-                if (a.write_bits && v0)
-                    *reinterpret_cast<uint16_t *>(sflag + w * fp + i0) =
-                        (uint16_t)((g0 <= a.theta ? 1u : 0u) | (v1 && g1 <= a.theta ? 0x100u : 0u));
-                if (a.flag)
-                    record_near(a, o, lrow + i0, v0 && fabsf(g0 - a.theta) <= a.band,
-                                v1 && fabsf(g1 - a.theta) <= a.band, lane);
-            }
-        });
+    for (int n2 = 0; n2 < NA; ++n2) {
+        const int k = p + B * n2;
+        const float2 xk = v[n2], xcc = c_conj(xc[n2]);
+        const float2 e = c_add(xk, xcc);
+        const float2 od = c_mul(c_conj(twP[k]), c_sub(xk, xcc));
+        v[n2] = c_add(e, c_mul_si<1>(od));
     }
-    if (!a.write_bits) return;   // uniform
-    __syncthreads();
-    // one free-bit word (32 translations along x) per thread, packed from its 32 flag bytes:
-    // for a 4-byte group v with bytes b_i in {0, 1}, the multiplier 0x01020408 = 2^24 + 2^17 +
-    // 2^10 + 2^3 moves byte i (bit 8 i) to bit 24 + i and every cross term to a distinct bit
-    // below 24 (no carries); bytes past nout are masked off
+}
+
+// Threshold epilogue of pass 2 for thread (window row r, k2 = p) holding z[p + A k1] (act:
+// the thread has a row): g[2j] = Re, g[2j+1] = Im for j = p + A k1, clamped at 0, written
+// straight from registers (consecutive lanes, consecutive j); the free flags g <= theta go to
+// the row's flag bytes in shared memory (when bits are wanted) and near-threshold translations
+// are listed for the re-check. Called by all 32 lanes of a warp.
+template <int NB>
+__device__ __forceinline__ void x_epilogue(const IrfftArgs &a, const float2 *u, int A, int p, bool act, int r, long o,
+                                           uint8_t *frow, int lane)
+{
+    int y = 0, z = 0;
+    if (act) {
+        y = r % a.rows_y;
+        z = r / a.rows_y;
+    }
+    float *grow = a.g + o * a.g_so + z * a.g_sz + y * a.g_sy;
+    const long lrow = ((long)z * a.rows_y + y) * a.nout;
+#pragma unroll
+    for (int k1 = 0; k1 < NB; ++k1) {
+        const int i0 = 2 * (p + A * k1);
+        const bool v0 = act && i0 < a.nout, v1 = act && i0 + 1 < a.nout;
+        const float g0 = fmaxf(u[k1].x, 0.f), g1 = fmaxf(u[k1].y, 0.f);
+        if (v1) *reinterpret_cast<float2 *>(grow + i0) = make_float2(g0, g1);
+        else if (v0) grow[i0] = g0;
+        if (a.write_bits && v0)
+            *reinterpret_cast<uint16_t *>(frow + i0) =
+                (uint16_t)((g0 <= a.theta ? 1u : 0u) | (v1 && g1 <= a.theta ? 0x100u : 0u));
+        if (a.flag)
+            record_near(a, o, lrow + i0, v0 && fabsf(g0 - a.theta) <= a.band, v1 && fabsf(g1 - a.theta) <= a.band,
+                        lane);
+    }
+}
+
+// Free-bit words of nr window rows r0 .. from their flag bytes (rows fp bytes apart), one word
+// (32 translations along x) per thread and step: for a 4-byte group v with bytes b_i in {0, 1},
+// the multiplier 0x01020408 = 2^24 + 2^17 + 2^10 + 2^3 moves byte i (bit 8 i) to bit 24 + i and
+// every cross term to a distinct bit below 24 (no carries); bytes past nout are masked off.
+template <int NT>
+__device__ __forceinline__ void x_pack_bits(const IrfftArgs &a, const uint8_t *sflag, int fp, int r0, int nr, long o)
+{
     const int nwq = (a.nout + 31) >> 5;
-    for (int i = threadIdx.x; i < R * nwq; i += kT2) {
+    for (int i = threadIdx.x; i < nr * nwq; i += NT) {
         const int ww = i / nwq, q = i - ww * nwq, rr = r0 + ww;
-        if (rr >= a.rows) break;   // later i only have larger rows
-        const uint4 *fw = reinterpret_cast<const uint4 *>(sflag + ww * fp + 32 * q);
+        const uint4 *fw = reinterpret_cast<const uint4 *>(sflag + (long)ww * fp + 32 * q);
         uint32_t word = 0;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -231,6 +192,218 @@ __global__ void __launch_bounds__(kT2) irfft2_threshold_kernel(IrfftArgs a)
     }
 }
 
+// Inverse x pass of nr <= NT / A consecutive window rows r0 .. r0 + nr - 1 of orientation slot
+// o; row r0 + w's half spectrum starts at rin + w * rstride. The M-point inverse DFT of the
+// packed samples runs in two passes: pass 1 gives row w the threads w B .. w B + B - 1 and
+// pass 2 the threads w A .. w A + A - 1, so the slots a pass does not need are whole idle
+// warps. Row w's line of the tile holds pass-1 element (n1, k2) at n1 Ap + k2 with Ap = A | 1
+// odd (stores of consecutive n1 fall in different bank pairs).
+template <int NT>
+__device__ __forceinline__ void x_rows2(const IrfftArgs &a, const float2 *rin, long rstride, int r0, int nr, long o,
+                                        float2 *tile, const float2 *twM, const float2 *twP, uint8_t *sflag)
+{
+    const int A = a.A2, B = a.B2, M = a.M, Ap = A | 1;
+    const int ld = max(M, B * Ap) + 1, fp = (2 * M + 31) & ~31;
+    {
+        const int w = threadIdx.x / B, p = threadIdx.x - w * B;
+        if (w < nr) {
+            float2 *line = tile + w * ld;
+            fft2::with_size(A, [&](auto AA) {
+                constexpr int NA = decltype(AA)::value;
+                float2 v[NA];
+                x_pack<NA>(rin + w * rstride, p, B, M, twP, v);
+                fft2::pass1<1, NA>(v, p, twM);
+#pragma unroll
+                for (int k2 = 0; k2 < NA; ++k2) line[p * Ap + k2] = v[k2];
+            });
+        }
+    }
+    __syncthreads();
+    // pass 2 (every thread enters the uniform size dispatch; inactive threads store nothing)
+    {
+        const int w = threadIdx.x / A, p = threadIdx.x - w * A;
+        const bool act = w < nr;
+        const float2 *line = tile + w * ld;
+        fft2::with_size(B, [&](auto BB) {
+            constexpr int NB = decltype(BB)::value;
+            float2 u[NB];
+            if (act) {
+#pragma unroll
+                for (int n1 = 0; n1 < NB; ++n1) u[n1] = line[n1 * Ap + p];
+                fft2::dft_reg<1, NB>(u);
+            }
+            x_epilogue<NB>(a, u, A, p, act, r0 + w, o, sflag + w * fp, threadIdx.x & 31);
+        });
+    }
+    if (!a.write_bits) return;   // uniform
+    __syncthreads();
+    x_pack_bits<NT>(a, sflag, fp, r0, nr, o);
+}
+
+// Shared-memory layout of x_rows2 after `base` float2 of other data: the tile (R lines of ld)
+// from the next even offset, then R rows of flag bytes (fp each) from a 16-byte boundary.
+struct XLayout {
+    long tile, flags, end;   // offsets in float2
+};
+__host__ __device__ inline XLayout x_layout(long base, int NT, int M, int A, int B)
+{
+    const int R = NT / A, ld = (M > B * (A | 1) ? M : B * (A | 1)) + 1, fp = (2 * M + 31) & ~31;
+    XLayout l;
+    l.tile = (base + 1) & ~1L;
+    l.flags = (l.tile + (long)R * ld + 1) & ~1L;
+    l.end = l.flags + ((long)R * fp + 7) / 8;
+    return l;
+}
+
+// Inverse x pass over R = 256 / A consecutive window rows per block (rows of the input evenly
+// spaced: in_sz = rows_y in_sy).
+__global__ void __launch_bounds__(kT2) irfft2_threshold_kernel(IrfftArgs a)
+{
+    extern __shared__ float2 sm[];
+    const int M = a.M, R = kT2 / a.A2;
+    const XLayout l = x_layout(2 * M + 1, kT2, M, a.A2, a.B2);
+    float2 *twM = sm, *twP = sm + M, *tile = sm + l.tile;
+    uint8_t *sflag = reinterpret_cast<uint8_t *>(sm + l.flags);
+    for (int i = threadIdx.x; i < M; i += kT2) twM[i] = a.twM[i];
+    for (int i = threadIdx.x; i <= M; i += kT2) twP[i] = a.twP[i];
+    __syncthreads();
+    const int r0 = (int)blockIdx.x * R;
+    const long o = blockIdx.z;
+    x_rows2<kT2>(a, a.in + o * a.in_so + (long)r0 * a.in_sy, a.in_sy, r0, min(R, a.rows - r0), o, tile, twM, twP,
+                 sflag);
+}
+
+// Inverse y pass and inverse x pass (with the threshold) of one z-plane of one orientation slot
+// per block, the plane staying in shared memory between them (no y-pass output in HBM). The
+// plane of the inverse-z output (P1 rows ky of hs complex kx, contiguous) arrives in one bulk
+// copy and every step runs in place on it:
+//   y pass 1 / y pass 2: per group of 32 columns kx (lane = column, warp = slot), all groups of
+//     one pass before the next pass; pass 2 keeps the window rows y < lout;
+//   x pass 1 / x pass 2: per round of rows y < lout; pass 1 writes its elements (n1, k2) at
+//     n1 A + k2 of the row itself (A B = M <= hs); pass 2 ends in the threshold epilogue.
+// Each pass loops inside one size case of the uniform dispatch (a loop around the dispatch
+// would keep every case's registers live); the free-bit words are packed at the end.
+constexpr int kYX = 512;
+
+__host__ __device__ inline long yx2_flags_offset(int Ly, int hs, int M)
+{
+    return ((long)Ly * hs + Ly + 2 * M + 1 + 1) & ~1L;   // float2 offset, 16-byte aligned
+}
+
+__global__ void __launch_bounds__(kYX) yx2_threshold_kernel(AxisArgs ay, IrfftArgs a, int hs)
+{
+    extern __shared__ float2 sm[];
+    __shared__ uint64_t bar;
+    const int Ay = ay.A2, By = ay.B2, Ly = Ay * By, Hx = ay.nx;
+    const int Ax = a.A2, Bx = a.B2, M = a.M, fp = (2 * M + 31) & ~31, nrow = a.rows_y;
+    const long pl = (long)Ly * hs;
+    float2 *plane = sm, *twy = sm + pl, *twM = twy + Ly, *twP = twM + M;
+    uint8_t *sflag = reinterpret_cast<uint8_t *>(sm + yx2_flags_offset(Ly, hs, M));
+    const int z = blockIdx.x;
+    const long o = blockIdx.y;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        const uint32_t bytes = (uint32_t)(pl * sizeof(float2));
+        tc::mbar_expect_tx(&bar, bytes);
+        tc::bulk_g2s(plane, ay.in + o * ay.in_so + (long)z * ay.in_sb, bytes, &bar);
+    }
+    for (int i = threadIdx.x; i < Ly; i += kYX) twy[i] = ay.tw[i];
+    for (int i = threadIdx.x; i < M; i += kYX) twM[i] = a.twM[i];
+    for (int i = threadIdx.x; i <= M; i += kYX) twP[i] = a.twP[i];
+    __syncthreads();
+    if (!tc::mbar_wait(&bar, 0)) {
+        // the copy did not land in time: report it, give it one more bounded wait, stop
+        if (threadIdx.x == 0) atomicExch(a.status, kDevTimeout);
+        tc::mbar_wait(&bar, 0);
+        return;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // y pass 1: slot p = warp < By loads x[p + By n2] of column c, A-point DFT and twiddles,
+    // element (n1, k2) back to row n1 Ay + k2 of the column
+    fft2::with_size(Ay, [&](auto AA) {
+        constexpr int NA = decltype(AA)::value;
+        for (int c0 = 0; c0 < Hx; c0 += 32) {
+            const int c = c0 + lane;
+            const bool act = warp < By && c < Hx;
+            float2 v[NA];
+            if (act) {
+#pragma unroll
+                for (int n2 = 0; n2 < NA; ++n2) v[n2] = plane[(long)(warp + By * n2) * hs + c];
+                fft2::pass1<1, NA>(v, warp, twy);
+            }
+            __syncthreads();
+            if (act) {
+#pragma unroll
+                for (int k2 = 0; k2 < NA; ++k2) plane[(long)(warp * NA + k2) * hs + c] = v[k2];
+            }
+        }
+    });
+    __syncthreads();
+    // y pass 2: slot p = warp < Ay, By-point DFT over n1, X[p + Ay k1] to row p + Ay k1 < lout
+    fft2::with_size(By, [&](auto BB) {
+        constexpr int NB = decltype(BB)::value;
+        for (int c0 = 0; c0 < Hx; c0 += 32) {
+            const int c = c0 + lane;
+            const bool act = warp < Ay && c < Hx;
+            float2 u[NB];
+            if (act) {
+#pragma unroll
+                for (int n1 = 0; n1 < NB; ++n1) u[n1] = plane[(long)(n1 * Ay + warp) * hs + c];
+                fft2::dft_reg<1, NB>(u);
+            }
+            __syncthreads();
+            if (act) {
+#pragma unroll
+                for (int k1 = 0; k1 < NB; ++k1) {
+                    const int y = warp + Ay * k1;
+                    if (y < ay.lout) plane[(long)y * hs + c] = u[k1];
+                }
+            }
+        }
+    });
+    __syncthreads();
+    // x pass 1: rows of Bx threads, kYX / Bx rows per round
+    fft2::with_size(Ax, [&](auto AA) {
+        constexpr int NA = decltype(AA)::value;
+        const int w0 = threadIdx.x / Bx, p = threadIdx.x - w0 * Bx, rpr = kYX / Bx;
+        for (int y0 = 0; y0 < nrow; y0 += rpr) {
+            const int y = y0 + w0;
+            const bool act = w0 < rpr && y < nrow;
+            float2 v[NA];
+            if (act) {
+                x_pack<NA>(plane + (long)y * hs, p, Bx, M, twP, v);
+                fft2::pass1<1, NA>(v, p, twM);
+            }
+            __syncthreads();
+            if (act) {
+#pragma unroll
+                for (int k2 = 0; k2 < NA; ++k2) plane[(long)y * hs + p * NA + k2] = v[k2];
+            }
+        }
+    });
+    __syncthreads();
+    // x pass 2 and the threshold epilogue: rows of Ax threads, kYX / Ax rows per round
+    fft2::with_size(Bx, [&](auto BB) {
+        constexpr int NB = decltype(BB)::value;
+        const int w0 = threadIdx.x / Ax, p = threadIdx.x - w0 * Ax, rpr = kYX / Ax;
+        for (int y0 = 0; y0 < nrow; y0 += rpr) {
+            const int y = y0 + w0;
+            const bool act = w0 < rpr && y < nrow;
+            float2 u[NB];
+            if (act) {
+#pragma unroll
+                for (int n1 = 0; n1 < NB; ++n1) u[n1] = plane[(long)y * hs + n1 * Ax + p];
+                fft2::dft_reg<1, NB>(u);
+            }
+            x_epilogue<NB>(a, u, Ax, p, act, z * nrow + y, o, sflag + (long)(act ? y : 0) * fp, lane);
+        }
+    });
+    if (!a.write_bits) return;   // uniform
+    __syncthreads();
+    x_pack_bits<kYX>(a, sflag, fp, z * nrow, nrow, o);
+}
+
 template <typename K> void set_smem2(K kernel, size_t bytes)
 {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -240,12 +413,11 @@ template <typename K> void set_smem2(K kernel, size_t bytes)
 
 size_t axis2_smem(int L) { return (size_t)(L * kW2 + L) * sizeof(float2); }
 
-size_t irfft2_smem(int M, int A, int B)
+size_t irfft2_smem(int M, int A, int B) { return (size_t)x_layout(2 * M + 1, kT2, M, A, B).end * sizeof(float2); }
+
+size_t yx2_smem(int Ly, int hs, int M, int rows)
 {
-    // R rows of flag bytes (the window has at most 2 M translations along x, rows padded to 32
-    // bytes) after the tables, starting on a 16-byte boundary
-    const int R = kT2 / A, ld = std::max(M, B * (A | 1)) + 1, fp = (2 * M + 31) & ~31;
-    return (size_t)(((R * ld + 2 * M + 2) & ~1) + (R * fp + 7) / 8) * sizeof(float2);
+    return (size_t)(yx2_flags_offset(Ly, hs, M) + ((long)rows * ((2 * M + 31) & ~31) + 7) / 8) * sizeof(float2);
 }
 
 void launch_axis2(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s)
@@ -269,6 +441,27 @@ void launch_irfft2_threshold(const IrfftArgs &a, int norient, cudaStream_t s)
     const int R = kT2 / a.A2;
     dim3 grid((a.rows + R - 1) / R, 1, norient);
     irfft2_threshold_kernel<<<grid, kT2, smem, s>>>(a);
+}
+
+} // namespace imf
+
+namespace imf {
+
+bool yx2_fits(const AxisArgs &ay, const IrfftArgs &a, int hs)
+{
+    if (ay.A2 <= 0 || a.A2 <= 0 || ay.in_sl != hs || ay.scale != 1.f || ay.conj_out || ay.mul || ay.j0 != 0 ||
+        ay.lin != ay.A2 * ay.B2 || ay.in_sb != (long)ay.lin * hs || (hs & 1))
+        return false;
+    // x pass 1 writes its elements into the row itself: M = A B must fit the row
+    if (a.M > hs) return false;
+    return yx2_smem(ay.A2 * ay.B2, hs, a.M, a.rows_y) <= (size_t)(227 * 1024 - 64);
+}
+
+void launch_yx2_threshold(const AxisArgs &ay, const IrfftArgs &a, int hs, int nz, int norient, cudaStream_t s)
+{
+    const size_t smem = yx2_smem(ay.A2 * ay.B2, hs, a.M, a.rows_y);
+    set_smem2(yx2_threshold_kernel, smem);
+    yx2_threshold_kernel<<<dim3(nz, norient), kYX, smem, s>>>(ay, a, hs);
 }
 
 } // namespace imf

@@ -33,12 +33,12 @@ namespace {
 enum KernelId {
     KID_ROTATE, KID_SPEC, KID_RFFT_FWD, KID_AXIS_FWD, KID_AXIS_INV_MUL, KID_AXIS_INV, KID_IRFFT_THRESH,
     KID_RECHECK, KID_SWEEP, KID_ERODE, KID_INIT, KID_MAX, KID_FINALIZE, KID_ABSMAX, KID_PENALIZE, KID_RHO_HL,
-    KID_DIRECT, KID_SWEEP_LEVELS, KID_COUNT
+    KID_DIRECT, KID_SWEEP_LEVELS, KID_YX, KID_COUNT
 };
 const char *kKernelNames[KID_COUNT] = {
     "rotate_resample", "tool_spectrum", "rfft_x_fwd", "fft_axis_fwd", "fft_z_inv_mul", "fft_y_inv",
     "irfft_x_threshold", "recheck_near_threshold", "sweep_dilate", "erode_min", "init", "max_omega0",
-    "finalize", "absmax_omega0", "penalize", "rho_hi_lo", "direct_corr_tcgen05", "sweep_levels"};
+    "finalize", "absmax_omega0", "penalize", "rho_hi_lo", "direct_corr_tcgen05", "sweep_levels", "fft_yx_inv_threshold"};
 
 struct Tool {
     bool set = false;
@@ -593,6 +593,8 @@ void imf_default_options(imf_options *opt)
     opt->hbm_budget_bytes = 0;
     opt->erode_groups = 0;
     opt->fft_stages_only = 0;
+    opt->accessible_by_sweep = 0;
+    opt->separate_yx_passes = 0;
 }
 
 imf_status imf_create(const imf_options *opt, imf_handle *out)
@@ -1066,29 +1068,32 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
                 Launch L(h, KID_AXIS_INV_MUL, s);
                 launch_axis_fft(1, a, t.P[1], nb, s);
             }
-            {
-                AxisArgs a{};
-                a.in = h->Y1; a.in_so = y1so; a.in_sb = (long)t.P[1] * t.Hs; a.in_sl = t.Hs;
-                a.out = h->Y2; a.out_so = y2so; a.out_sb = (long)t.win[1] * t.Hs; a.out_sl = t.Hs;
-                a.nx = t.Hx; a.lin = t.P[1]; a.j0 = 0; a.lout = t.win[1]; a.scale = 1.f; a.tw = t.twy; a.plan = t.ply;
-                a.A2 = t.sy[0]; a.B2 = t.sy[1];
-                Launch L(h, KID_AXIS_INV, s);
-                launch_axis_fft(1, a, t.win[2], nb, s);
-            }
-            {
-                IrfftArgs a{};
-                a.in = h->Y2; a.in_sy = t.Hs; a.in_sz = (long)t.win[1] * t.Hs; a.in_so = y2so;
-                a.rows_y = t.win[1]; a.rows = t.win[1] * t.win[2]; a.nout = t.win[0];
-                a.g = h->g; a.g_sy = t.gpx; a.g_sz = (long)t.win[1] * t.gpx; a.g_so = gso;
-                a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
-                a.theta = (float)t.theta; a.band = (float)t.band; a.flag = op.recheck;
-                a.flags = h->flags; a.flag_count = fcount; a.flag_total = h->dev_small + 4; a.flag_cap = h->flag_cap;
-                a.status = status;
-                a.orient_base = o0; a.M = t.M; a.twM = t.twM; a.twP = t.twP; a.plan = t.plM;
-                a.A2 = t.sM[0]; a.B2 = t.sM[1];
-                a.write_bits = h->run_sweep || h->keep_g;
+            AxisArgs ay{};
+            ay.in = h->Y1; ay.in_so = y1so; ay.in_sb = (long)t.P[1] * t.Hs; ay.in_sl = t.Hs;
+            ay.out = h->Y2; ay.out_so = y2so; ay.out_sb = (long)t.win[1] * t.Hs; ay.out_sl = t.Hs;
+            ay.nx = t.Hx; ay.lin = t.P[1]; ay.j0 = 0; ay.lout = t.win[1]; ay.scale = 1.f; ay.tw = t.twy; ay.plan = t.ply;
+            ay.A2 = t.sy[0]; ay.B2 = t.sy[1];
+            IrfftArgs ax{};
+            ax.in = h->Y2; ax.in_sy = t.Hs; ax.in_sz = (long)t.win[1] * t.Hs; ax.in_so = y2so;
+            ax.rows_y = t.win[1]; ax.rows = t.win[1] * t.win[2]; ax.nout = t.win[0];
+            ax.g = h->g; ax.g_sy = t.gpx; ax.g_sz = (long)t.win[1] * t.gpx; ax.g_so = gso;
+            ax.bits = h->bits; ax.b_sy = t.wpr; ax.b_sz = (long)t.win[1] * t.wpr; ax.b_so = bso;
+            ax.theta = (float)t.theta; ax.band = (float)t.band; ax.flag = op.recheck;
+            ax.flags = h->flags; ax.flag_count = fcount; ax.flag_total = h->dev_small + 4; ax.flag_cap = h->flag_cap;
+            ax.status = status;
+            ax.orient_base = o0; ax.M = t.M; ax.twM = t.twM; ax.twP = t.twP; ax.plan = t.plM;
+            ax.A2 = t.sM[0]; ax.B2 = t.sM[1];
+            ax.write_bits = h->run_sweep || h->keep_g;
+            if (!op.separate_yx_passes && yx2_fits(ay, ax, t.Hs)) {
+                Launch L(h, KID_YX, s);
+                launch_yx2_threshold(ay, ax, t.Hs, t.win[2], nb, s);
+            } else {
+                {
+                    Launch L(h, KID_AXIS_INV, s);
+                    launch_axis_fft(1, ay, t.win[2], nb, s);
+                }
                 Launch L(h, KID_IRFFT_THRESH, s);
-                launch_irfft_threshold(a, nb, s);
+                launch_irfft_threshold(ax, nb, s);
             }
             TRY(tail_batch(h, t, rho, fix, o0, nb, s));
             h->last_batch_base = o0;

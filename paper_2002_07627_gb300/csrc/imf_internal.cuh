@@ -11,6 +11,7 @@ constexpr int kThreads = 256;
 
 // Device status word values (mirror imf_status).
 constexpr int kDevOk = 0;
+constexpr int kDevTimeout = 4;
 constexpr int kDevOverflow = 7;
 
 // ---------------------------------------------------------------------------------------
@@ -55,7 +56,7 @@ struct RfftArgs {
 // free translations are those with g <= theta).
 struct IrfftArgs {
     const float2 *in;
-    long in_sy, in_sz, in_so;
+    long in_sy, in_sz, in_so;    // rows evenly spaced: in_sz = rows_y * in_sy
     int rows_y, rows;            // window rows per z-plane, total window rows
     int nout;                    // window extent along x
     float *g;
@@ -84,6 +85,10 @@ void launch_irfft_threshold(const IrfftArgs &a, int norient, cudaStream_t s);
 void launch_axis2(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s);
 void launch_irfft2_threshold(const IrfftArgs &a, int norient, cudaStream_t s);
 size_t axis2_smem(int L);
+// the inverse y and x passes of one z-plane per block (fft2_kernels.cu); yx2_fits says whether
+// the plane (and the x pass scratch) fits in shared memory for these arguments
+bool yx2_fits(const AxisArgs &ay, const IrfftArgs &a, int hs);
+void launch_yx2_threshold(const AxisArgs &ay, const IrfftArgs &a, int hs, int nz, int norient, cudaStream_t s);
 size_t irfft2_smem(int M, int A, int B);
 
 // ---------------------------------------------------------------------------------------

@@ -403,3 +403,36 @@ def test_sweep_of_long_cutter_runs_matches_oracle():
     check_against_oracle(d, got, ref)
     assert got["accessible"].any() and not got["accessible"].all()
     check_against_oracle(d, run_gpu(d, orient_batch=3), ref)
+
+def _kernels_run(imf, design):
+    """Names of the kernels one more compute of `design` launches on `imf`."""
+    rho = torch.from_numpy(np.ascontiguousarray(design.rho)).cuda()
+    fix = None if design.fixture is None else torch.from_numpy(np.ascontiguousarray(design.fixture)).cuda()
+    imf.reset_kernel_times()
+    imf.set_profiling(True)
+    imf.compute(rho, fix)
+    imf.sync()
+    names = set(imf.kernel_times())
+    imf.set_profiling(False)
+    return names
+
+
+def test_fused_yx_pass_equals_separate_passes():
+    """The inverse y and x passes fused per z-plane (the plane kept in shared memory) run the
+    same arithmetic as the two separate kernels: f, the normalised field and the accessible set
+    are identical, and both meet the contract against the oracle. The last case is a grid whose
+    plane does not fit in shared memory, where the library falls back to the two kernels."""
+    d = _small3d(seed=4, n=(37, 44, 29), n_orient=6)
+    ref = oracle.imf(d)
+    for kw in ({}, {"accessible_by_sweep": True}):
+        a = run_gpu(d, orient_batch=4, **kw)
+        b = run_gpu(d, orient_batch=4, separate_yx_passes=True, **kw)
+        check_against_oracle(d, a, ref)
+        for k in ("f", "fbar", "secluded", "accessible"):
+            assert np.array_equal(a[k], b[k]), k
+        assert "fft_yx_inv_threshold" in _kernels_run(a["imf"], d)
+        kb = _kernels_run(b["imf"], d)
+        assert "fft_yx_inv_threshold" not in kb and "fft_y_inv" in kb
+    d = synth.config_beams(200, 12, 3)
+    a = run_gpu(d, orient_batch=3)
+    assert "fft_yx_inv_threshold" not in _kernels_run(a["imf"], d)
