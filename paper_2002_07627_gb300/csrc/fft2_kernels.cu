@@ -166,9 +166,8 @@ __device__ __forceinline__ void x_epilogue(const IrfftArgs &a, const float2 *u, 
 }
 
 // Free-bit words of nr window rows r0 .. from their flag bytes (rows fp bytes apart), one word
-// (32 translations along x) per thread and step: for a 4-byte group v with bytes b_i in {0, 1},
-// the multiplier 0x01020408 = 2^24 + 2^17 + 2^10 + 2^3 moves byte i (bit 8 i) to bit 24 + i and
-// every cross term to a distinct bit below 24 (no carries); bytes past nout are masked off.
+// (32 translations along x) per thread and step (pack_flag_bytes); bytes past nout are masked
+// off.
 template <int NT>
 __device__ __forceinline__ void x_pack_bits(const IrfftArgs &a, const uint8_t *sflag, int fp, int r0, int nr, long o)
 {
@@ -176,15 +175,9 @@ __device__ __forceinline__ void x_pack_bits(const IrfftArgs &a, const uint8_t *s
     for (int i = threadIdx.x; i < nr * nwq; i += NT) {
         const int ww = i / nwq, q = i - ww * nwq, rr = r0 + ww;
         const uint4 *fw = reinterpret_cast<const uint4 *>(sflag + (long)ww * fp + 32 * q);
-        uint32_t word = 0;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint4 v = fw[h];
-            const uint32_t g4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                word |= (((g4[k] & 0x01010101u) * 0x01020408u) >> 24 & 0xfu) << (16 * h + 4 * k);
-        }
+        const uint4 f0 = fw[0], f1 = fw[1];
+        const uint32_t g8[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+        uint32_t word = pack_flag_bytes(g8);
         const int rem = a.nout - 32 * q;
         if (rem < 32) word &= (1u << rem) - 1u;
         const int y = rr % a.rows_y, z = rr / a.rows_y;

@@ -1,11 +1,14 @@
-// Host-only exports that run the kernels' FFT building blocks (fft.cuh, fft2.cuh) on the CPU,
-// for the CPU unit tests. Not part of libimf and never loaded by the product path.
+// Host-only exports that run the kernels' building blocks (fft.cuh, fft2.cuh, erode_plan.h,
+// sweep_bits.cuh) on the CPU, for the CPU unit tests. Not part of libimf and never loaded by the
+// product path.
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "fft.cuh"
 #include "fft2.cuh"
 #include "erode_plan.h"
+#include "sweep_bits.cuh"
 
 extern "C" int imf_host_fft(int L, int sign, const float *in, float *out)
 {
@@ -97,4 +100,31 @@ extern "C" void imf_host_erode_constants(long *out)
 {
     out[0] = imf::kErTX; out[1] = imf::kErTY; out[2] = imf::kErTZ; out[3] = imf::kErXT;
     out[4] = imf::kErMaxL; out[5] = (long)imf::kErodeBudget; out[6] = imf::kErMaxRunsPerChunk;
+}
+
+// One cutter run of the sweep as the kernels compute it (sweep_bits.cuh): the dilation levels
+// of a row of wpr words, then the two windows of the run's descriptor for output word q at
+// shift s >= 0 and length L (1 .. 32). Returns 1 for arguments out of range (reads past the row).
+extern "C" int imf_host_sweep_run(const uint32_t *row, int wpr, int q, int s, int L, uint32_t *out)
+{
+    if (!row || !out || wpr < 2 || q < 0 || s < 0 || L < 1 || L > 32) return 1;
+    const int4 d = imf::sweep_pair(0, s, L);
+    if (q + d.x + d.y + 1 >= wpr) return 1;
+    std::vector<uint32_t> lev((size_t)imf::kSweepLevels * wpr);
+    for (int w = 0; w < wpr; ++w) {
+        uint32_t l[imf::kSweepLevels - 1];
+        imf::sweep_level_words(row[w], w + 1 < wpr ? row[w + 1] : 0u, l);
+        lev[w] = row[w];
+        for (int j = 1; j < imf::kSweepLevels; ++j) lev[(size_t)j * wpr + w] = l[j - 1];
+    }
+    *out = imf::sweep_pair_bits(lev.data() + (size_t)d.w * wpr + q + d.x, d);
+    return 0;
+}
+
+// The x pass's packing of 32 free-flag bytes into one word (pack_flag_bytes).
+extern "C" uint32_t imf_host_pack_flags(const uint8_t *bytes32)
+{
+    uint32_t g8[8];
+    std::memcpy(g8, bytes32, sizeof g8);
+    return imf::pack_flag_bytes(g8);
 }

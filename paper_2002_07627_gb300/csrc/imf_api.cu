@@ -836,16 +836,13 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
         // level j with 2^j <= L <= 2^(j+1) (runs are at most 32 long), windows s and s + L - 2^j
         for (size_t m = 0; m < ivs[i].size(); m += 4) {
             const int a0 = ivs[i][m], b0 = ivs[i][m + 1], dy = ivs[i][m + 2], dz = ivs[i][m + 3];
-            const int L = b0 - a0 + 1;
-            int j = 0;
-            while (j < kSweepLevels - 1 && (2 << j) <= L) ++j;
-            const int sa = t.kmax[0] - b0, sb = sa + L - (1 << j);
+            const int L = b0 - a0 + 1, sa = t.kmax[0] - b0;
             const long row = (long)(t.kmax[2] - dz) * t.win[1] * t.wpr + (long)(t.kmax[1] - dy) * t.wpr;
             if (row + (sa >> 5) > 0x7fffffffL) {
                 free_tool(h, t);
                 return fail(h, IMF_ERR_INVALID_ARG, "translation window too large for the sweep descriptors");
             }
-            ivv.push_back(make_int4((int)(row + (sa >> 5)), (sb >> 5) - (sa >> 5), (sa & 31) | ((sb & 31) << 8), j));
+            ivv.push_back(sweep_pair(row, sa, L));
         }
         ivst[i + 1] = (int)ivv.size();
         t.n_sh += (long)t.sh[i].size() / 3;

@@ -1,6 +1,8 @@
 // Internal kernel interface of libimf (not part of the C ABI).
 #pragma once
 #include <cstdint>
+
+#include "sweep_bits.cuh"
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
@@ -133,9 +135,9 @@ struct RecheckArgs {
 void launch_recheck(const RecheckArgs &a, cudaStream_t s);
 void launch_recheck_blocks(const RecheckArgs &a, int max_points, cudaStream_t s);
 
-// Free bits with their dilation levels: level j (0 .. kSweepLevels - 1) of every slot lives at
-// bits + j * lstride, word i of level j being the OR of the free bits i*32+t .. i*32+t+2^j-1.
-constexpr int kSweepLevels = 5;
+// Free bits with their dilation levels (sweep_bits.cuh): level j (0 .. kSweepLevels - 1) of
+// every slot lives at bits + j * lstride, bit t of word i of level j being the OR of the free
+// bits 32 i + t .. 32 i + t + 2^j - 1.
 struct SweepLevelsArgs {
     uint32_t *bits;              // level 0 of slot 0 (the free bits)
     long lstride;                // words between levels
@@ -146,9 +148,7 @@ struct SweepArgs {
     const uint32_t *bits;        // level 0 of slot 0; level j at + j * lstride
     long lstride;
     long b_sy, b_sz, b_so;
-    // per cutter run, one int4: x = window row offset (kz - dz) b_sz + (ky - dy) b_sy plus the
-    // word of the first shift s = kx - b, y = word distance to the second shift s + L - 2^j,
-    // z = (s & 31) | ((s + L - 2^j) & 31) << 8, w = level j = min(4, floor(log2 L))
+    // per cutter run, sweep_pair(row, s, L) with row = (kz - dz) b_sz + (ky - dy) b_sy
     const int4 *pairs;
     const int *pair_start;       // n_orient + 1
     int nx, ny, nz, awords;

@@ -138,15 +138,10 @@ __global__ void sweep_levels_kernel(SweepLevelsArgs a)
 {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < a.n; i += (long)gridDim.x * blockDim.x) {
         const int w = (int)(i % a.wpr);
-        const uint32_t lo = a.bits[i], hi = w + 1 < a.wpr ? a.bits[i + 1] : 0u;
-        uint64_t v = (uint64_t)lo | ((uint64_t)hi << 32);
-        // after the step with shift 2^(j-1), bit t < 32 of v is the OR of the source bits
-        // t .. t + 2^j - 1 (all below bit 64 for j <= 4)
+        uint32_t lev[kSweepLevels - 1];
+        sweep_level_words(a.bits[i], w + 1 < a.wpr ? a.bits[i + 1] : 0u, lev);
 #pragma unroll
-        for (int j = 1; j < kSweepLevels; ++j) {
-            v |= v >> (1 << (j - 1));
-            a.bits[j * a.lstride + i] = (uint32_t)v;
-        }
+        for (int j = 1; j < kSweepLevels; ++j) a.bits[j * a.lstride + i] = lev[j - 1];
     }
 }
 
@@ -184,9 +179,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a)
             if (!live || (acc & full) == full) continue;
             for (int i = 0; i < cn; ++i) {
                 const int4 d = sp[i];
-                const uint32_t *p = base + (long)d.w * a.lstride + d.x;
-                const uint32_t u0 = p[0], u1 = p[1], v0 = p[d.y], v1 = p[d.y + 1];
-                acc |= __funnelshift_r(u0, u1, d.z & 31) | __funnelshift_r(v0, v1, d.z >> 8);
+                acc |= sweep_pair_bits(base + (long)d.w * a.lstride + d.x, d);
             }
         }
         if (live) {

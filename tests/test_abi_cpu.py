@@ -188,3 +188,59 @@ def test_erosion_plan_covers_every_sharp_point_once_within_the_tile(lib, case):
             covered += [(kx, ky, kz) for kx in range(kx_last - Lr + 1, kx_last + 1)]
     assert len(covered) == len(sh)
     assert sorted(covered) == sorted(map(tuple, sh.tolist()))
+
+
+def _sliding_or(row_bits, start, L):
+    """32 bits: bit t is the OR of row_bits[start + t .. start + t + L - 1] (0 past the row)."""
+    n = len(row_bits)
+    out = 0
+    for t in range(32):
+        lo, hi = start + t, min(n, start + t + L)
+        if lo < hi and row_bits[lo:hi].any():
+            out |= 1 << t
+    return out
+
+
+def test_sweep_run_from_dilation_levels_equals_the_sliding_or(lib):
+    """One cutter run of the sweep (Eq. eq_conv_A) as the kernels compute it: dilation levels
+    D_j of the free bits and two windows of length 2^j per run must give the sliding OR of
+    length L for every run length 1 .. 32, every bit shift and output word, on sparse, dense
+    and structured rows (brute force on the unpacked bits)."""
+    L_ = ctypes.CDLL(build.HOSTLIB)
+    L_.imf_host_sweep_run.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_void_p]
+    rng = np.random.default_rng(7)
+    wpr = 8
+    rows = [rng.random(32 * wpr) < p for p in (0.02, 0.3, 0.9)]
+    iso = np.zeros(32 * wpr, bool)
+    iso[[0, 31, 32, 63, 100, 159, 160, 200]] = True          # isolated bits at word edges
+    rows.append(iso)
+    out = np.zeros(1, np.uint32)
+    for bits in rows:
+        words = np.packbits(bits.reshape(-1, 32)[:, ::-1], axis=1).view(">u4").astype(np.uint32).ravel()
+        words = np.ascontiguousarray(words)
+        for L in range(1, 33):
+            for s in list(range(0, 40)) + [63, 64, 95]:
+                for q in (0, 1, 2):
+                    rc = L_.imf_host_sweep_run(words.ctypes.data, wpr, q, s, L, out.ctypes.data)
+                    if q + s // 32 + 2 >= wpr:
+                        continue
+                    assert rc == 0, (L, s, q)
+                    assert int(out[0]) == _sliding_or(bits, 32 * q + s, L), (L, s, q)
+    assert L_.imf_host_sweep_run(words.ctypes.data, wpr, 0, 0, 33, out.ctypes.data) == 1   # runs are <= 32
+    assert L_.imf_host_sweep_run(words.ctypes.data, wpr, 7, 0, 4, out.ctypes.data) == 1    # past the row
+
+
+def test_flag_bytes_pack_into_bits(lib):
+    """The x pass's packing of 32 free-flag bytes into one word: bit b = low bit of byte b,
+    whatever the other bits of the bytes hold (the multiply must not carry between groups)."""
+    L_ = ctypes.CDLL(build.HOSTLIB)
+    L_.imf_host_pack_flags.argtypes = [ctypes.c_void_p]
+    L_.imf_host_pack_flags.restype = ctypes.c_uint32
+    rng = np.random.default_rng(3)
+    cases = [np.zeros(32, np.uint8), np.ones(32, np.uint8)] + [rng.integers(0, 2, 32).astype(np.uint8) for _ in range(200)]
+    cases += [rng.integers(0, 256, 32).astype(np.uint8) for _ in range(200)]
+    for b in cases:
+        b = np.ascontiguousarray(b)
+        want = sum(int(v & 1) << i for i, v in enumerate(b))
+        assert L_.imf_host_pack_flags(b.ctypes.data) == want
