@@ -177,6 +177,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a)
             for (int i = threadIdx.x; i < cn; i += blockDim.x) sp[i] = a.pairs[c0 + i];
             __syncthreads();
             if (!live || (acc & full) == full) continue;
+            // unrolled so that the loads of several runs are in flight at once
+#pragma unroll 4
             for (int i = 0; i < cn; ++i) {
                 const int4 d = sp[i];
                 acc |= sweep_pair_bits(base + (long)d.w * a.lstride + d.x, d);
