@@ -18,13 +18,16 @@
 namespace imf {
 namespace fft2 {
 
-constexpr int kMaxFactor = 16;
+constexpr int kMaxFactor = 16;      // factors of the kernels with 16 slots per pencil
+constexpr int kMaxFactorBig = 24;   // factors of the axis kernel with 32 slots per pencil
 
 __host__ __device__ constexpr bool supported(int n)
 {
     return n == 2 || n == 3 || n == 4 || n == 5 || n == 6 || n == 7 || n == 8 || n == 9 || n == 10 || n == 12 ||
            n == 14 || n == 15 || n == 16;
 }
+// factors above 16 (only kernels built for them dispatch these)
+__host__ __device__ constexpr bool supported_big(int n) { return n == 18 || n == 20 || n == 21 || n == 24; }
 
 // cos and sin of 2 pi m / n from their Taylor series (argument reduced to [-pi, pi))
 __host__ __device__ constexpr double taylor_cos(double x)
@@ -112,15 +115,17 @@ template <int S, int N> __host__ __device__ __forceinline__ void dft_reg(float2 
     }
 }
 
-// Split of L for the two passes: A (pass-1 DFT size) >= B (pass-2 DFT size), both supported,
-// as balanced as possible. Returns false when L has no such split.
-inline bool choose_split(int L, int *A, int *B)
+// Split of L for the two passes: A (pass-1 DFT size) >= B (pass-2 DFT size), both supported
+// with factors up to maxA (kMaxFactor or kMaxFactorBig), as balanced as possible. Returns false
+// when L has no such split.
+inline bool choose_split(int L, int *A, int *B, int maxA = kMaxFactor)
 {
+    auto ok = [&](int n) { return n <= maxA && (supported(n) || supported_big(n)); };
     int bestA = 0, bestB = 0;
-    for (int b = 2; b <= kMaxFactor; ++b) {
+    for (int b = 2; b <= maxA; ++b) {
         if (L % b) continue;
         const int a = L / b;
-        if (a < b || !supported(a) || !supported(b)) continue;
+        if (a < b || !ok(a) || !ok(b)) continue;
         if (!bestA || a < bestA) { bestA = a; bestB = b; }
     }
     if (!bestA) return false;
@@ -168,13 +173,25 @@ template <typename F> __host__ __device__ __forceinline__ void with_size(int n, 
     }
 }
 
+// with_size over the sizes above 16 as well (kernels with 32 slots per pencil).
+template <typename F> __host__ __device__ __forceinline__ void with_size_big(int n, F &&f)
+{
+    switch (n) {
+    case 18: f(std::integral_constant<int, 18>{}); break;
+    case 20: f(std::integral_constant<int, 20>{}); break;
+    case 21: f(std::integral_constant<int, 21>{}); break;
+    case 24: f(std::integral_constant<int, 24>{}); break;
+    default: with_size(n, f); break;
+    }
+}
+
 // Host emulation of a whole transform of one pencil (tests): x (length L = A B) -> X with
 // the kernels' pass structure and arithmetic; T is scratch of length L.
 template <int S>
 inline void fft2_pencil_host(int A, int B, const float2 *x, float2 *X, float2 *T, const float2 *tw)
 {
     for (int n1 = 0; n1 < B; ++n1)
-        with_size(A, [&](auto AA) {
+        with_size_big(A, [&](auto AA) {
             constexpr int a = decltype(AA)::value;
             float2 v[a];
             for (int n2 = 0; n2 < a; ++n2) v[n2] = x[n1 + B * n2];
@@ -182,7 +199,7 @@ inline void fft2_pencil_host(int A, int B, const float2 *x, float2 *X, float2 *T
             for (int k2 = 0; k2 < a; ++k2) T[n1 * a + k2] = v[k2];
         });
     for (int k2 = 0; k2 < A; ++k2)
-        with_size(B, [&](auto BB) {
+        with_size_big(B, [&](auto BB) {
             constexpr int b = decltype(BB)::value;
             float2 u[b];
             for (int n1 = 0; n1 < b; ++n1) u[n1] = T[n1 * A + k2];

@@ -20,28 +20,43 @@ namespace {
 constexpr int kW2 = 16;          // pencils (axis passes) or rows (x pass) per block
 constexpr int kT2 = 256;         // threads per block: kW2 pencils x 16 slots
 
-// Columns [z][y][kx] of W = 16 consecutive kx per block; a pencil is one (batch row b, kx)
-// pair. When nx is not a multiple of 16, the last grid column of blocks takes the remaining
-// ntail kx columns of 16 batch rows at a time, so no block transforms empty pencils.
-template <int S> __global__ void __launch_bounds__(kT2) axis2_kernel(AxisArgs a, int nbatch, int nfull, int ntail)
+// Columns [z][y][kx] of W consecutive kx per block; a pencil is one (batch row b, kx) pair.
+// With factors up to 16 a block has W = 16 pencils of 16 slots; with factors up to 24 (BIG)
+// W = 8 pencils of 32 slots. When nx is not a multiple of W, the last grid column of blocks
+// takes the remaining ntail kx columns of W batch rows at a time, so no block transforms empty
+// pencils.
+template <bool BIG> struct AxisShape {
+    static constexpr int W = BIG ? 8 : kW2;       // pencils per block
+    static constexpr int LOGW = BIG ? 3 : 4;
+    template <typename F> __device__ __forceinline__ static void with(int n, F &&f)
+    {
+        if constexpr (BIG) fft2::with_size_big(n, f);
+        else fft2::with_size(n, f);
+    }
+};
+
+template <int S, bool BIG>
+__global__ void __launch_bounds__(kT2) axis2_kernel(AxisArgs a, int nbatch, int nfull, int ntail)
 {
+    using Sh = AxisShape<BIG>;
+    constexpr int kW = Sh::W;
     extern __shared__ float2 sm[];
     const int A = a.A2, B = a.B2, L = A * B;
-    float2 *tile = sm, *tw = sm + (size_t)L * kW2;
-    const int w = threadIdx.x & (kW2 - 1), p = threadIdx.x >> 4;
+    float2 *tile = sm, *tw = sm + (size_t)L * kW;
+    const int w = threadIdx.x & (kW - 1), p = threadIdx.x >> Sh::LOGW;
     long b;
     int c;
     bool ok;
     if ((int)blockIdx.x < nfull) {
         b = blockIdx.y;
-        c = (int)blockIdx.x * kW2 + w;
+        c = (int)blockIdx.x * kW + w;
         ok = true;
     } else {
-        const long f0 = (long)blockIdx.y * kW2;
+        const long f0 = (long)blockIdx.y * kW;
         if (f0 >= (long)nbatch * ntail) return;  // whole block idle (uniform)
         const long f = f0 + w;
         b = f / ntail;
-        c = nfull * kW2 + (int)(f - b * ntail);
+        c = nfull * kW + (int)(f - b * ntail);
         ok = b < nbatch;
     }
     for (int i = threadIdx.x; i < L; i += kT2) tw[i] = a.tw[i];
@@ -53,7 +68,7 @@ template <int S> __global__ void __launch_bounds__(kT2) axis2_kernel(AxisArgs a,
     const bool act1 = p < B && ok;
     const float2 *in = a.in + o * a.in_so + b * a.in_sb + c;
     const float2 *mul = a.mul ? a.mul + o * a.mul_so + b * a.mul_sb + c : nullptr;
-    fft2::with_size(A, [&](auto AA) {
+    Sh::with(A, [&](auto AA) {
         constexpr int NA = decltype(AA)::value;
         float2 v[NA];
         if (act1) {
@@ -84,18 +99,18 @@ template <int S> __global__ void __launch_bounds__(kT2) axis2_kernel(AxisArgs a,
         if (act1) {
             fft2::twiddle<S, NA>(v, p, tw);
 #pragma unroll
-            for (int k2 = 0; k2 < NA; ++k2) tile[(p * NA + k2) * kW2 + w] = v[k2];
+            for (int k2 = 0; k2 < NA; ++k2) tile[(p * NA + k2) * kW + w] = v[k2];
         }
     });
     __syncthreads();
     // pass 2: slot p = k2 < A, B-point DFT over n1; X[k2 + A k1] -> out[j - j0] if in window
     if (p < A && ok) {
         float2 *out = a.out + o * a.out_so + b * a.out_sb + c;
-        fft2::with_size(B, [&](auto BB) {
+        Sh::with(B, [&](auto BB) {
             constexpr int NB = decltype(BB)::value;
             float2 u[NB];
 #pragma unroll
-            for (int n1 = 0; n1 < NB; ++n1) u[n1] = tile[(n1 * A + p) * kW2 + w];
+            for (int n1 = 0; n1 < NB; ++n1) u[n1] = tile[(n1 * A + p) * kW + w];
             fft2::dft_reg<S, NB>(u);
 #pragma unroll
             for (int k1 = 0; k1 < NB; ++k1) {
@@ -404,7 +419,12 @@ template <typename K> void set_smem2(K kernel, size_t bytes)
 
 } // namespace
 
-size_t axis2_smem(int L) { return (size_t)(L * kW2 + L) * sizeof(float2); }
+// the BIG kernel has half the pencils per block and lengths up to 24 x 24
+static size_t axis2_smem_for(int A, int B)
+{
+    const bool big = A > fft2::kMaxFactor;
+    return (size_t)(A * B * (big ? AxisShape<true>::W : kW2) + A * B) * sizeof(float2);
+}
 
 size_t irfft2_smem(int M, int A, int B) { return (size_t)x_layout(2 * M + 1, kT2, M, A, B).end * sizeof(float2); }
 
@@ -413,18 +433,25 @@ size_t yx2_smem(int Ly, int hs, int M, int rows)
     return (size_t)(yx2_flags_offset(Ly, hs, M) + ((long)rows * ((2 * M + 31) & ~31) + 7) / 8) * sizeof(float2);
 }
 
-void launch_axis2(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s)
+template <bool BIG> static void launch_axis2_shape(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s)
 {
-    const size_t smem = axis2_smem(a.A2 * a.B2);
-    const int nfull = a.nx / kW2, ntail = a.nx % kW2;
+    constexpr int kW = AxisShape<BIG>::W;
+    const size_t smem = axis2_smem_for(a.A2, a.B2);
+    const int nfull = a.nx / kW, ntail = a.nx % kW;
     dim3 grid(nfull + (ntail ? 1 : 0), nbatch, norient);
     if (sign < 0) {
-        set_smem2(axis2_kernel<-1>, smem);
-        axis2_kernel<-1><<<grid, kT2, smem, s>>>(a, nbatch, nfull, ntail);
+        set_smem2(axis2_kernel<-1, BIG>, smem);
+        axis2_kernel<-1, BIG><<<grid, kT2, smem, s>>>(a, nbatch, nfull, ntail);
     } else {
-        set_smem2(axis2_kernel<1>, smem);
-        axis2_kernel<1><<<grid, kT2, smem, s>>>(a, nbatch, nfull, ntail);
+        set_smem2(axis2_kernel<1, BIG>, smem);
+        axis2_kernel<1, BIG><<<grid, kT2, smem, s>>>(a, nbatch, nfull, ntail);
     }
+}
+
+void launch_axis2(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s)
+{
+    if (a.A2 > fft2::kMaxFactor) launch_axis2_shape<true>(sign, a, nbatch, norient, s);
+    else launch_axis2_shape<false>(sign, a, nbatch, norient, s);
 }
 
 void launch_irfft2_threshold(const IrfftArgs &a, int norient, cudaStream_t s)
@@ -442,7 +469,8 @@ namespace imf {
 
 bool yx2_fits(const AxisArgs &ay, const IrfftArgs &a, int hs)
 {
-    if (ay.A2 <= 0 || a.A2 <= 0 || ay.in_sl != hs || ay.scale != 1.f || ay.conj_out || ay.mul || ay.j0 != 0 ||
+    // y pass slots are the block's 16 warps, x pass factors those of the x-pass kernel
+    if (ay.A2 <= 0 || a.A2 <= 0 || ay.A2 > fft2::kMaxFactor || a.A2 > fft2::kMaxFactor || ay.in_sl != hs || ay.scale != 1.f || ay.conj_out || ay.mul || ay.j0 != 0 ||
         ay.lin != ay.A2 * ay.B2 || ay.in_sb != (long)ay.lin * hs || (hs & 1))
         return false;
     // x pass 1 writes its elements into the row itself: M = A B must fit the row

@@ -47,7 +47,7 @@ extern "C" long imf_host_check_div(int maxd, int maxj)
 extern "C" int imf_host_fft2(int L, int sign, const float *in, float *out)
 {
     int A = 0, B = 0;
-    if (L < 4 || !imf::fft2::choose_split(L, &A, &B)) return -1;
+    if (L < 4 || !imf::fft2::choose_split(L, &A, &B, imf::fft2::kMaxFactorBig)) return -1;
     std::vector<float2> tw(L), x(L), X(L), T(L);
     for (int m = 0; m < L; ++m) {
         const double ang = -2.0 * M_PI * (double)m / (double)L;

@@ -261,12 +261,13 @@ int next_smooth(int n)
 
 // Relative cost of one length-L pass: L times the summed per-point cost of its radix stages
 // (radix-8 and radix-4 butterflies are the cheapest per point, 7 and 5 the dearest), or a
-// flat per-point cost for lengths the two-pass register transform handles.
-double fft_cost(int L)
+// flat per-point cost for lengths the two-pass register transform handles with factors up to
+// maxA (16 for the x pass, 24 for the y and z passes).
+double fft_cost(int L, int maxA)
 {
     int A = 0, B = 0;
     // a length with a two-pass split crosses shared memory once and runs unrolled DFTs
-    if (fft2::choose_split(L, &A, &B)) return L * 1.1;
+    if (fft2::choose_split(L, &A, &B, maxA)) return L * (A > fft2::kMaxFactor ? 1.2 : 1.1);
     FftPlan p;
     if (!make_plan(L, &p)) return 1e300;
     double c = 0;
@@ -285,14 +286,14 @@ double fft_cost(int L)
 
 // FFT plan choice: among smooth lengths from the minimum up to 12 % above it, the cheapest
 // by fft_cost (a padded transform is correct for any length at or above the minimum).
-int best_smooth(int n)
+int best_smooth(int n, int maxA)
 {
     const int n0 = next_smooth(n);
     int best = n0;
-    double bc = fft_cost(n0);
+    double bc = fft_cost(n0, maxA);
     for (int m = n0 + 1; m <= n0 + n0 / 8; ++m) {
         if (!is_smooth(m)) continue;
-        const double c = fft_cost(m);
+        const double c = fft_cost(m, maxA);
         if (c < bc) { bc = c; best = m; }
     }
     return best;
@@ -803,18 +804,18 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
             return fail(h, IMF_ERR_INVALID_ARG, "rotated tool offsets exceed +-511 voxels");
         }
     }
-    t.M = best_smooth((req[0] + 1) / 2);
+    t.M = best_smooth((req[0] + 1) / 2, fft2::kMaxFactor);
     t.P[0] = 2 * t.M;
-    t.P[1] = best_smooth(req[1]);
-    t.P[2] = best_smooth(req[2]);
+    t.P[1] = best_smooth(req[1], fft2::kMaxFactorBig);
+    t.P[2] = best_smooth(req[2], fft2::kMaxFactorBig);
     t.Hx = t.M + 1;
     t.Hs = (t.Hx + 1) & ~1;
     t.gpx = (t.win[0] + 3) & ~3;
     t.wpr = (t.win[0] + 31) / 32 + 2;
     const bool split = !h->opt.fft_stages_only;
     if (!split || !fft2::choose_split(t.M, &t.sM[0], &t.sM[1])) t.sM[0] = t.sM[1] = 0;
-    if (!split || !fft2::choose_split(t.P[1], &t.sy[0], &t.sy[1])) t.sy[0] = t.sy[1] = 0;
-    if (!split || !fft2::choose_split(t.P[2], &t.sz[0], &t.sz[1])) t.sz[0] = t.sz[1] = 0;
+    if (!split || !fft2::choose_split(t.P[1], &t.sy[0], &t.sy[1], fft2::kMaxFactorBig)) t.sy[0] = t.sy[1] = 0;
+    if (!split || !fft2::choose_split(t.P[2], &t.sz[0], &t.sz[1], fft2::kMaxFactorBig)) t.sz[0] = t.sz[1] = 0;
     if (!make_plan(t.M, &t.plM) || !make_plan(t.P[1], &t.ply) || !make_plan(t.P[2], &t.plz)) {
         free_tool(h, t);
         return fail(h, IMF_ERR_INVALID_ARG, "no FFT plan for %d x %d x %d", t.P[0], t.P[1], t.P[2]);

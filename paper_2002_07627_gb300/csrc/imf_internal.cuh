@@ -86,7 +86,6 @@ void launch_irfft_threshold(const IrfftArgs &a, int norient, cudaStream_t s);
 // two-pass register variants (fft2_kernels.cu); the dispatchers above call them when A2 > 0
 void launch_axis2(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s);
 void launch_irfft2_threshold(const IrfftArgs &a, int norient, cudaStream_t s);
-size_t axis2_smem(int L);
 // the inverse y and x passes of one z-plane per block (fft2_kernels.cu); yx2_fits says whether
 // the plane (and the x pass scratch) fits in shared memory for these arguments
 bool yx2_fits(const AxisArgs &ay, const IrfftArgs &a, int hs);

@@ -41,14 +41,15 @@ def test_host_fft_matches_numpy(lib, L):
     assert np.max(np.abs(inv - np.fft.ifft(x) * L)) < 2e-6 * scale * max(1.0, np.log2(L))
 
 
-_SPLIT_SIZES = (2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16)
+_SPLIT_SIZES = (2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 18, 20, 21, 24)
 _SPLIT_LENGTHS = sorted({a * b for a in _SPLIT_SIZES for b in _SPLIT_SIZES if a >= b})
 
 
 @pytest.mark.parametrize("L", _SPLIT_LENGTHS)
 def test_host_two_pass_fft_matches_numpy(lib, L):
-    """The two-pass register transform (every length A B with A, B in the supported set) agrees
-    with numpy's FFT in both directions, and its split is the balanced one with A >= B."""
+    """The two-pass register transform (every length A B with A, B in the supported set, factors
+    above 16 included: the y and z passes use them for lengths above 256) agrees with numpy's
+    FFT in both directions, and its split is the balanced one with A >= B."""
     rng = np.random.default_rng(1000 + L)
     x = rng.normal(size=L) + 1j * rng.normal(size=L)
     fwd, (A, B) = binding.host_fft2(x, -1)
@@ -63,7 +64,7 @@ def test_host_two_pass_fft_matches_numpy(lib, L):
 def test_host_two_pass_fft_single_tones(lib):
     """A unit impulse at n0 transforms to exp(-+2 pi i n0 k / L) exactly up to rounding: pins
     the sign convention and the index maps n = n1 + B n2, k = k2 + A k1 separately."""
-    for L in (96, 168, 192, 150, 210):
+    for L in (96, 168, 192, 150, 210, 320, 400, 576):
         for n0 in (0, 1, 7, L - 1):
             x = np.zeros(L, complex)
             x[n0] = 1.0
