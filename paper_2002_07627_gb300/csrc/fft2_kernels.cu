@@ -35,8 +35,12 @@ template <bool BIG> struct AxisShape {
     }
 };
 
-template <int S, bool BIG>
-__global__ void __launch_bounds__(kT2) axis2_kernel(AxisArgs a, int nbatch, int nfull, int ntail)
+// MUL: whether the pointwise factor a.mul is applied on load (the inverse z pass): 1 always,
+// 0 never, -1 decided at run time. The small shape (axis2_kernel) decides at run time (62
+// registers, four blocks per SM); the big shape (axis2_big_kernel) is specialised, so that
+// without the factor it fits three blocks per SM (80 registers) while the z pass keeps its 120.
+template <int S, bool BIG, int MUL>
+__device__ __forceinline__ void axis2_body(const AxisArgs &a, int nbatch, int nfull, int ntail)
 {
     using Sh = AxisShape<BIG>;
     constexpr int kW = Sh::W;
@@ -67,12 +71,12 @@ __global__ void __launch_bounds__(kT2) axis2_kernel(AxisArgs a, int nbatch, int 
     // thread enters (the size is uniform), so the barrier inside is reached by all.
     const bool act1 = p < B && ok;
     const float2 *in = a.in + o * a.in_so + b * a.in_sb + c;
-    const float2 *mul = a.mul ? a.mul + o * a.mul_so + b * a.mul_sb + c : nullptr;
+    const float2 *mul = (MUL != 0 && a.mul) ? a.mul + o * a.mul_so + b * a.mul_sb + c : nullptr;
     Sh::with(A, [&](auto AA) {
         constexpr int NA = decltype(AA)::value;
         float2 v[NA];
         if (act1) {
-            if (mul) {
+            if (MUL == 1 || mul) {
                 float2 m[NA];
 #pragma unroll
                 for (int n2 = 0; n2 < NA; ++n2) {
@@ -123,6 +127,17 @@ __global__ void __launch_bounds__(kT2) axis2_kernel(AxisArgs a, int nbatch, int 
             }
         });
     }
+}
+
+template <int S> __global__ void __launch_bounds__(kT2) axis2_kernel(AxisArgs a, int nbatch, int nfull, int ntail)
+{
+    axis2_body<S, false, -1>(a, nbatch, nfull, ntail);
+}
+
+template <int S, int MUL>
+__global__ void __launch_bounds__(kT2, MUL == 0 ? 3 : 1) axis2_big_kernel(AxisArgs a, int nbatch, int nfull, int ntail)
+{
+    axis2_body<S, true, MUL>(a, nbatch, nfull, ntail);
 }
 
 // Pass-1 input of the inverse x pass for thread p of a row: the half spectrum X[0..M] of the
@@ -439,12 +454,17 @@ template <bool BIG> static void launch_axis2_shape(int sign, const AxisArgs &a, 
     const size_t smem = axis2_smem_for(a.A2, a.B2);
     const int nfull = a.nx / kW, ntail = a.nx % kW;
     dim3 grid(nfull + (ntail ? 1 : 0), nbatch, norient);
-    if (sign < 0) {
-        set_smem2(axis2_kernel<-1, BIG>, smem);
-        axis2_kernel<-1, BIG><<<grid, kT2, smem, s>>>(a, nbatch, nfull, ntail);
+    auto go = [&](auto kernel) {
+        set_smem2(kernel, smem);
+        kernel<<<grid, kT2, smem, s>>>(a, nbatch, nfull, ntail);
+    };
+    if constexpr (BIG) {
+        if (sign < 0) go(axis2_big_kernel<-1, 0>);
+        else if (a.mul) go(axis2_big_kernel<1, 1>);
+        else go(axis2_big_kernel<1, 0>);
     } else {
-        set_smem2(axis2_kernel<1, BIG>, smem);
-        axis2_kernel<1, BIG><<<grid, kT2, smem, s>>>(a, nbatch, nfull, ntail);
+        if (sign < 0) go(axis2_kernel<-1>);
+        else go(axis2_kernel<1>);
     }
 }
 
