@@ -18,7 +18,7 @@
 // first) exactly as the float minimum does, so the result does not depend on the split.
 #include <cfloat>
 
-#include "imf_internal.cuh"
+#include "erode.cuh"
 
 namespace imf {
 

@@ -8,7 +8,7 @@
 #include <utility>
 #include <vector>
 
-#include "imf_internal.cuh"
+#include "erode.cuh"
 
 namespace imf {
 

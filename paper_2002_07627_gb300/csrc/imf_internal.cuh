@@ -1,11 +1,11 @@
 // Internal kernel interface of libimf (not part of the C ABI).
 #pragma once
 #include <cstdint>
-
-#include "sweep_bits.cuh"
 #include <cuda_runtime.h>
 
+#include "erode.cuh"
 #include "fft.cuh"
+#include "sweep_bits.cuh"
 
 namespace imf {
 
@@ -131,7 +131,6 @@ struct RecheckArgs {
     double theta;
     int orient_base;
 };
-void launch_recheck(const RecheckArgs &a, cudaStream_t s);
 void launch_recheck_blocks(const RecheckArgs &a, int max_points, cudaStream_t s);
 
 // Free bits with their dilation levels (sweep_bits.cuh): level j (0 .. kSweepLevels - 1) of
@@ -158,41 +157,7 @@ void launch_sweep_levels(const SweepLevelsArgs &a, cudaStream_t s);
 void launch_sweep(const SweepArgs &a, cudaStream_t s);
 
 
-// Tiled minimum over sharp points. A block owns kErTX x kErTY x kErTZ outputs (kErXT
-// consecutive x per thread; 1024 threads, one block per SM); the sharp points of an
-// orientation are runs along x, grouped in dz-chunks whose g tile fits the shared-memory
-// budget. Larger blocks fill less halo per output and need fewer chunks per orientation
-// (64 x 16 x 8: 4.17 ms per 128^3 x 64 step against 4.77 ms for 64 x 8 x 8 in 512 threads
-// and 7.2 ms for 32 x 8 x 8 in 256 threads).
-constexpr int kErTX = 64, kErTY = 16, kErTZ = 8, kErXT = 8, kErMaxL = 16;
-constexpr int kErThreads = (kErTX / kErXT) * kErTY * kErTZ;
-constexpr int kErBlocksPerSM = 1024 / kErThreads;            // 64 registers per thread
-constexpr int kErMaxRunsPerChunk = 2 * kErThreads;
-// shared-memory tile budget per block: kErBlocksPerSM blocks of tile + run table fit in 228 KB
-// (one 1024-thread block: 208 KB of tile + 16 KB of run descriptors)
-constexpr size_t kErodeBudget = (kErThreads >= 1024 ? 208 : kErThreads >= 512 ? 104 : 50) * 1024;
-struct ErodeChunk {
-    int run0, run1;              // runs of this chunk, sorted by length
-    int lend[kErMaxL + 1];       // runs of length L are run0 + lend[L-1] .. run0 + lend[L] - 1
-    int txh, tyh, tzh;           // tile extents
-    int pitch_y, pitch_z;        // shared-memory row and plane pitch (floats)
-    int ox, oy, oz;              // tile origin = block output origin + (ox, oy, oz) in window index
-};
-struct Erode2Args {
-    const float *g;
-    long g_so;
-    int gpx, gpy;                // window pitch (x) and rows per z-plane
-    int wx, wy, wz;              // window extents
-    const ErodeChunk *chunks;
-    const int *chunk_start;      // n_orient + 1
-    const int2 *runs;            // (shared-memory offset, length)
-    int nx, ny, nz;
-    int orient_base, nb;
-    int ngroups;                 // orientation groups per tile (blockIdx.z = group * tiles_z + tile z)
-    float *f;
-};
-void launch_erode2(const Erode2Args &a, size_t smem, cudaStream_t s);
-int erode2_blocks_per_sm(size_t smem);
+// Tiled minimum over sharp points: erode.cuh.
 
 // Direct collision convolution on the tensor cores (direct_tc.cu).
 struct DirectArgs {

@@ -69,59 +69,14 @@ __global__ void scatter_tool_kernel(float *dst, int Px, int Py, int Pz, const ui
 
 // ---------------------------------------------------------------------------------------
 // Near-threshold re-check: g(t) = sum_{v in RT} rho_O(t + v) by a compensated FP32 sum
-// (Neumaier), compared with theta in FP64. One warp per flagged translation.
+// (Neumaier), compared with theta in FP64 (recheck_blocks_kernel below: one block per flagged
+// translation).
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
     s = a + b;
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
-}
-
-__global__ void recheck_kernel(RecheckArgs a)
-{
-    const int n = min(*a.count, a.cap);
-    const int lane = threadIdx.x & 31;
-    const long nw = ((long)gridDim.x * blockDim.x) >> 5;
-    for (long e = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n; e += nw) {
-        const int2 fl = a.flags[e];
-        const int og = fl.x, lin = fl.y;
-        const int i = lin % a.wx, y = (lin / a.wx) % a.wy, z = lin / (a.wx * a.wy);
-        const int tx = i - a.kx, ty = y - a.ky, tz = z - a.kz;
-        float s = 0.f, c = 0.f;
-        for (int m = a.rt_start[og] + lane; m < a.rt_start[og + 1]; m += 32) {
-            const uint32_t p = a.rt_off[m];
-            const int x = tx + (int)(p & 1023u) - 512;
-            const int yy = ty + (int)((p >> 10) & 1023u) - 512;
-            const int zz = tz + (int)((p >> 20) & 1023u) - 512;
-            if (x < 0 || yy < 0 || zz < 0 || x >= a.nx || yy >= a.ny || zz >= a.nz) continue;
-            const long idx = ((long)zz * a.ny + yy) * a.nx + x;
-            float r = a.rho[idx];
-            if (a.fix && a.fix[idx]) r = fminf(1.f, r + 1.f);
-            float t, err;
-            two_sum(s, r, t, err);
-            s = t;
-            c += err;
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float s2 = __shfl_down_sync(0xffffffffu, s, off);
-            const float c2 = __shfl_down_sync(0xffffffffu, c, off);
-            float t, err;
-            two_sum(s, s2, t, err);
-            s = t;
-            c = c + c2 + err;
-        }
-        if (lane == 0) {
-            const double tot = (double)s + (double)c;
-            const long slot = og - a.orient_base;
-            a.g[slot * a.g_so + (long)z * a.g_sz + (long)y * a.g_sy + i] = (float)tot;
-            uint32_t *w = a.bits + slot * a.b_so + (long)z * a.b_sz + (long)y * a.b_sy + (i >> 5);
-            const uint32_t bit = 1u << (i & 31);
-            if (tot <= a.theta) atomicOr(w, bit);
-            else atomicAnd(w, ~bit);
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -342,11 +297,6 @@ void launch_scatter_tool(float *dst, int Px, int Py, int Pz, const uint32_t *off
                          cudaStream_t s)
 {
     scatter_tool_kernel<<<blocks_for(n), kThreads, 0, s>>>(dst, Px, Py, Pz, off, n, kx, ky, kz);
-}
-
-void launch_recheck(const RecheckArgs &a, cudaStream_t s)
-{
-    recheck_kernel<<<152 * 8, kThreads, 0, s>>>(a);
 }
 
 void launch_sweep_levels(const SweepLevelsArgs &a, cudaStream_t s)
