@@ -433,6 +433,26 @@ def test_fused_yx_pass_equals_separate_passes():
         assert "fft_yx_inv_threshold" in _kernels_run(a["imf"], d)
         kb = _kernels_run(b["imf"], d)
         assert "fft_yx_inv_threshold" not in kb and "fft_y_inv" in kb
+    # odd window extents and another split of the planes
+    d = _small3d(seed=9, n=(61, 23, 50), n_orient=5)
+    a = run_gpu(d, orient_batch=5, accessible_by_sweep=True)
+    b = run_gpu(d, orient_batch=5, accessible_by_sweep=True, separate_yx_passes=True)
+    for k in ("f", "fbar", "secluded", "accessible"):
+        assert np.array_equal(a[k], b[k]), k
     d = synth.config_beams(200, 12, 3)
     a = run_gpu(d, orient_batch=3)
     assert "fft_yx_inv_threshold" not in _kernels_run(a["imf"], d)
+
+def test_big_factor_axis_pass_matches_oracle():
+    """A grid whose y axis pads above 256: the y passes run the two-pass FFT with a factor above
+    16 (the 32-slot axis kernel); full parity against the oracle, both accessible routes."""
+    rho = synth.beam_density((24, 262, 6), n_beams=6, seed=2)
+    fix = synth.slab_fixture(rho.shape, 1, axis="z")
+    d = synth.Design(rho, fix, [synth.cylinder_tool(1, 4, 2, 3, synth.fibonacci_quats(3))])
+    ref = oracle.imf(d)
+    for kw in ({}, {"accessible_by_sweep": True}):
+        got = run_gpu(d, orient_batch=2, **kw)
+        assert got["imf"].tool_info(0).P[1] > 256
+        check_against_oracle(d, got, ref)
+    # the radix-stage kernels give the same classification and the IMF within the contract
+    check_against_oracle(d, run_gpu(d, orient_batch=2, fft_stages_only=True), ref)
