@@ -536,6 +536,25 @@ def run_ours(args):
     acc_mismatch = sum(int(a_np[z, y, x] != av) for (x, y, z), fv, av in zip(pts, fo, Ao)
                        if om0[z, y, x] and abs(fv - theta) > 1e-3 * theta / 0.01)
 
+    # stated IMF error on seeded sub-blocks (the whole design as obstacle, FP64 oracle)
+    nsub = args.error_subblocks if args.error_subblocks >= 0 else (8 if args.workload == "beams256" else 0)
+    sub = None
+    if nsub:
+        E = min(args.error_subblock_ext, *shape)
+        serr, smis, t0 = 0.0, 0, time.perf_counter()
+        for seed in range(1, nsub + 1):
+            r = np.random.default_rng(seed)
+            x0 = [int(r.integers(0, shape[2] - E + 1)), int(r.integers(0, shape[1] - E + 1)),
+                  int(r.integers(0, shape[0] - E + 1))]
+            fo_b, Ao_b = oracle.imf_subblock(d, x0, (E, E, E))
+            sl = (slice(x0[2], x0[2] + E), slice(x0[1], x0[1] + E), slice(x0[0], x0[0] + E))
+            om = om0[sl]
+            serr = max(serr, float(np.max(np.abs(f[sl] - fo_b)[om], initial=0.0)) / max(M, 1e-30))
+            clear = om & (np.abs(fo_b - theta) > 1e-3 * theta / 0.01)
+            smis += int(np.sum((a_np[sl] != Ao_b) & clear))
+        sub = {"blocks": nsub, "ext": [E, E, E], "seeds": list(range(1, nsub + 1)), "max_abs_over_max_f": serr,
+               "accessible_mismatches": smis, "oracle_s": round(time.perf_counter() - t0, 1)}
+
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         u, dt, x0, ext = run_cpu_oracle_sample(d, args.cpu_block)
@@ -556,7 +575,7 @@ def run_ours(args):
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)), "calls": len(lat)},
            "variants": variant,
            "imf_error": {"max_abs_over_max_f": err, "points": len(pts), "vs": "FP64 oracle point queries",
-                         "accessible_mismatches": acc_mismatch},
+                         "accessible_mismatches": acc_mismatch, "subblocks": sub},
            "near_threshold_rechecked": int(flagged),
            "roofline": roof, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": int(launches), "clocks": clk.summary()}
@@ -577,6 +596,9 @@ def main():
     ap.add_argument("--cpu-block", type=int, default=24)
     ap.add_argument("--error-points", type=int, default=6)
     ap.add_argument("--latency-calls", type=int, default=200, help="calls behind the p50 / p99 latency (>= 200)")
+    ap.add_argument("--error-subblocks", type=int, default=-1,
+                    help="seeded cubic sub-blocks checked against the FP64 oracle (-1: 8 for beams256, else 0)")
+    ap.add_argument("--error-subblock-ext", type=int, default=32)
     ap.add_argument("--orient-batch", type=int, default=0, help="orientations per device batch (0: library default)")
     ap.add_argument("--erode-groups", type=int, default=0,
                     help="orientation groups per tile of the minimum over sharp points (0: library default)")
