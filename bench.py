@@ -165,9 +165,11 @@ def algorithmic_bytes(kernel, info, shape, nb, bits=True):
     return None
 
 
-def traffic_record(kernel, workload):
+def traffic_record(kernel, workload, orient_per_launch=None):
     """dram bytes per launch of `kernel` from the committed ncu summary, if it was captured on
-    this workload and the kernel source is unchanged since the capture (else None)."""
+    this workload and the kernel source is unchanged since the capture (else None). A record
+    taken at another number of orientations per launch is scaled by the ratio (the kernel's
+    traffic is its per-orientation g reads)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -185,7 +187,11 @@ def traffic_record(kernel, workload):
         hsh.update(open(path, "rb").read())
     if hsh.hexdigest()[:16] != rec.get("source_sha256_16"):
         return None
-    return rec.get("bytes_per_launch")
+    b = rec.get("bytes_per_launch")
+    o = rec.get("orientations_per_launch")
+    if b is not None and o and orient_per_launch and orient_per_launch != o:
+        b = b * orient_per_launch / o
+    return b
 
 
 def run_cpu_oracle_sample(d, block, seed=0):
@@ -465,7 +471,7 @@ def run_ours(args):
         peak = 152 * 128 * smax * 1e6 / 1e12
         ach = comps / avg_s / 1e12
         roof = {"kernel": dname, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tcomparisons/s",
-                "frac": ach / peak, "traffic": traffic_record(dname, args.workload),
+                "frac": ach / peak, "traffic": traffic_record(dname, args.workload, n_orient * args.steps / dcnt),
                 "peak_source": f"152 SMs x 128 lanes x {smax:.0f} MHz (unit counts and clock)",
                 "algorithmic_comparisons_per_launch": comps, "avg_launch_ms": dms / dcnt,
                 "note": "outputs already at 0 skip later orientations; they count as done"}

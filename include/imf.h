@@ -69,7 +69,8 @@ typedef struct {
     int precision;           /* IMF_AUTO | IMF_FP32_FFT | IMF_BF16_DIRECT (collision path)     */
     int recheck;             /* 1: re-check translations with |g - theta| <= band exactly      */
     double recheck_band;     /* band half-width in voxel volumes; <= 0 picks a default         */
-    int orient_batch;        /* orientations per batch of device work; 0 = 16 (fewer if budget) */
+    int orient_batch;        /* orientations per batch of device work; 0 = 64 (fewer if the
+                                HBM budget needs it)                                           */
     size_t hbm_budget_bytes; /* cap on library-owned device memory; 0 = no cap (App. B)        */
     int erode_groups;        /* orientation groups per tile of the minimum over sharp points
                                 (work-unit granularity only; the result does not depend on it);

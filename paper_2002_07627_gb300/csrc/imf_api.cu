@@ -511,7 +511,10 @@ imf_status ensure_work(imf_handle h)
     if (rs > h->rho_spec_n) { dfree(h, h->rho_spec, h->rho_spec_n); TRY(dalloc(h, &h->rho_spec, rs)); h->rho_spec_n = rs; }
     if (x1 > h->X1_n) { dfree(h, h->X1, h->X1_n); TRY(dalloc(h, &h->X1, x1)); h->X1_n = x1; }
     if (x2 > h->X2_n) { dfree(h, h->X2, h->X2_n); TRY(dalloc(h, &h->X2, x2)); h->X2_n = x2; }
-    int want = op.orient_batch > 0 ? op.orient_batch : 16;
+    // default batch: 64 orientations (larger batches prune more in the minimum and the sweep,
+    // since outputs that reach 0 skip the rest of their orientation group, and leave fewer
+    // partial waves; 128^3 x 64: 5.9 ms per step against 6.3 with 16)
+    int want = op.orient_batch > 0 ? op.orient_batch : 64;
     want = std::max(std::min(want, maxo), min_slots);
     // per orientation slot: Y1, Y2, g, free bits and its share of the near-threshold list
     const size_t per_slot = y1 * 8 + y2 * 8 + gn * 4 + bn * 4 * kSweepLevels + (gn / 32 + 1) * sizeof(int2);
@@ -1251,10 +1254,10 @@ imf_status imf_autotune(imf_handle h, const float *rho_omega, const uint8_t *fix
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     float best_ms = 1e30f;
-    int best_nb = h->opt.orient_batch > 0 ? h->opt.orient_batch : 16;
-    const int cands[5] = {4, 8, 16, 32, 64};
+    int best_nb = h->opt.orient_batch > 0 ? h->opt.orient_batch : 64;
+    const int cands[6] = {4, 8, 16, 32, 64, 128};
     imf_status st = IMF_OK;
-    for (int c = 0; c < 5 && st == IMF_OK; ++c) {
+    for (int c = 0; c < 6 && st == IMF_OK; ++c) {
         const int nb = cands[c];
         if (nb > 4 && nb / 2 >= maxo) break;      // larger batches change nothing
         h->opt.orient_batch = nb;
