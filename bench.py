@@ -283,7 +283,8 @@ def run_batch(args):
                       "form": f"resident handles, autotuned orientation batch, CUDA graphs, {args.streams} streams",
                       "autotuned_batches": chosen},
            "plain": {"value": units / tp, "ms_per_pass": tp * 1e3,
-                     "form": "one design at a time on one stream, default options, no graphs"},
+                     "form": "one design at a time on one stream, default options, no graphs, the batched "
+                             "form's memory cap per handle"},
            "speedup_vs_plain": tp / tb}
     print(json.dumps(out), flush=True)
     return 0

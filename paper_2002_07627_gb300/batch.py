@@ -18,8 +18,9 @@ import numpy as np
 from . import binding
 
 
-def spectra_bytes_estimate(design, Pmargin=1.0) -> int:
-    """Rough device footprint of one design (tool spectra + work buffers), for admission."""
+def spectra_bytes_estimate(design, Pmargin=1.0, orient_batch: int = 16) -> int:
+    """Rough device footprint of one design (tool spectra + work buffers for `orient_batch`
+    orientation slots), for admission."""
     nz, ny, nx = design.rho.shape
     tot = 0
     for t in design.tools:
@@ -30,7 +31,7 @@ def spectra_bytes_estimate(design, Pmargin=1.0) -> int:
         tot += int(len(t.quats) * P[2] * P[1] * half * 8)
         win = [n + ext for n in (nx, ny, nz)]
         slot = win[2] * P[1] * half * 8 + win[2] * win[1] * half * 8 + win[0] * win[1] * win[2] * 4.2
-        tot += int(min(16, len(t.quats)) * slot + 2 * P[0] * P[1] * P[2] * 4)
+        tot += int(min(orient_batch, len(t.quats)) * slot + 2 * P[0] * P[1] * P[2] * 4)
     return tot
 
 
@@ -107,14 +108,15 @@ class BatchRunner:
         self.entries = []
 
 
-def run_plain(designs, reps: int = 1, device: int = 0):
-    """The plain form: one design at a time on one stream, default options, no graphs.
-    Returns (seconds per pass, units per pass)."""
+def run_plain(designs, reps: int = 1, device: int = 0, work_budget: int = 2 << 30):
+    """The plain form: one design at a time on one stream, default options, no graphs; each
+    handle's device memory is capped like the batched form's (spectra + `work_budget` of work
+    buffers), since all handles stay resident. Returns (seconds per pass, units per pass)."""
     import torch
     dev = torch.device("cuda", device)
     items = []
     for d in designs:
-        imf = binding.Imf(d.rho.shape)
+        imf = binding.Imf(d.rho.shape, hbm_budget_bytes=int(spectra_bytes_estimate(d)) + work_budget)
         imf.set_tools(d.tools)
         rho = torch.from_numpy(np.ascontiguousarray(d.rho)).to(dev)
         fix = None if d.fixture is None else torch.from_numpy(np.ascontiguousarray(d.fixture)).to(dev)

@@ -226,22 +226,27 @@ class ImfServer:
 class GpuExecutor:
     """Runs requests through libimf on a pool of CUDA streams, one stream per slot."""
 
-    def __init__(self, slots: int, device: int = 0):
+    def __init__(self, slots: int, device: int = 0, orient_batch: int = 16):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
+        # orientations per device batch of every served handle; the admission footprint counts
+        # the work buffers of exactly that many slots
+        self.orient_batch = int(orient_batch)
 
     def footprint(self, spec: DesignSpec) -> int:
         from .batch import spectra_bytes_estimate
         from .synth import Design
-        return spectra_bytes_estimate(Design(np.zeros(spec.shape, np.float32), spec.fixture, spec.tools))
+        return spectra_bytes_estimate(Design(np.zeros(spec.shape, np.float32), spec.fixture, spec.tools),
+                                      orient_batch=self.orient_batch)
 
     def create(self, design_id, spec: DesignSpec):
         from . import binding
         torch = self.torch
         torch.cuda.set_device(self.dev)
-        imf = binding.Imf(spec.shape, lam=spec.lam, tau=spec.tau, theta_rel=spec.theta_rel)
+        imf = binding.Imf(spec.shape, lam=spec.lam, tau=spec.tau, theta_rel=spec.theta_rel,
+                          orient_batch=self.orient_batch)
         imf.set_tools(spec.tools)
         st = {"imf": imf,
               "rho": torch.empty(spec.shape, dtype=torch.float32, device=self.dev),
