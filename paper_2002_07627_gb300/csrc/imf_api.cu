@@ -996,11 +996,14 @@ imf_status tail_batch(imf_handle h, const Tool &t, const float *rho, const uint8
         a.wx = t.win[0]; a.wy = t.win[1]; a.wz = t.win[2];
         a.chunks = t.er_chunks; a.chunk_start = t.er_chunk_start; a.runs = t.er_runs;
         a.nx = op.nx; a.ny = op.ny; a.nz = op.nz; a.orient_base = o0; a.nb = nb; a.f = h->f;
-        // enough (tile, orientation group) units for about six waves of resident blocks
+        // (tile, orientation group) units: at least about twelve waves of resident blocks and
+        // at most 16 orientations per block (measured optimum: 8 groups of 8 orientations at
+        // 128^3 x 64, 4 groups of 16 at 256^3 with 64 orientations per launch)
         const long tiles = (long)((op.nx + kErTX - 1) / kErTX) * ((op.ny + kErTY - 1) / kErTY) *
                            ((op.nz + kErTZ - 1) / kErTZ);
         const long slots = (long)t.erode_bps * h->nsm;
-        int G = op.erode_groups > 0 ? op.erode_groups : (int)((6 * slots + tiles - 1) / tiles);
+        int G = op.erode_groups > 0 ? op.erode_groups
+                                    : (int)std::max((12 * slots + tiles - 1) / tiles, (long)(nb + 15) / 16);
         a.ngroups = std::max(1, std::min(G, nb));
         Launch L(h, KID_ERODE, s);
         launch_erode2(a, t.erode_smem, s);
