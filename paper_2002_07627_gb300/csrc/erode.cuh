@@ -10,8 +10,9 @@ namespace imf {
 // consecutive x per thread; 1024 threads, one block per SM); the sharp points of an
 // orientation are runs along x, grouped in dz-chunks whose g tile fits the shared-memory
 // budget. Larger blocks fill less halo per output and need fewer chunks per orientation
-// (64 x 16 x 8: 4.17 ms per 128^3 x 64 step against 4.77 ms for 64 x 8 x 8 in 512 threads
-// and 7.2 ms for 32 x 8 x 8 in 256 threads).
+// (measured on 128^3 x 64 with 16 orientations per launch: 64 x 16 x 8 outputs in 1024
+// threads 4.17 ms per step against 4.77 ms for 64 x 8 x 8 in 512 threads and 7.2 ms for
+// 32 x 8 x 8 in 256 threads).
 constexpr int kErTX = 64, kErTY = 16, kErTZ = 8, kErXT = 8, kErMaxL = 16;
 constexpr int kErThreads = (kErTX / kErXT) * kErTY * kErTZ;
 constexpr int kErBlocksPerSM = 1024 / kErThreads;            // 64 registers per thread
