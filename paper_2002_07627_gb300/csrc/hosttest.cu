@@ -1,6 +1,6 @@
 // Host-only exports that run the kernels' building blocks (fft.cuh, fft2.cuh, erode_plan.h,
-// sweep_bits.cuh) on the CPU, for the CPU unit tests. Not part of libimf and never loaded by the
-// product path.
+// fft_plan.h, sweep_bits.cuh) on the CPU, for the CPU unit tests. Not part of libimf and never
+// loaded by the product path.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -8,6 +8,7 @@
 #include "fft.cuh"
 #include "fft2.cuh"
 #include "erode_plan.h"
+#include "fft_plan.h"
 #include "sweep_bits.cuh"
 
 extern "C" int imf_host_fft(int L, int sign, const float *in, float *out)
@@ -127,4 +128,14 @@ extern "C" uint32_t imf_host_pack_flags(const uint8_t *bytes32)
     uint32_t g8[8];
     std::memcpy(g8, bytes32, sizeof g8);
     return imf::pack_flag_bytes(g8);
+}
+
+// The padded length the planner picks for a minimum length n with two-pass factors up to maxA,
+// and the split it then uses (A, B; 0 when the length runs the radix-stage kernels).
+extern "C" int imf_host_plan_length(int n, int maxA, int *A, int *B)
+{
+    const int L = imf::best_smooth(n, maxA);
+    *A = *B = 0;
+    if (!imf::fft2::choose_split(L, A, B, maxA)) *A = *B = 0;
+    return L;
 }

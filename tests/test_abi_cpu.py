@@ -245,3 +245,36 @@ def test_flag_bytes_pack_into_bits(lib):
         b = np.ascontiguousarray(b)
         want = sum(int(v & 1) << i for i, v in enumerate(b))
         assert L_.imf_host_pack_flags(b.ctypes.data) == want
+
+
+def _is_smooth(n):
+    for p in (2, 3, 5, 7):
+        while n % p == 0:
+            n //= p
+    return n == 1
+
+
+def test_planner_picks_smooth_two_pass_lengths_close_to_the_minimum(lib):
+    """The padded FFT length (the linear correlation needs any length >= the minimum): it is
+    2-3-5-7 smooth, at most 1/8 above the smallest smooth length, and a two-pass split is used
+    whenever a smooth length in that range has one (the cost model prefers them). Above 256 the
+    y and z passes (factors up to 24) find splits the x pass (factors up to 16) cannot."""
+    L_ = ctypes.CDLL(build.HOSTLIB)
+    L_.imf_host_plan_length.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]
+    A, B = ctypes.c_int(), ctypes.c_int()
+    sizes = (2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 18, 20, 21, 24)
+    for maxA in (16, 24):
+        ok_sizes = [s for s in sizes if s <= maxA]
+        splittable = {a * b for a in ok_sizes for b in ok_sizes if a >= b}
+        for n in range(4, 600):
+            L = L_.imf_host_plan_length(n, maxA, ctypes.byref(A), ctypes.byref(B))
+            n0 = next(m for m in range(n, 10 * n) if _is_smooth(m))
+            assert _is_smooth(L) and n <= L <= n0 + n0 // 8, (n, maxA, L)
+            if any(m in splittable for m in range(n0, n0 + n0 // 8 + 1) if _is_smooth(m)):
+                assert A.value * B.value == L and A.value >= B.value and A.value <= maxA, (n, maxA, L)
+    # the 256^3 workload's y axis: 294 needs a factor above 16
+    L = L_.imf_host_plan_length(294, 16, ctypes.byref(A), ctypes.byref(B))
+    assert A.value == 0
+    L = L_.imf_host_plan_length(294, 24, ctypes.byref(A), ctypes.byref(B))
+    assert A.value > 16 and A.value * B.value == L
