@@ -30,7 +30,9 @@ def spectra_bytes_estimate(design, Pmargin=1.0, orient_batch: int = 16) -> int:
         half = P[0] / 2 + 1
         tot += int(len(t.quats) * P[2] * P[1] * half * 8)
         win = [n + ext for n in (nx, ny, nz)]
-        slot = win[2] * P[1] * half * 8 + win[2] * win[1] * half * 8 + win[0] * win[1] * win[2] * 4.2
+        # per slot: the two complex intermediates, g (4 B) and the free bits with their four
+        # dilation levels (5 x 1/8 B) per translation
+        slot = win[2] * P[1] * half * 8 + win[2] * win[1] * half * 8 + win[0] * win[1] * win[2] * 4.7
         tot += int(min(orient_batch, len(t.quats)) * slot + 2 * P[0] * P[1] * P[2] * 4)
     return tot
 
