@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -87,7 +88,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # raw samples go to the system temporary directory; the JSON line carries their summary
+        self.path = os.path.join(tempfile.gettempdir(), f"imf_bench_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
