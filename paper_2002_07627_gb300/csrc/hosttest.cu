@@ -1,6 +1,6 @@
 // Host-only exports that run the kernels' building blocks (fft.cuh, fft2.cuh, erode_plan.h,
-// fft_plan.h, sweep_bits.cuh) on the CPU, for the CPU unit tests. Not part of libimf and never
-// loaded by the product path.
+// fft_plan.h, orient_order.h, sweep_bits.cuh) on the CPU, for the CPU unit tests. Not part of
+// libimf and never loaded by the product path.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -9,6 +9,7 @@
 #include "fft2.cuh"
 #include "erode_plan.h"
 #include "fft_plan.h"
+#include "orient_order.h"
 #include "sweep_bits.cuh"
 
 extern "C" int imf_host_fft(int L, int sign, const float *in, float *out)
@@ -138,4 +139,14 @@ extern "C" int imf_host_plan_length(int n, int maxA, int *A, int *B)
     *A = *B = 0;
     if (!imf::fft2::choose_split(L, A, B, maxA)) *A = *B = 0;
     return L;
+}
+
+// The internal orientation order for n rotations (row-major 3 x 3 each): the nearest-neighbour
+// chain, interleaved by spread_order when `spread` is set.
+extern "C" void imf_host_orient_order(const double *R, int n, int spread, int *out)
+{
+    std::vector<double> r(R, R + 9 * (size_t)n);
+    std::vector<int> o = imf::locality_order(r, n);
+    if (spread) o = imf::spread_order(o);
+    for (int i = 0; i < n; ++i) out[i] = o[i];
 }

@@ -26,6 +26,7 @@
 #include "imf_internal.cuh"
 #include "erode_plan.h"
 #include "fft_plan.h"
+#include "orient_order.h"
 
 using namespace imf;
 
@@ -316,48 +317,6 @@ void free_tool(imf_handle h, Tool &t)
     dfree(h, t.d_taps);
     dfree(h, t.d_bmat);
     t = Tool();
-}
-
-// Greedy nearest-neighbour chain over the rotations (Frobenius distance), so that consecutive
-// orientations, and therefore every group of the direct path, have overlapping supports.
-std::vector<int> locality_order(const std::vector<double> &R, int n)
-{
-    std::vector<int> order;
-    std::vector<char> used(n, 0);
-    int cur = 0;
-    for (int step = 0; step < n; ++step) {
-        order.push_back(cur);
-        used[cur] = 1;
-        int best = -1;
-        double bd = 1e300;
-        for (int j = 0; j < n; ++j) {
-            if (used[j]) continue;
-            double d = 0;
-            for (int e = 0; e < 9; ++e) d += (R[9 * cur + e] - R[9 * j + e]) * (R[9 * cur + e] - R[9 * j + e]);
-            if (d < bd) { bd = d; best = j; }
-        }
-        if (best < 0) break;
-        cur = best;
-    }
-    return order;
-}
-
-// Chain positions in the order of the base-2 radical inverse of their index (van der Corput):
-// every prefix of the result is spread evenly along the chain.
-std::vector<int> spread_order(const std::vector<int> &chain)
-{
-    const int n = (int)chain.size();
-    std::vector<std::pair<double, int>> key(n);
-    for (int i = 0; i < n; ++i) {
-        double v = 0, b = 0.5;
-        for (unsigned k = (unsigned)i; k; k >>= 1, b *= 0.5)
-            if (k & 1) v += b;
-        key[i] = {v, i};
-    }
-    std::sort(key.begin(), key.end());
-    std::vector<int> out(n);
-    for (int i = 0; i < n; ++i) out[i] = chain[key[i].second];
-    return out;
 }
 
 constexpr size_t kDirectSmemLimit = 220 * 1024;

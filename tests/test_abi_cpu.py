@@ -278,3 +278,46 @@ def test_planner_picks_smooth_two_pass_lengths_close_to_the_minimum(lib):
     assert A.value == 0
     L = L_.imf_host_plan_length(294, 24, ctypes.byref(A), ctypes.byref(B))
     assert A.value > 16 and A.value * B.value == L
+
+
+def _rotations(n, seed):
+    rng = np.random.default_rng(seed)
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    R = np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                  2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                  2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], axis=1)
+    return np.ascontiguousarray(R)
+
+
+def test_orientation_order_chain_and_interleave(lib):
+    """The internal orientation order: a greedy nearest-neighbour chain from the first rotation
+    (Frobenius distance; brute force here), and on the FFT path its interleave by the radical
+    inverse, which is a permutation of the chain whose every prefix of length 2^k takes one
+    chain position from each block of n / 2^k consecutive positions."""
+    L_ = ctypes.CDLL(build.HOSTLIB)
+    L_.imf_host_orient_order.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    for n, seed in ((1, 0), (7, 1), (64, 2), (100, 3)):
+        R = _rotations(n, seed)
+        chain = np.zeros(n, np.int32)
+        spread = np.zeros(n, np.int32)
+        L_.imf_host_orient_order(R.ctypes.data, n, 0, chain.ctypes.data)
+        L_.imf_host_orient_order(R.ctypes.data, n, 1, spread.ctypes.data)
+        # brute-force greedy chain
+        used, cur, want = np.zeros(n, bool), 0, []
+        for _ in range(n):
+            want.append(cur)
+            used[cur] = True
+            if used.all():
+                break
+            d = np.where(used, np.inf, ((R - R[cur]) ** 2).sum(1))
+            cur = int(np.argmin(d))
+        assert chain.tolist() == want
+        assert sorted(spread.tolist()) == list(range(n))
+        pos = {c: i for i, c in enumerate(chain.tolist())}
+        ranks = [pos[c] for c in spread.tolist()]
+        if n == 64:
+            for k in range(7):
+                m = 1 << k
+                assert sorted(r // (n // m) for r in ranks[:m]) == list(range(m)), k
