@@ -8,10 +8,13 @@ resampling and spectra (imf_set_tool) are per-tool-set setup and run before timi
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ...]
 
-Default workload: 3D beams 128^3, 40 beams (r 2-5), 6-voxel base-plate fixture, cylinder cutter
-r=3 L=20 with holder r=8 L=16, 64 Fibonacci-hemisphere orientations, FP32 FFT path with the
-near-threshold re-check. Under torchrun (N > 1) every rank runs its own design (weak scaling,
-no data-path collective); only the step timing is reduced (max over ranks).
+Default workload: 3D beams 256^3, 120 beams (r 2-5), base-plate fixture, cylinder cutter r=3
+L=20 with holder r=8 L=16, 128 Fibonacci-hemisphere orientations, FP32 FFT path with the
+near-threshold re-check; its IMF error is stated against the FP64 oracle on 8 seeded 32^3
+sub-blocks. The 128^3 x 64 workload (40 beams) is measured the same way in the same run and
+reported under `variants.beams128` (8 seeded 16^3 sub-blocks). Under torchrun (N > 1) every rank
+runs its own design (weak scaling, no data-path collective); only the step timing is reduced
+(max over ranks).
 
 Rank 0 prints one JSON line. `--impl reference` times the FP64 CPU oracle (the only other
 place this file runs it) on a bounded sample of the same workload.
@@ -350,6 +353,194 @@ def run_serve(args):
     return 0
 
 
+def kernel_rooflines(imf, info, shape, n_orient, steps, sweep_route, workload):
+    """Per-kernel times (CUDA events on the launching stream, accumulated by the library) and
+    one roofline entry per kernel class: algorithmic bytes (or comparisons) per launch over the
+    kernel's average launch time, against the measured HBM copy bandwidth (or the derived ALU
+    comparison rate for the minimum over sharp points)."""
+    kt = imf.kernel_times()
+    hbm, bf16, peak_src = measured_peaks()
+    smax = 2070.0
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        smax = float(json.load(open(pp)).get("sm_max_mhz", smax))
+    alu_peak = 152 * 128 * smax * 1e6 / 1e12
+    nz_, ny_, nx_ = shape
+    nb = max(1.0, n_orient * steps / max(1, kt.get("fft_z_inv_mul", (0, 1))[1]))
+    entries = []
+    for name, (ms, cnt) in sorted(kt.items(), key=lambda kv: -kv[1][0]):
+        avg_s = ms / cnt * 1e-3
+        e = {"kernel": name, "ms_per_step": ms / steps, "launches_per_step": cnt / steps, "avg_launch_ms": ms / cnt}
+        if name == "erode_min":
+            # minimum over sharp points: the definition compares |sharp_R| candidates per design
+            # voxel and orientation; peak = 152 SMs x 128 FP32 lanes x max SM clock (one
+            # comparison per lane per clock; a three-input min counts as two)
+            comps = float(nx_ * ny_ * nz_) * info.n_sharp / max(1, cnt / steps)
+            ach = comps / avg_s / 1e12
+            e.update({"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tcomparisons/s",
+                      "frac": ach / alu_peak,
+                      "traffic": traffic_record(name, workload, n_orient * steps / cnt),
+                      "peak_source": f"152 SMs x 128 lanes x {smax:.0f} MHz (unit counts and clock)",
+                      "algorithmic_comparisons_per_launch": comps,
+                      "note": "outputs already at 0 skip later orientations; they count as done"})
+        elif name == "direct_corr_tcgen05":
+            wx, wy, wz = info.win
+            flops = 2.0 * info.n_rt * wx * wy * wz / max(1, cnt / steps)
+            ach = flops / avg_s / 1e12
+            e.update({"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                      "traffic": traffic_record(name, workload), "peak_source": f"bf16 burst, {peak_src}",
+                      "algorithmic_flops_per_launch": flops})
+        else:
+            ab = algorithmic_bytes(name, info, shape, nb, bits=sweep_route)
+            if ab is not None:
+                ach = ab / avg_s / 1e9
+                e.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                          "traffic": traffic_record(name, workload), "peak_source": peak_src,
+                          "algorithmic_bytes_per_launch": ab})
+            else:
+                e.update({"bound": "latency", "note": "no fixed algorithmic byte count (work depends on the data)"})
+        entries.append(e)
+    return entries
+
+
+def error_check(d, f, a_np, n_points, nsub, ext):
+    """Stated IMF error of one result against the FP64 oracle: literal point queries (the
+    argmax of f on Omega_0 and random points) and `nsub` seeded cubic sub-blocks of edge `ext`
+    computed in full by the oracle with the whole design as obstacle (seeds 1..nsub)."""
+    import oracle
+    shape = d.rho.shape
+    rng = np.random.default_rng(1)
+    om0 = d.fixture == 0 if d.fixture is not None else np.ones(shape, bool)
+    pts = [np.array(np.unravel_index(np.argmax(np.where(om0, f, -1)), shape))[::-1]]
+    for _ in range(n_points - 1):
+        pts.append(np.array([rng.integers(0, shape[2]), rng.integers(0, shape[1]), rng.integers(0, shape[0])]))
+    fo, Ao = oracle.point_query(d.rho, d.fixture, d.tools, np.array(pts))
+    M = float(f[pts[0][2], pts[0][1], pts[0][0]])
+    err = max(abs(float(f[z, y, x]) - fv) for (x, y, z), fv in zip(pts, fo)) / max(M, 1e-30)
+    theta = 0.01 * float(sum(((t.holder != 0) | (t.cutter != 0)).sum() for t in d.tools[:1]))
+    band = 1e-3 * theta / 0.01
+    acc_mismatch = sum(int(a_np[z, y, x] != av) for (x, y, z), fv, av in zip(pts, fo, Ao)
+                       if om0[z, y, x] and abs(fv - theta) > band)
+    sub = None
+    if nsub:
+        E = min(ext, *shape)
+        serr, smis, nclear, t0 = 0.0, 0, 0, time.perf_counter()
+        for seed in range(1, nsub + 1):
+            r = np.random.default_rng(seed)
+            x0 = [int(r.integers(0, shape[2] - E + 1)), int(r.integers(0, shape[1] - E + 1)),
+                  int(r.integers(0, shape[0] - E + 1))]
+            fo_b, Ao_b = oracle.imf_subblock(d, x0, (E, E, E))
+            sl = (slice(x0[2], x0[2] + E), slice(x0[1], x0[1] + E), slice(x0[0], x0[0] + E))
+            om = om0[sl]
+            serr = max(serr, float(np.max(np.abs(f[sl] - fo_b)[om], initial=0.0)) / max(M, 1e-30))
+            clear = om & (np.abs(fo_b - theta) > band)
+            nclear += int(clear.sum())
+            smis += int(np.sum((a_np[sl] != Ao_b) & clear))
+        sub = {"blocks": nsub, "ext": [E, E, E], "seeds": list(range(1, nsub + 1)), "max_abs_over_max_f": serr,
+               "accessible_mismatches": smis, "accessible_compared": nclear,
+               "oracle_s": round(time.perf_counter() - t0, 1)}
+    return {"max_abs_over_max_f": max(err, sub["max_abs_over_max_f"]) if sub else err,
+            "points": len(pts), "point_max_abs_over_max_f": err, "vs": "FP64 oracle (point queries and sub-blocks)",
+            "accessible_mismatches": acc_mismatch + (sub["accessible_mismatches"] if sub else 0), "subblocks": sub}
+
+
+class Workload:
+    """One design with its tools set on a library handle, plus the device buffers of a step."""
+
+    def __init__(self, name, args, dev, seed, by_sweep):
+        import torch
+        from paper_2002_07627_gb300 import binding
+        self.name = name
+        self.d = make_design(name, seed)
+        self.shape = self.d.rho.shape
+        self.nG = int(np.prod(self.shape))
+        self.n_orient = sum(len(t.quats) for t in self.d.tools)
+        self.prec = {"auto": 0, "fft": 1, "direct": 2}[args.precision]
+        self.by_sweep = by_sweep
+        self.args = args
+        self.dev = dev
+        self.imf = self.handle(by_sweep)
+        self.info = self.imf.tool_info(0)
+        self.rho = torch.from_numpy(self.d.rho).to(dev)
+        self.fix = torch.from_numpy(self.d.fixture).to(dev) if self.d.fixture is not None else None
+        if args.precision == "auto":
+            self.imf.autotune(self.rho, self.fix)
+        self.info = self.imf.tool_info(0)
+        self.fbar = torch.empty_like(self.rho)
+        self.sec = torch.empty(self.shape, dtype=torch.uint8, device=dev)
+        self.acc = torch.empty(self.shape, dtype=torch.uint8, device=dev)   # the accessible set, every step
+        self.sens0 = torch.from_numpy(np.random.default_rng(seed).normal(size=self.shape).astype(np.float32)).to(dev)
+        self.sens = self.sens0.clone()
+        self.sweep_route = by_sweep or len(self.d.tools) > 1 or any(getattr(t, "sharp", None) is not None
+                                                                    for t in self.d.tools)
+
+    def handle(self, by_sweep):
+        from paper_2002_07627_gb300 import binding
+        a = self.args
+        imf = binding.Imf(self.shape, orient_batch=a.orient_batch, precision=self.prec, erode_groups=a.erode_groups,
+                          fft_stages_only=a.fft_stages_only, accessible_by_sweep=by_sweep)
+        imf.set_tools(self.d.tools)
+        return imf
+
+    def step_fn(self, imf, stream):
+        def step():
+            imf.compute(self.rho, self.fix, self.fbar, self.sec, accessible=self.acc, stream=stream)
+            imf.penalize(self.sens, self.rho, self.fbar, self.sec, self.fix, w_acc=0.5, stream=stream)
+        return step
+
+    def timed_steps(self, k, fn, stream, flush):
+        import torch
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a, b in ev:
+            flush.zero_()
+            self.sens.copy_(self.sens0)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    def accessible_label(self, by_sweep):
+        return ("sweep of the free translations by the cutter (Eq. eq_conv_A)" if by_sweep or self.sweep_route
+                else "A = [f <= theta]: sharp points = the whole cutter (App. A)")
+
+    def close(self):
+        self.imf.close()
+
+
+def run_secondary(name, args, dev, stream, flush):
+    """A second workload measured the same way (steps, per-kernel rooflines, IMF error against
+    the oracle on seeded sub-blocks), reported beside the headline line."""
+    import torch
+    w = Workload(name, args, dev, 0, not args.accessible_from_imf)
+    step = w.step_fn(w.imf, stream)
+    for _ in range(args.warmup):
+        w.sens.copy_(w.sens0)
+        step()
+    w.imf.sync()
+    times = w.timed_steps(args.steps, step, stream, flush)
+    w.imf.sync()
+    ms = sum(times) / len(times)
+    w.imf.reset_kernel_times()
+    w.imf.set_profiling(True)
+    w.timed_steps(args.steps, step, stream, flush)
+    rl = kernel_rooflines(w.imf, w.info, w.shape, w.n_orient, args.steps, w.sweep_route, name)
+    w.imf.set_profiling(False)
+    raw = torch.empty_like(w.rho)
+    acc = torch.empty(w.shape, dtype=torch.uint8, device=dev)
+    w.imf.compute(w.rho, w.fix, w.fbar, w.sec, raw=raw, accessible=acc)
+    w.imf.sync()
+    err = error_check(w.d, raw.cpu().numpy(), acc.cpu().numpy(), args.error_points,
+                      args.secondary_subblocks, args.secondary_subblock_ext)
+    out = {"ms_per_step": ms, "value": w.nG * w.n_orient / (ms * 1e-3),
+           "config": dict(workload_config(name, w.d), fft_grid=list(w.info.P), translation_window=list(w.info.win),
+                          accessible=w.accessible_label(w.by_sweep)),
+           "imf_error": err, "roofline": next((e for e in rl if e["kernel"] == "erode_min"), rl[0]),
+           "roofline_all": rl}
+    w.close()
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_setup()
@@ -361,50 +552,18 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     from paper_2002_07627_gb300 import build, binding
     build.build()
-    d = make_design(args.workload, seed=rank)
-    shape = d.rho.shape
-    nG = int(np.prod(shape))
-    n_orient = sum(len(t.quats) for t in d.tools)
-    prec = {"auto": 0, "fft": 1, "direct": 2}[args.precision]
     # the timed step runs every step of the method as its own kernel, the sweep of the free
     # translations (Eq. eq_conv_A) included; --accessible-from-imf times the library's default
     # route instead (A read off the minimum where that is exact, App. A)
     by_sweep = not args.accessible_from_imf
-    imf = binding.Imf(shape, orient_batch=args.orient_batch, precision=prec, erode_groups=args.erode_groups,
-                      fft_stages_only=args.fft_stages_only, accessible_by_sweep=by_sweep)
-    imf.set_tools(d.tools)
-    info = imf.tool_info(0)
-    rho = torch.from_numpy(d.rho).to(dev)
-    fix = torch.from_numpy(d.fixture).to(dev) if d.fixture is not None else None
-    if args.precision == "auto":
-        imf.autotune(rho, fix)
-    info = imf.tool_info(0)
-    fbar = torch.empty_like(rho)
-    sec = torch.empty(shape, dtype=torch.uint8, device=dev)
-    acc_step = torch.empty(shape, dtype=torch.uint8, device=dev)   # the accessible set, every step
-    sens0 = torch.from_numpy(np.random.default_rng(rank).normal(size=shape).astype(np.float32)).to(dev)
-    sens = sens0.clone()
+    w = Workload(args.workload, args, dev, rank, by_sweep)
+    d, shape, nG, n_orient, imf, info = w.d, w.shape, w.nG, w.n_orient, w.imf, w.info
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
-
-    def step():
-        imf.compute(rho, fix, fbar, sec, accessible=acc_step, stream=stream)
-        imf.penalize(sens, rho, fbar, sec, fix, w_acc=0.5, stream=stream)
-
-    def timed_steps(k, fn=None):
-        fn = fn or step
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
-        for a, b in ev:
-            flush.zero_()
-            sens.copy_(sens0)
-            a.record(stream)
-            fn()
-            b.record(stream)
-        torch.cuda.synchronize()
-        return [a.elapsed_time(b) for a, b in ev]
+    step = w.step_fn(imf, stream)
 
     for _ in range(args.warmup):
-        sens.copy_(sens0)
+        w.sens.copy_(w.sens0)
         step()
     imf.sync()
     if ws > 1:
@@ -412,7 +571,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     l0 = imf.stats().launches
     with ClockSampler(dev.index) as clk:
-        times = timed_steps(args.steps)
+        times = w.timed_steps(args.steps, step, stream, flush)
     imf.sync()
     launches = imf.stats().launches - l0
     total_ms = reduce_max(sum(times), dev)
@@ -423,26 +582,20 @@ def run_ours(args):
     flagged = imf.stats().flagged
 
     # latency percentiles over at least 200 calls (L2 flushed before each), outside the timed region
-    lat = times if len(times) >= 200 else timed_steps(max(200, args.latency_calls))
+    lat = times if len(times) >= 200 else w.timed_steps(max(200, args.latency_calls), step, stream, flush)
 
     # the other route for the accessible set, on a second handle, timed the same way
-    alt = binding.Imf(shape, orient_batch=args.orient_batch, precision=prec, erode_groups=args.erode_groups,
-                      fft_stages_only=args.fft_stages_only, accessible_by_sweep=not by_sweep)
-    alt.set_tools(d.tools)
+    alt = w.handle(not by_sweep)
     if args.precision == "auto":
-        alt.autotune(rho, fix)
-
-    def alt_step():
-        alt.compute(rho, fix, fbar, sec, accessible=acc_step, stream=stream)
-        alt.penalize(sens, rho, fbar, sec, fix, w_acc=0.5, stream=stream)
-
+        alt.autotune(w.rho, w.fix)
+    alt_step = w.step_fn(alt, stream)
     for _ in range(args.warmup):
         alt_step()
     alt.sync()
-    alt_ms = reduce_max(sum(timed_steps(args.steps, alt_step)), dev) / args.steps
+    alt_ms = reduce_max(sum(w.timed_steps(args.steps, alt_step, stream, flush)), dev) / args.steps
     alt.sync()
     alt.close()
-    variant = {("accessible_from_imf" if by_sweep else "accessible_by_sweep"): {
+    variants = {("accessible_from_imf" if by_sweep else "accessible_by_sweep"): {
         "ms_per_step": alt_ms, "value": ws * nG * n_orient / (alt_ms * 1e-3),
         "accessible": ("A = [f <= theta] where exact (one tool, sharp points = the whole cutter), the library "
                        "default" if by_sweep else "sweep of the free translations (Eq. eq_conv_A)")}}
@@ -450,50 +603,12 @@ def run_ours(args):
     # per-kernel times with CUDA events on the launching stream (separate pass of K steps)
     imf.reset_kernel_times()
     imf.set_profiling(True)
-    timed_steps(args.steps)
-    kt = imf.kernel_times()
+    w.timed_steps(args.steps, step, stream, flush)
+    rl = kernel_rooflines(imf, info, shape, n_orient, args.steps, w.sweep_route, args.workload)
     imf.set_profiling(False)
-    dom = max(((k, v) for k, v in kt.items()), key=lambda kv: kv[1][0])
-    dname, (dms, dcnt) = dom
-    nb = max(1.0, n_orient * args.steps / max(1, kt.get("fft_z_inv_mul", (0, 1))[1]))
-    sweep_route = by_sweep or len(d.tools) > 1 or any(getattr(t, "sharp", None) is not None for t in d.tools)
-    abytes = algorithmic_bytes(dname, info, shape, nb, bits=sweep_route)
-    hbm, bf16, peak_src = measured_peaks()
-    roof = None
-    avg_s = dms / dcnt * 1e-3
-    if dname == "erode_min":
-        # minimum over sharp points: the definition compares |sharp_R| candidates per design voxel
-        # and orientation; peak = 152 SMs x 128 FP32 lanes x max SM clock (one comparison per
-        # lane per clock; a three-input min counts as two)
-        nz_, ny_, nx_ = shape
-        comps = float(nx_ * ny_ * nz_) * info.n_sharp / max(1, dcnt / args.steps)
-        smax = 2070.0
-        pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
-        if os.path.exists(pp):
-            smax = float(json.load(open(pp)).get("sm_max_mhz", smax))
-        peak = 152 * 128 * smax * 1e6 / 1e12
-        ach = comps / avg_s / 1e12
-        roof = {"kernel": dname, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tcomparisons/s",
-                "frac": ach / peak, "traffic": traffic_record(dname, args.workload, n_orient * args.steps / dcnt),
-                "peak_source": f"152 SMs x 128 lanes x {smax:.0f} MHz (unit counts and clock)",
-                "algorithmic_comparisons_per_launch": comps, "avg_launch_ms": dms / dcnt,
-                "note": "outputs already at 0 skip later orientations; they count as done"}
-    elif dname == "direct_corr_tcgen05":
-        # algorithmic work of the collision sums: |R T| multiply-adds per translation and
-        # orientation (the BF16 hi / lo split and the dense union-tap GEMM are implementation)
-        wx, wy, wz = info.win
-        flops = 2.0 * info.n_rt * wx * wy * wz / max(1, dcnt / args.steps)
-        ach = flops / avg_s / 1e12
-        roof = {"kernel": dname, "bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
-                "frac": ach / bf16, "traffic": traffic_record(dname, args.workload), "peak_source": f"bf16 burst, {peak_src}",
-                "algorithmic_flops_per_launch": flops, "avg_launch_ms": dms / dcnt}
-    elif abytes is not None:
-        ach = abytes / avg_s / 1e9
-        roof = {"kernel": dname, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": traffic_record(dname, args.workload), "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": dms / dcnt}
-    kernel_share = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
-                    for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}
+    roof = dict(rl[0])
+    kernel_share = {e["kernel"]: {"ms_per_step": e["ms_per_step"], "launches_per_step": e["launches_per_step"]}
+                    for e in rl}
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
@@ -525,50 +640,26 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return 0
 
-    # stated IMF error: oracle point queries at the argmax and at random points
-    import oracle
-    raw = torch.empty_like(rho)
+    # stated IMF error against the FP64 oracle: point queries and seeded sub-blocks
+    raw = torch.empty_like(w.rho)
     acc = torch.empty(shape, dtype=torch.uint8, device=dev)
-    imf.compute(rho, fix, fbar, sec, raw=raw, accessible=acc)
+    imf.compute(w.rho, w.fix, w.fbar, w.sec, raw=raw, accessible=acc)
     imf.sync()
-    f = raw.cpu().numpy()
-    rng = np.random.default_rng(1)
-    om0 = d.fixture == 0 if d.fixture is not None else np.ones(shape, bool)
-    pts = [np.array(np.unravel_index(np.argmax(np.where(om0, f, -1)), shape))[::-1]]
-    for _ in range(args.error_points - 1):
-        pts.append(np.array([rng.integers(0, shape[2]), rng.integers(0, shape[1]), rng.integers(0, shape[0])]))
-    fo, Ao = oracle.point_query(d.rho, d.fixture, d.tools, np.array(pts))
-    M = float(f[pts[0][2], pts[0][1], pts[0][0]])
-    err = max(abs(float(f[z, y, x]) - fv) for (x, y, z), fv in zip(pts, fo)) / max(M, 1e-30)
-    a_np = acc.cpu().numpy()
-    theta = 0.01 * float(sum(((t.holder != 0) | (t.cutter != 0)).sum() for t in d.tools[:1]))
-    acc_mismatch = sum(int(a_np[z, y, x] != av) for (x, y, z), fv, av in zip(pts, fo, Ao)
-                       if om0[z, y, x] and abs(fv - theta) > 1e-3 * theta / 0.01)
+    nsub = args.error_subblocks if args.error_subblocks >= 0 else (8 if args.workload.startswith("beams") else 0)
+    ext = args.error_subblock_ext if args.error_subblock_ext > 0 else (32 if args.workload == "beams256" else 16)
+    err = error_check(d, raw.cpu().numpy(), acc.cpu().numpy(), args.error_points, nsub, ext)
+    path_name = {1: "fp32_fft", 2: "bf16_direct_tcgen05"}[imf.tool_info(0).path]
+    w.close()
 
-    # stated IMF error on seeded sub-blocks (the whole design as obstacle, FP64 oracle)
-    nsub = args.error_subblocks if args.error_subblocks >= 0 else (8 if args.workload == "beams256" else 0)
-    sub = None
-    if nsub:
-        E = min(args.error_subblock_ext, *shape)
-        serr, smis, t0 = 0.0, 0, time.perf_counter()
-        for seed in range(1, nsub + 1):
-            r = np.random.default_rng(seed)
-            x0 = [int(r.integers(0, shape[2] - E + 1)), int(r.integers(0, shape[1] - E + 1)),
-                  int(r.integers(0, shape[0] - E + 1))]
-            fo_b, Ao_b = oracle.imf_subblock(d, x0, (E, E, E))
-            sl = (slice(x0[2], x0[2] + E), slice(x0[1], x0[1] + E), slice(x0[0], x0[0] + E))
-            om = om0[sl]
-            serr = max(serr, float(np.max(np.abs(f[sl] - fo_b)[om], initial=0.0)) / max(M, 1e-30))
-            clear = om & (np.abs(fo_b - theta) > 1e-3 * theta / 0.01)
-            smis += int(np.sum((a_np[sl] != Ao_b) & clear))
-        sub = {"blocks": nsub, "ext": [E, E, E], "seeds": list(range(1, nsub + 1)), "max_abs_over_max_f": serr,
-               "accessible_mismatches": smis, "oracle_s": round(time.perf_counter() - t0, 1)}
+    # the 128^3 x 64 plain workload beside the headline (its own steps, rooflines and error)
+    if args.secondary and args.secondary != args.workload and ws == 1:
+        variants[args.secondary] = run_secondary(args.secondary, args, dev, stream, flush)
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        u, dt, x0, ext = run_cpu_oracle_sample(d, args.cpu_block)
+        u, dt, x0, ext_ = run_cpu_oracle_sample(d, args.cpu_block)
         cpu = {"value": u / dt, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
-               "sample": f"FP64 oracle on a {ext[0]}x{ext[1]}x{ext[2]} sub-block at {x0} x {n_orient} orientations "
+               "sample": f"FP64 oracle on a {ext_[0]}x{ext_[1]}x{ext_[2]} sub-block at {x0} x {n_orient} orientations "
                          f"({dt:.1f} s)"}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -576,17 +667,13 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": dict(workload_config(args.workload, d), l2="256 MiB buffer written between timed steps",
                           fft_grid=list(info.P), translation_window=list(info.win),
-                          collision_path={1: "fp32_fft", 2: "bf16_direct_tcgen05"}[imf.tool_info(0).path],
-                          accessible=("sweep of the free translations by the cutter (Eq. eq_conv_A)"
-                                      if by_sweep or len(d.tools) > 1
-                                      or any(getattr(t, "sharp", None) is not None for t in d.tools)
-                                      else "A = [f <= theta]: sharp points = the whole cutter (App. A)")),
+                          collision_path=path_name,
+                          accessible=w.accessible_label(by_sweep)),
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)), "calls": len(lat)},
-           "variants": variant,
-           "imf_error": {"max_abs_over_max_f": err, "points": len(pts), "vs": "FP64 oracle point queries",
-                         "accessible_mismatches": acc_mismatch, "subblocks": sub},
+           "variants": variants,
+           "imf_error": err,
            "near_threshold_rechecked": int(flagged),
-           "roofline": roof, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
+           "roofline": roof, "roofline_all": rl, "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": int(launches), "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
     if ws > 1:
@@ -600,14 +687,19 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="beams128", choices=sorted(WORKLOADS) + ["planar64", "batch64", "serve"])
+    ap.add_argument("--workload", default="beams256", choices=sorted(WORKLOADS) + ["planar64", "batch64", "serve"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-block", type=int, default=24)
     ap.add_argument("--error-points", type=int, default=6)
     ap.add_argument("--latency-calls", type=int, default=200, help="calls behind the p50 / p99 latency (>= 200)")
     ap.add_argument("--error-subblocks", type=int, default=-1,
-                    help="seeded cubic sub-blocks checked against the FP64 oracle (-1: 8 for beams256, else 0)")
-    ap.add_argument("--error-subblock-ext", type=int, default=32)
+                    help="seeded cubic sub-blocks checked against the FP64 oracle (-1: 8 for the 3D beams workloads)")
+    ap.add_argument("--error-subblock-ext", type=int, default=0,
+                    help="edge of those sub-blocks (0: 32 at 256^3, else 16)")
+    ap.add_argument("--secondary", default="beams128", choices=sorted(WORKLOADS) + ["planar64", ""],
+                    help="second workload measured beside the headline and reported under variants ('' = none)")
+    ap.add_argument("--secondary-subblocks", type=int, default=8)
+    ap.add_argument("--secondary-subblock-ext", type=int, default=16)
     ap.add_argument("--orient-batch", type=int, default=0, help="orientations per device batch (0: library default)")
     ap.add_argument("--erode-groups", type=int, default=0,
                     help="orientation groups per tile of the minimum over sharp points (0: library default)")

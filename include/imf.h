@@ -86,6 +86,10 @@ typedef struct {
                                 output in HBM; 0 = one kernel per z-plane that keeps the plane
                                 in shared memory, wherever it fits (same arithmetic, same
                                 results)                                                       */
+    int plan_only;           /* 1: imf_set_tool resamples the tool and plans every size on the
+                                host and touches no device (no allocation, no kernel); the
+                                handle then answers imf_get_tool_info and imf_footprint but
+                                refuses imf_compute (admission planning); 0 = default          */
 } imf_options;
 
 /* Fill *opt with the defaults above (grid 0x0x0, which imf_create rejects). */
@@ -157,7 +161,11 @@ imf_status imf_penalize_sensitivity(imf_handle h, float *sens, const float *rho_
  *   sens, rho_omega, imf_bar, secluded, fixture (or NULL): DEVICE arrays of n elements, as in
  *   imf_penalize_sensitivity; tau is the density threshold (0.5 in the paper).
  *   The first call on a device looks up the scratch address on that device (the device that
- *   is current); make that first call before any stream capture.
+ *   is current). With lazy module loading (the CUDA default) that lookup may load the
+ *   library's device code, which allocates the scratch array and can synchronize the device:
+ *   make the first call on each device during set-up, before any stream capture and outside
+ *   any section that must not allocate. The address is cached for the life of the device's
+ *   context; after a cudaDeviceReset this entry point must not be called again in the process.
  *   Every call shares the scratch array: calls that overlap on the GPU (other streams or
  *   other host threads) race and must not be issued. Asynchronous on cuda_stream.
  * Errors: IMF_ERR_INVALID_ARG (NULL array, n < 1 or n above the limit, w_acc outside [0, 1),
@@ -240,15 +248,41 @@ imf_status imf_get_offsets(imf_handle h, int tool_id, int orient, int which, int
 imf_status imf_set_debug(imf_handle h, int keep_last_g);
 imf_status imf_get_last_g(imf_handle h, int slot, float *g_out, long cap, int *orient_out);
 
+/* Copy the free bits of slot `slot` of the last batch into a HOST buffer, for tests: word
+ * [z][y][w] (z < win[2], y < win[1], w < (win[0] + 31) / 32 + 2), bit i & 31 of word i >> 5 is
+ * [g(t) <= theta] for the translation at window index (i, y, z), after the near-threshold
+ * re-check (Eq. eq_conv_D). Available when imf_set_debug(h, 1) was set before the compute (or on
+ * the sweep route). `orient_out` receives the caller's orientation index. Synchronous.
+ * Errors: IMF_ERR_INVALID_ARG (bad slot, capacity), IMF_ERR_NOT_READY (bits not kept). */
+imf_status imf_get_last_bits(imf_handle h, int slot, uint32_t *bits_out, long cap, int *orient_out);
+
 typedef struct {
     long launches;           /* kernels launched by the library since creation             */
     long computes;           /* imf_compute calls                                          */
     long flagged;            /* near-threshold translations re-checked (last compute)      */
     long flagged_total;      /* since creation                                             */
     int n_kernels;           /* entries filled in the per-kernel timing table              */
+    size_t owned_bytes;      /* device bytes the handle owns now                           */
 } imf_stats;
 
 imf_status imf_get_stats(imf_handle h, imf_stats *out);
+
+/* Device footprint of a handle, from the plan of its tools (the sizes App. B's memory-budgeted
+ * batching needs before committing memory). Works on a plan_only handle, which holds nothing.
+ *   slots : orientation slots of the work buffers (orientations per device batch); 0 = what
+ *           the first imf_compute without an HBM budget uses (orient_batch, 64 by default,
+ *           capped by the orientation count).
+ * Fills resident (tool spectra and tables of every set tool), work (the work buffers the first
+ * imf_compute allocates with that many slots), setup_peak (the largest footprint during the
+ * imf_set_tool calls, transient rotation and spectrum buffers included) and total =
+ * max(resident + work, setup_peak): the most the handle holds through its first compute, not
+ * counting imf_compute_host's staging buffers. Synchronous, host only.
+ * Errors: IMF_ERR_INVALID_ARG (NULL, slots < 0), IMF_ERR_NOT_READY (no tool set). */
+typedef struct {
+    size_t resident, work, setup_peak, total;
+    int slots;
+} imf_footprint_info;
+imf_status imf_footprint(imf_handle h, int slots, imf_footprint_info *out);
 
 /* Per-kernel timing with CUDA events on the launching stream (off by default). When on,
  * every launch is bracketed by events; imf_get_kernel_times accumulates their durations. */

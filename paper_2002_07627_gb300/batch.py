@@ -18,23 +18,24 @@ import numpy as np
 from . import binding
 
 
-def spectra_bytes_estimate(design, Pmargin=1.0, orient_batch: int = 16) -> int:
-    """Rough device footprint of one design (tool spectra + work buffers for `orient_batch`
-    orientation slots), for admission."""
-    nz, ny, nx = design.rho.shape
-    tot = 0
-    for t in design.tools:
-        tz, ty, tx = t.cutter.shape
-        ext = int(np.ceil(np.sqrt(tx * tx + ty * ty + tz * tz))) + 2
-        P = [(n + ext) * Pmargin for n in (nx, ny, nz)]
-        half = P[0] / 2 + 1
-        tot += int(len(t.quats) * P[2] * P[1] * half * 8)
-        win = [n + ext for n in (nx, ny, nz)]
-        # per slot: the two complex intermediates, g (4 B) and the free bits with their four
-        # dilation levels (5 x 1/8 B) per translation
-        slot = win[2] * P[1] * half * 8 + win[2] * win[1] * half * 8 + win[0] * win[1] * win[2] * 4.7
-        tot += int(min(orient_batch, len(t.quats)) * slot + 2 * P[0] * P[1] * P[2] * 4)
-    return tot
+def planned_footprint(design, orient_batch: int = 0, slots: int = 0):
+    """Device footprint of one design from the library's own plan (imf_footprint on a plan_only
+    handle: the tool is resampled and every size planned on the host; nothing is allocated).
+    Returns the ImfFootprint (resident spectra and tables, work buffers for `slots` orientation
+    slots or the first compute's default, set-up peak, total)."""
+    imf = binding.Imf(design.rho.shape, orient_batch=orient_batch, plan_only=True)
+    try:
+        imf.set_tools(design.tools)
+        return imf.footprint(slots)
+    finally:
+        imf.close()
+
+
+def handle_budget(design, work_budget: int) -> int:
+    """HBM cap of one resident handle: its spectra and tables plus `work_budget` bytes of work
+    buffers, and never below what its set-up needs transiently."""
+    fp = planned_footprint(design, slots=1)
+    return int(max(fp.setup_peak, fp.resident + max(work_budget, fp.work)))
 
 
 @dataclass
@@ -60,7 +61,7 @@ class BatchRunner:
         self.entries = []
         for d in designs:
             # cap each design's device memory at its spectra plus `work_budget` of work buffers
-            imf = binding.Imf(d.rho.shape, hbm_budget_bytes=int(spectra_bytes_estimate(d)) + work_budget)
+            imf = binding.Imf(d.rho.shape, hbm_budget_bytes=handle_budget(d, work_budget))
             imf.set_tools(d.tools)
             rho = torch.from_numpy(np.ascontiguousarray(d.rho)).to(self.dev)
             fix = None if d.fixture is None else torch.from_numpy(np.ascontiguousarray(d.fixture)).to(self.dev)
@@ -118,7 +119,7 @@ def run_plain(designs, reps: int = 1, device: int = 0, work_budget: int = 2 << 3
     dev = torch.device("cuda", device)
     items = []
     for d in designs:
-        imf = binding.Imf(d.rho.shape, hbm_budget_bytes=int(spectra_bytes_estimate(d)) + work_budget)
+        imf = binding.Imf(d.rho.shape, hbm_budget_bytes=handle_budget(d, work_budget))
         imf.set_tools(d.tools)
         rho = torch.from_numpy(np.ascontiguousarray(d.rho)).to(dev)
         fix = None if d.fixture is None else torch.from_numpy(np.ascontiguousarray(d.fixture)).to(dev)

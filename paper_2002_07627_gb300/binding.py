@@ -24,7 +24,7 @@ EXPORTS = ["imf_default_options", "imf_create", "imf_set_tool", "imf_compute", "
            "imf_get_tool_info", "imf_get_offsets", "imf_set_debug", "imf_get_last_g", "imf_get_stats",
            "imf_set_profiling", "imf_get_kernel_time", "imf_reset_kernel_times",
            "imf_penalize_sensitivity_noalloc", "imf_capture_graph", "imf_launch_graph", "imf_autotune",
-           "imf_set_path", "imf_selftest_mma"]
+           "imf_set_path", "imf_selftest_mma", "imf_get_last_bits", "imf_footprint"]
 
 
 class ImfOptions(ctypes.Structure):
@@ -34,7 +34,7 @@ class ImfOptions(ctypes.Structure):
                 ("recheck_band", ctypes.c_double), ("orient_batch", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("erode_groups", ctypes.c_int),
                 ("fft_stages_only", ctypes.c_int), ("accessible_by_sweep", ctypes.c_int),
-                ("separate_yx_passes", ctypes.c_int)]
+                ("separate_yx_passes", ctypes.c_int), ("plan_only", ctypes.c_int)]
 
 
 class ImfToolInfo(ctypes.Structure):
@@ -46,7 +46,12 @@ class ImfToolInfo(ctypes.Structure):
 
 class ImfStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_long), ("computes", ctypes.c_long), ("flagged", ctypes.c_long),
-                ("flagged_total", ctypes.c_long), ("n_kernels", ctypes.c_int)]
+                ("flagged_total", ctypes.c_long), ("n_kernels", ctypes.c_int), ("owned_bytes", ctypes.c_size_t)]
+
+
+class ImfFootprint(ctypes.Structure):
+    _fields_ = [("resident", ctypes.c_size_t), ("work", ctypes.c_size_t), ("setup_peak", ctypes.c_size_t),
+                ("total", ctypes.c_size_t), ("slots", ctypes.c_int)]
 
 
 _lib = None
@@ -79,7 +84,9 @@ def load(path: str | None = None):
     L.imf_get_offsets.argtypes = [H, I, I, I, P, Lg, ctypes.POINTER(Lg)]
     L.imf_set_debug.argtypes = [H, I]
     L.imf_get_last_g.argtypes = [H, I, P, Lg, ctypes.POINTER(I)]
+    L.imf_get_last_bits.argtypes = [H, I, P, Lg, ctypes.POINTER(I)]
     L.imf_get_stats.argtypes = [H, ctypes.POINTER(ImfStats)]
+    L.imf_footprint.argtypes = [H, I, ctypes.POINTER(ImfFootprint)]
     L.imf_set_profiling.argtypes = [H, I]
     L.imf_get_kernel_time.argtypes = [H, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(D),
                                       ctypes.POINTER(Lg)]
@@ -155,7 +162,7 @@ class Imf:
 
     def __init__(self, shape_zyx, lam=0.01, tau=0.5, theta_rel=0.01, precision=IMF_AUTO, recheck=True,
                  recheck_band=0.0, orient_batch=0, hbm_budget_bytes=0, voxel=1.0, erode_groups=0, fft_stages_only=False,
-                 accessible_by_sweep=False, separate_yx_passes=False):
+                 accessible_by_sweep=False, separate_yx_passes=False, plan_only=False):
         self.lib = load()
         opt = ImfOptions()
         self.lib.imf_default_options(ctypes.byref(opt))
@@ -168,6 +175,7 @@ class Imf:
         opt.fft_stages_only = int(fft_stages_only)
         opt.accessible_by_sweep = int(accessible_by_sweep)
         opt.separate_yx_passes = int(separate_yx_passes)
+        opt.plan_only = int(plan_only)
         self.shape = (nz, ny, nx)
         self.opt = opt
         h = ctypes.c_void_p()
@@ -297,10 +305,33 @@ class Imf:
         self._check(self.lib.imf_get_last_g(self.h, slot, buf.ctypes.data, buf.size, ctypes.byref(o)))
         return o.value, buf.reshape(wz, wy, gpx)[:, :, :wx]
 
+    def set_debug(self, keep_last_g=True):
+        """Keep the last orientation batch's collision field and free bits (tests)."""
+        self._check(self.lib.imf_set_debug(self.h, int(keep_last_g)))
+
+    def last_bits(self, slot=0):
+        """(caller's orientation index, free flags [wz][wy][wx] as uint8) of a slot of the last
+        batch, unpacked from the library's bit words."""
+        info = self.tool_info(0)
+        o = ctypes.c_int()
+        wx, wy, wz = info.win
+        wpr = (wx + 31) // 32 + 2
+        buf = np.zeros(wz * wy * wpr, np.uint32)
+        self._check(self.lib.imf_get_last_bits(self.h, slot, buf.ctypes.data, buf.size, ctypes.byref(o)))
+        bits = np.unpackbits(buf.view(np.uint8).reshape(wz, wy, wpr * 4), axis=-1, bitorder="little")
+        return o.value, bits[:, :, :wx]
+
     def stats(self) -> ImfStats:
         s = ImfStats()
         self._check(self.lib.imf_get_stats(self.h, ctypes.byref(s)))
         return s
+
+    def footprint(self, slots=0) -> ImfFootprint:
+        """Planned device bytes of this handle (imf_footprint); `slots` orientation slots of work
+        buffers, 0 = the first compute's default."""
+        f = ImfFootprint()
+        self._check(self.lib.imf_footprint(self.h, int(slots), ctypes.byref(f)))
+        return f
 
     def set_profiling(self, on=True):
         self._check(self.lib.imf_set_profiling(self.h, int(on)))

@@ -79,6 +79,11 @@ struct Tool {
     uint16_t *d_bmat = nullptr;
     int dlo[3] = {0, 0, 0}, dP[3] = {1, 1, 1};
     double direct_macs = 0;              // tensor MACs per compute (both BF16 halves)
+    // device bytes of this tool: resident tables (offset lists, run descriptors, twiddles,
+    // direct-path taps) and the largest footprint of its imf_set_tool beyond what was owned
+    // before (transient rotation and spectrum buffers included)
+    size_t table_bytes = 0, setup_bytes = 0;
+    bool planned_only = false;           // sizes planned on the host, nothing on the device
 };
 
 struct ProfRec {
@@ -263,6 +268,38 @@ void quat_to_R(const double *q, double *R)
     R[8] = 1.0 - 2.0 * (x * x + y * y);
 }
 
+// Host copy of rotate_kernel's arithmetic for one orientation (the same FP64 operation order,
+// host code compiled without contraction), so the plan-only path resamples the tool on the CPU
+// with the same result as the device.
+void rotate_host(const uint8_t *T, const uint8_t *K, const uint8_t *S, int tx, int ty, int tz, const int *o,
+                 const double *R, const int *bx, uint8_t *oT, uint8_t *oK, uint8_t *oS)
+{
+    const long vol = (long)bx[3] * bx[4] * bx[5];
+    for (long idx = 0; idx < vol; ++idx) {
+        const int i = (int)(idx % bx[3]);
+        const int j = (int)((idx / bx[3]) % bx[4]);
+        const int k = (int)(idx / ((long)bx[3] * bx[4]));
+        const double v0 = bx[0] + i, v1 = bx[1] + j, v2 = bx[2] + k;
+        int u[3];
+        for (int c = 0; c < 3; ++c) {
+            const double a0 = R[c] * v0, a1 = R[3 + c] * v1, a2 = R[6 + c] * v2;
+            const double p = (a0 + a1) + a2;
+            u[c] = (int)std::floor(p + 0.5);
+        }
+        const int ax = o[0] + u[0], ay = o[1] + u[1], az = o[2] + u[2];
+        uint8_t t = 0, kk = 0, ss = 0;
+        if (ax >= 0 && ax < tx && ay >= 0 && ay < ty && az >= 0 && az < tz) {
+            const long src = ((long)az * ty + ay) * tx + ax;
+            t = T[src];
+            kk = K[src];
+            ss = S[src];
+        }
+        oT[idx] = t;
+        oK[idx] = kk;
+        oS[idx] = ss;
+    }
+}
+
 // Scan box of the rotated array: the tool's voxel cubes rotate into the hull of the rotated
 // corners of its voxel-edge box; one voxel of margin on every side.
 void scan_box(const double *R, int tx, int ty, int tz, const int *o, int *box)
@@ -385,27 +422,67 @@ bool plan_direct(Tool &t, const int n[3], int vlo[3], int vhi[3], std::vector<in
     return false;
 }
 
+// Sizes of the per-handle work buffers for the current tools (elements; see ensure_work).
+struct WorkSizes {
+    size_t rs = 0, x1 = 0, x2 = 0, y1 = 0, y2 = 0, gn = 0, bn = 0, hl = 0;
+    int maxo = 1, min_slots = 1;
+};
+
+WorkSizes work_sizes(imf_handle h)
+{
+    const imf_options &op = h->opt;
+    WorkSizes w;
+    for (int i = 0; i < h->n_tools; ++i) {
+        const Tool &t = h->tools[i];
+        w.rs = std::max(w.rs, (size_t)t.P[2] * t.P[1] * t.Hs);
+        w.x1 = std::max(w.x1, (size_t)op.nz * op.ny * t.Hs);
+        w.x2 = std::max(w.x2, (size_t)op.nz * t.P[1] * t.Hs);
+        w.y1 = std::max(w.y1, (size_t)t.win[2] * t.P[1] * t.Hs);
+        w.y2 = std::max(w.y2, (size_t)t.win[2] * t.win[1] * t.Hs);
+        w.gn = std::max(w.gn, (size_t)t.win[2] * t.win[1] * t.gpx);
+        w.bn = std::max(w.bn, (size_t)t.win[2] * t.win[1] * t.wpr);
+        w.maxo = std::max(w.maxo, t.n_orient);
+        if (t.path == IMF_BF16_DIRECT) {
+            w.hl = std::max(w.hl, (size_t)t.dP[0] * t.dP[1] * t.dP[2]);
+            w.min_slots = std::max(w.min_slots, std::min(t.dG, t.n_orient));
+        }
+    }
+    return w;
+}
+
+// Orientation slots of the first imf_compute without an HBM budget: the requested batch (64 by
+// default), at most the largest orientation count, at least one direct-path group.
+int default_slots(imf_handle h, const WorkSizes &w)
+{
+    int want = h->opt.orient_batch > 0 ? h->opt.orient_batch : 64;
+    return std::max(std::min(want, w.maxo), w.min_slots);
+}
+
+// Bytes the work buffers of a first imf_compute with `slots` orientation slots allocate
+// (each allocation as dalloc makes it: at least one element).
+size_t work_bytes(imf_handle h, const WorkSizes &w, int slots)
+{
+    const imf_options &op = h->opt;
+    auto b = [](size_t n, size_t e) { return std::max<size_t>(n, 1) * e; };
+    const size_t N = (size_t)op.nx * op.ny * op.nz;
+    const size_t awords = (size_t)(op.nx + 31) / 32;
+    size_t t = 0;
+    if (w.hl) t += b(w.hl, 4);
+    t += b(N, 4) + b((size_t)op.nz * op.ny * awords, 4) + b(8, 4);
+    t += b(w.rs, 8) + b(w.x1, 8) + b(w.x2, 8);
+    t += b(w.y1 * slots, 8) + b(w.y2 * slots, 8) + b(w.gn * slots, 4) + b(w.bn * slots * kSweepLevels, 4);
+    const long wcap = std::max<long>(1 << 16, (long)(w.gn * slots / 32));
+    t += b((size_t)wcap, 8);
+    return t;
+}
+
 imf_status ensure_work(imf_handle h)
 {
     const imf_options &op = h->opt;
     const long N = (long)op.nx * op.ny * op.nz;
-    size_t rs = 0, x1 = 0, x2 = 0, y1 = 0, y2 = 0, gn = 0, bn = 0, hl = 0;
-    int maxo = 1, min_slots = 1;
-    for (int i = 0; i < h->n_tools; ++i) {
-        const Tool &t = h->tools[i];
-        rs = std::max(rs, (size_t)t.P[2] * t.P[1] * t.Hs);
-        x1 = std::max(x1, (size_t)op.nz * op.ny * t.Hs);
-        x2 = std::max(x2, (size_t)op.nz * t.P[1] * t.Hs);
-        y1 = std::max(y1, (size_t)t.win[2] * t.P[1] * t.Hs);
-        y2 = std::max(y2, (size_t)t.win[2] * t.win[1] * t.Hs);
-        gn = std::max(gn, (size_t)t.win[2] * t.win[1] * t.gpx);
-        bn = std::max(bn, (size_t)t.win[2] * t.win[1] * t.wpr);
-        maxo = std::max(maxo, t.n_orient);
-        if (t.path == IMF_BF16_DIRECT) {
-            hl = std::max(hl, (size_t)t.dP[0] * t.dP[1] * t.dP[2]);
-            min_slots = std::max(min_slots, std::min(t.dG, t.n_orient));
-        }
-    }
+    const WorkSizes ws = work_sizes(h);
+    const size_t rs = ws.rs, x1 = ws.x1, x2 = ws.x2, y1 = ws.y1, y2 = ws.y2, gn = ws.gn, bn = ws.bn, hl = ws.hl;
+    const int min_slots = ws.min_slots;
     if (hl > h->rhohl_n) { dfree(h, h->rhohl); h->rhohl_n = 0; TRY(dalloc(h, &h->rhohl, hl)); h->rhohl_n = hl; }
     if (!h->f) {
         TRY(dalloc(h, &h->f, (size_t)N));
@@ -420,8 +497,7 @@ imf_status ensure_work(imf_handle h)
     // default batch: 64 orientations (larger batches prune more in the minimum and the sweep,
     // since outputs that reach 0 skip the rest of their orientation group, and leave fewer
     // partial waves; 128^3 x 64: 5.9 ms per step against 6.3 with 16)
-    int want = op.orient_batch > 0 ? op.orient_batch : 64;
-    want = std::max(std::min(want, maxo), min_slots);
+    int want = default_slots(h, ws);
     // per orientation slot: Y1, Y2, g, free bits and its share of the near-threshold list
     const size_t per_slot = y1 * 8 + y2 * 8 + gn * 4 + bn * 4 * kSweepLevels + (gn / 32 + 1) * sizeof(int2);
     if (op.hbm_budget_bytes) {
@@ -523,6 +599,7 @@ void imf_default_options(imf_options *opt)
     opt->fft_stages_only = 0;
     opt->accessible_by_sweep = 0;
     opt->separate_yx_passes = 0;
+    opt->plan_only = 0;
 }
 
 imf_status imf_create(const imf_options *opt, imf_handle *out)
@@ -649,7 +726,17 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
     long *dboff = nullptr;
     imf_status st = IMF_OK;
     std::vector<uint8_t> hout;
-    {
+    const bool plan_only = h->opt.plan_only != 0;
+    auto vbytes = [](size_t n, size_t e) { return std::max<size_t>(n, 1) * e; };
+    const size_t rot_bytes = 3 * vbytes((size_t)tv, 1) + vbytes(R.size(), 8) + vbytes(box.size(), 4) +
+                             vbytes(boff.size(), 8) + vbytes((size_t)tot * 3, 1);
+    if (plan_only) {
+        // resample on the host (same arithmetic as rotate_kernel); nothing touches the device
+        hout.assign((size_t)tot * 3, 0);
+        for (int i = 0; i < n_orient; ++i)
+            rotate_host(T.data(), K.data(), S.data(), tx, ty, tz, t.o, &R[9 * i], &box[6 * i], hout.data() + boff[i],
+                        hout.data() + tot + boff[i], hout.data() + 2 * tot + boff[i]);
+    } else {
         auto cleanup = [&]() {
             dfree(h, dT, (size_t)tv); dfree(h, dK, (size_t)tv); dfree(h, dS, (size_t)tv);
             dfree(h, dout, (size_t)tot * 3); dfree(h, dR, R.size()); dfree(h, dbox, box.size());
@@ -794,40 +881,53 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
         return fail(h, IMF_ERR_INVALID_ARG, "sharp-point set too wide for the tiled minimum (%zu bytes of tile)",
                     t.erode_smem);
     }
-    {
+    if (!plan_only) {
         int dev = 0, n = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
             h->nsm = n;
+        t.erode_bps = erode2_blocks_per_sm(t.erode_smem);
     }
-    t.erode_bps = erode2_blocks_per_sm(t.erode_smem);
     st = IMF_OK;
     auto bail = [&](imf_status s2) { free_tool(h, t); return s2; };
-    twiddles(t.M, t.M, t.M, tw);
-    if ((st = upload(h, &t.twM, tw))) return bail(st);
-    twiddles(t.P[0], t.P[0], t.M + 1, tw);
-    if ((st = upload(h, &t.twP, tw))) return bail(st);
-    twiddles(t.P[1], t.P[1], t.P[1], tw);
-    if ((st = upload(h, &t.twy, tw))) return bail(st);
-    twiddles(t.P[2], t.P[2], t.P[2], tw);
-    if ((st = upload(h, &t.twz, tw))) return bail(st);
-    if ((st = upload(h, &t.rt_off, rto)) || (st = upload(h, &t.rt_start, rts)) || (st = upload(h, &t.sw_pairs, ivv)) ||
-        (st = upload(h, &t.sw_start, ivst)) ||
-        (st = upload(h, &t.er_chunks, chunks)) || (st = upload(h, &t.er_chunk_start, chst)) ||
-        (st = upload(h, &t.er_runs, eruns)))
-        return bail(st);
+    // resident tables: twiddles, offset lists, sweep and erosion descriptors (counted the same
+    // way whether they are uploaded or only planned)
+    t.table_bytes = vbytes((size_t)t.M, 8) + vbytes((size_t)t.M + 1, 8) + vbytes((size_t)t.P[1], 8) +
+                    vbytes((size_t)t.P[2], 8) + vbytes(rto.size(), 4) + vbytes(rts.size(), 4) +
+                    vbytes(ivv.size(), sizeof(int4)) + vbytes(ivst.size(), 4) +
+                    vbytes(chunks.size(), sizeof(ErodeChunk)) + vbytes(chst.size(), 4) +
+                    vbytes(eruns.size(), sizeof(int2));
+    if (!plan_only) {
+        twiddles(t.M, t.M, t.M, tw);
+        if ((st = upload(h, &t.twM, tw))) return bail(st);
+        twiddles(t.P[0], t.P[0], t.M + 1, tw);
+        if ((st = upload(h, &t.twP, tw))) return bail(st);
+        twiddles(t.P[1], t.P[1], t.P[1], tw);
+        if ((st = upload(h, &t.twy, tw))) return bail(st);
+        twiddles(t.P[2], t.P[2], t.P[2], tw);
+        if ((st = upload(h, &t.twz, tw))) return bail(st);
+        if ((st = upload(h, &t.rt_off, rto)) || (st = upload(h, &t.rt_start, rts)) ||
+            (st = upload(h, &t.sw_pairs, ivv)) || (st = upload(h, &t.sw_start, ivst)) ||
+            (st = upload(h, &t.er_chunks, chunks)) || (st = upload(h, &t.er_chunk_start, chst)) ||
+            (st = upload(h, &t.er_runs, eruns)))
+            return bail(st);
+    }
     // --- direct tensor-core path: groups, union taps, B matrices
     const int prec = h->opt.precision;
     if (prec != IMF_FP32_FFT) {
         std::vector<int> taps;
         std::vector<uint16_t> bm;
         t.dir_ok = plan_direct(t, n, vlo, vhi, taps, bm);
-        if (t.dir_ok && ((st = upload(h, &t.d_taps, taps)) || (st = upload(h, &t.d_bmat, bm)))) return bail(st);
+        if (t.dir_ok) t.table_bytes += vbytes(taps.size(), 4) + vbytes(bm.size(), 2);
+        if (t.dir_ok && !plan_only && ((st = upload(h, &t.d_taps, taps)) || (st = upload(h, &t.d_bmat, bm))))
+            return bail(st);
     }
     if (prec == IMF_BF16_DIRECT && !t.dir_ok)
         return bail(fail(h, IMF_ERR_INVALID_ARG, "tool too large for the direct tensor-core path"));
     t.path = prec == IMF_BF16_DIRECT ? IMF_BF16_DIRECT : IMF_FP32_FFT;
     if (prec == IMF_BF16_DIRECT) {
+        t.setup_bytes = std::max(rot_bytes, t.table_bytes);
+        t.planned_only = plan_only;
         t.set = true;
         if (tool_id == h->n_tools) h->n_tools++;
         return IMF_OK;
@@ -836,6 +936,16 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
     // --- tool spectra: conj(FFT(1_RT)) / Ptot (reflection as conjugation, Alg. 1 footnote)
     const size_t per = (size_t)t.P[2] * t.P[1] * t.Hs;
     t.spec_bytes = per * n_orient * sizeof(float2);
+    // transient buffers of the spectrum build: the dense padded tool and two intermediates
+    t.setup_bytes = std::max(rot_bytes, t.table_bytes + t.spec_bytes + (size_t)t.P[0] * t.P[1] * t.P[2] * 4 +
+                                            2 * per * sizeof(float2));
+    if (plan_only) {
+        t.planned_only = true;
+        t.has_spec = true;
+        t.set = true;
+        if (tool_id == h->n_tools) h->n_tools++;
+        return IMF_OK;
+    }
     if ((st = dalloc(h, &t.spec, per * n_orient))) return bail(st);
     float *dense = nullptr;
     float2 *s1 = nullptr, *s2 = nullptr;
@@ -1055,8 +1165,11 @@ imf_status imf_compute(imf_handle h, const float *rho_omega, const uint8_t *fixt
 {
     if (!h) return IMF_ERR_INVALID_ARG;
     if (h->n_tools == 0) return fail(h, IMF_ERR_NOT_READY, "imf_compute before imf_set_tool");
-    for (int i = 0; i < h->n_tools; ++i)
+    for (int i = 0; i < h->n_tools; ++i) {
         if (!h->tools[i].set) return fail(h, IMF_ERR_NOT_READY, "tool %d not set", i);
+        if (h->tools[i].planned_only)
+            return fail(h, IMF_ERR_NOT_READY, "tool %d was planned only (plan_only handle): nothing on the device", i);
+    }
     if (!rho_omega || !imf_bar || !secluded) return fail(h, IMF_ERR_INVALID_ARG, "NULL required array");
     return compute_impl(h, rho_omega, fixture, imf_bar, secluded, imf_raw, accessible, (cudaStream_t)cuda_stream);
 }
@@ -1333,6 +1446,21 @@ imf_status imf_get_last_g(imf_handle h, int slot, float *g_out, long cap, int *o
     return IMF_OK;
 }
 
+imf_status imf_get_last_bits(imf_handle h, int slot, uint32_t *bits_out, long cap, int *orient_out)
+{
+    if (!h || h->last_tool < 0 || slot < 0 || slot >= h->last_batch_n) return IMF_ERR_INVALID_ARG;
+    if (!h->keep_g && !h->run_sweep)
+        return fail(h, IMF_ERR_NOT_READY, "free bits are kept only with imf_set_debug or on the sweep route");
+    const Tool &t = h->tools[h->last_tool];
+    const long n = (long)t.win[2] * t.win[1] * t.wpr;
+    if (orient_out) *orient_out = t.perm[h->last_batch_base + slot];
+    if (!bits_out) return IMF_OK;
+    if (cap < n) return fail(h, IMF_ERR_INVALID_ARG, "capacity %ld < %ld", cap, n);
+    if (h->used_stream) CU(cudaStreamSynchronize(h->last_stream));
+    CU(cudaMemcpy(bits_out, h->bits + (size_t)slot * h->bits_n, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    return IMF_OK;
+}
+
 imf_status imf_get_stats(imf_handle h, imf_stats *out)
 {
     if (!h || !out) return IMF_ERR_INVALID_ARG;
@@ -1341,6 +1469,28 @@ imf_status imf_get_stats(imf_handle h, imf_stats *out)
     out->flagged = h->flagged_last;
     out->flagged_total = h->flagged_total;
     out->n_kernels = KID_COUNT;
+    out->owned_bytes = h->owned_bytes;
+    return IMF_OK;
+}
+
+imf_status imf_footprint(imf_handle h, int slots, imf_footprint_info *out)
+{
+    if (!h || !out) return IMF_ERR_INVALID_ARG;
+    if (h->n_tools == 0) return fail(h, IMF_ERR_NOT_READY, "imf_footprint before imf_set_tool");
+    if (slots < 0) return fail(h, IMF_ERR_INVALID_ARG, "slots %d < 0", slots);
+    const WorkSizes ws = work_sizes(h);
+    const int s = slots > 0 ? std::max(slots, ws.min_slots) : default_slots(h, ws);
+    size_t resident = 0, peak = 0;
+    for (int i = 0; i < h->n_tools; ++i) {
+        const Tool &t = h->tools[i];
+        peak = std::max(peak, resident + t.setup_bytes);
+        resident += t.spec_bytes + t.table_bytes;
+    }
+    out->resident = resident;
+    out->work = work_bytes(h, ws, s);
+    out->setup_peak = peak;
+    out->total = std::max(resident + out->work, peak);
+    out->slots = s;
     return IMF_OK;
 }
 

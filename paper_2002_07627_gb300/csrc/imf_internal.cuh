@@ -210,4 +210,16 @@ void launch_absmax_omega0(const float *v, const uint8_t *fix, long n, unsigned *
 void launch_penalize(float *sens, const float *rho, const float *fbar, const uint8_t *sec, long n,
                      const unsigned *maxbits, double w, double tau, cudaStream_t s);
 
+// Eq. eq_filtered_sens with the filter of Eq. eq_accFilter at one voxel (FP32):
+// S = (1 - w) S_phi / m + w S_IMF with S_IMF = f_bar where rho > tau, 1 on Gamma, 0 elsewhere;
+// S_phi stays unnormalised when m = max |S_phi| over Omega_0 is 0. Shared by the handle's
+// penalty kernel and the allocation-free one.
+__device__ __forceinline__ float penalized_sensitivity(float s, float rho, float fbar, uint8_t sec, float m, float w,
+                                                       float tau)
+{
+    const float sb = m > 0.f ? s * (1.f / m) : s;
+    const float simf = rho > tau ? fbar : (sec ? 1.f : 0.f);
+    return (1.f - w) * sb + w * simf;
+}
+
 } // namespace imf

@@ -277,12 +277,8 @@ __global__ void penalize_kernel(float *sens, const float *rho, const float *fbar
                                 const unsigned *maxbits, float w, float tau)
 {
     const float m = __uint_as_float(*maxbits);
-    const float inv = m > 0.f ? 1.f / m : 1.f;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const float sb = m > 0.f ? sens[i] * inv : sens[i];
-        const float simf = rho[i] > tau ? fbar[i] : (sec[i] ? 1.f : 0.f);
-        sens[i] = (1.f - w) * sb + w * simf;
-    }
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        sens[i] = penalized_sensitivity(sens[i], rho[i], fbar[i], sec[i], m, w, tau);
 }
 
 } // namespace

@@ -72,15 +72,13 @@ __global__ void __launch_bounds__(kNoallocThreads) noalloc_penalize(float *sens,
                                                                   float w, float tau)
 {
     const float m = scratch[kMaxPartials];
-    const float inv = m > 0.f ? 1.f / m : 1.f;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const float sb = m > 0.f ? sens[i] * inv : sens[i];
-        const float simf = rho[i] > tau ? fbar[i] : (sec[i] ? 1.f : 0.f);
-        sens[i] = (1.f - w) * sb + w * simf;
-    }
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        sens[i] = imf::penalized_sensitivity(sens[i], rho[i], fbar[i], sec[i], m, w, tau);
 }
 
 // Device address of the scratch array, looked up once per device with that device current.
+// The address stays valid for the life of the device's primary context: a caller that resets
+// the device (cudaDeviceReset) must not call this entry point again in the same process.
 std::mutex g_noalloc_mu;
 float *g_noalloc_ptr[256] = {nullptr};
 

@@ -236,17 +236,29 @@ class GpuExecutor:
         self.orient_batch = int(orient_batch)
 
     def footprint(self, spec: DesignSpec) -> int:
-        from .batch import spectra_bytes_estimate
+        """Bytes a served design holds on the device: the library's planned footprint (spectra,
+        tables, set-up peak and the work buffers of `orient_batch` slots, imf_footprint) plus the
+        request buffers this executor allocates with torch (rho, fixture, f_bar, Gamma)."""
+        from .batch import planned_footprint
         from .synth import Design
-        return spectra_bytes_estimate(Design(np.zeros(spec.shape, np.float32), spec.fixture, spec.tools),
-                                      orient_batch=self.orient_batch)
+        fp = planned_footprint(Design(np.zeros(spec.shape, np.float32), spec.fixture, spec.tools),
+                               orient_batch=self.orient_batch)
+        n = int(np.prod(spec.shape))
+        return int(fp.total) + n * (4 + 4 + 1 + (1 if spec.fixture is not None else 0))
+
+    def library_budget(self, spec: DesignSpec) -> int:
+        from .batch import planned_footprint
+        from .synth import Design
+        return int(planned_footprint(Design(np.zeros(spec.shape, np.float32), spec.fixture, spec.tools),
+                                     orient_batch=self.orient_batch).total)
 
     def create(self, design_id, spec: DesignSpec):
         from . import binding
         torch = self.torch
         torch.cuda.set_device(self.dev)
+        # the library enforces the admitted footprint (IMF_ERR_BUDGET beyond it)
         imf = binding.Imf(spec.shape, lam=spec.lam, tau=spec.tau, theta_rel=spec.theta_rel,
-                          orient_batch=self.orient_batch)
+                          orient_batch=self.orient_batch, hbm_budget_bytes=self.library_budget(spec))
         imf.set_tools(spec.tools)
         st = {"imf": imf,
               "rho": torch.empty(spec.shape, dtype=torch.float32, device=self.dev),

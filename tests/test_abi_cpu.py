@@ -111,6 +111,56 @@ def test_default_options_and_create_checks(lib):
     lib.imf_destroy(None)
 
 
+def test_noalloc_penalty_rejects_bad_arguments_on_the_host(lib):
+    """The allocation-free penalty checks its arguments before any CUDA call: NULL arrays,
+    n < 1, n above the scratch limit, w_acc outside [0, 1) and tau outside [0, 1] are refused
+    with IMF_ERR_INVALID_ARG. The pointers below are never dereferenced."""
+    f = lib.imf_penalize_sensitivity_noalloc
+    p = 0x1000
+    assert f(None, p, p, p, None, 10, 0.3, 0.5, None) == 1
+    assert f(p, None, p, p, None, 10, 0.3, 0.5, None) == 1
+    assert f(p, p, None, p, None, 10, 0.3, 0.5, None) == 1
+    assert f(p, p, p, None, None, 10, 0.3, 0.5, None) == 1
+    assert f(p, p, p, p, None, 0, 0.3, 0.5, None) == 1
+    assert f(p, p, p, p, None, -5, 0.3, 0.5, None) == 1
+    assert f(p, p, p, p, None, 268435456 + 1, 0.3, 0.5, None) == 1
+    assert f(p, p, p, p, None, 10, 1.0, 0.5, None) == 1
+    assert f(p, p, p, p, None, 10, -0.1, 0.5, None) == 1
+    assert f(p, p, p, p, None, 10, float("nan"), 0.5, None) == 1
+    assert f(p, p, p, p, None, 10, 0.3, 1.5, None) == 1
+    assert f(p, p, p, p, None, 10, 0.3, -0.5, None) == 1
+
+
+def test_plan_only_footprint_of_the_128_workload(lib):
+    """The planner runs on the host (plan_only handle: the tool is resampled on the CPU with the
+    device kernel's arithmetic and nothing touches a device). For the 128^3 x 64 workload's tool
+    it picks the padded grid (192, 192, 168) the GPU runs use; the footprint adds the resident
+    spectra (n_orient Pz Py Hs complex64) and tables, the work buffers of 64 orientation slots
+    and the set-up peak; a plan-only handle refuses to compute."""
+    tool = synth.cylinder_tool(3, 20, 8, 16, synth.fibonacci_quats(64))
+    imf = binding.Imf((128, 128, 128), plan_only=True)
+    imf.set_tools([tool])
+    info = imf.tool_info(0)
+    assert info.P == (192, 192, 168)
+    Hs = (192 // 2 + 1 + 1) & ~1
+    assert info.spectra_bytes == 64 * 168 * 192 * Hs * 8
+    fp = imf.footprint()
+    assert fp.slots == 64
+    assert info.spectra_bytes < fp.resident < 1.01 * info.spectra_bytes
+    wx, wy, wz = info.win
+    gpx, wpr = (wx + 3) & ~3, (wx + 31) // 32 + 2
+    per_slot = wz * 192 * Hs * 8 + wz * wy * Hs * 8 + wz * wy * gpx * 4 + wz * wy * wpr * 4 * 5
+    assert fp.work > 64 * per_slot and fp.work < 64 * per_slot + 200 * 2 ** 20
+    assert fp.total == max(fp.resident + fp.work, fp.setup_peak)
+    assert fp.setup_peak > info.spectra_bytes
+    fp1 = imf.footprint(1)
+    assert fp1.slots == 1 and fp1.work < fp.work
+    with pytest.raises(binding.ImfError) as ei:
+        imf._check(imf.lib.imf_compute(imf.h, 1, None, 1, 1, None, None, None))
+    assert ei.value.status == 5
+    imf.close()
+
+
 def test_stage_reciprocals_are_exact(lib):
     L = ctypes.CDLL(build.HOSTLIB)
     L.imf_host_check_div.restype = ctypes.c_long

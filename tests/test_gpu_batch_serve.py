@@ -4,6 +4,7 @@ runs mixed with requests of other designs."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2002_07627_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -40,6 +41,15 @@ def _plain(d):
     return out
 
 
+def _check_vs_oracle(d, fbar, sec, lam=0.01):
+    """f_bar and Gamma of one design against the FP64 oracle, away from the allowance
+    discontinuity (the IMF contract of the plain form)."""
+    ref = oracle.imf(d)
+    clear = np.abs(ref["fbar"] - lam) > 1e-4
+    assert np.abs(fbar.astype(np.float64) - ref["fbar"])[clear].max() <= 2e-4
+    assert np.array_equal(sec[clear], ref["secluded"][clear])
+
+
 def test_batch_runner_graphs_and_autotune_match_plain_compute():
     _need_gpu()
     from paper_2002_07627_gb300.batch import BatchRunner
@@ -51,9 +61,10 @@ def test_batch_runner_graphs_and_autotune_match_plain_compute():
     for _ in range(2):
         br.run()
     br.check()
-    for e, (fb, sec) in zip(br.entries, ref):
+    for e, (fb, sec), d in zip(br.entries, ref, ds):
         assert np.array_equal(e.fbar.cpu().numpy(), fb)
         assert np.array_equal(e.sec.cpu().numpy(), sec)
+        _check_vs_oracle(d, e.fbar.cpu().numpy(), e.sec.cpu().numpy())
     br.close()
 
 
@@ -87,6 +98,7 @@ def test_served_result_is_the_same_alone_and_in_the_mix():
     assert np.array_equal(alone[0], mixed[0]) and np.array_equal(alone[1], mixed[1])
     ref = _plain(ds[0])
     assert np.array_equal(alone[0], ref[0]) and np.array_equal(alone[1], ref[1])
+    _check_vs_oracle(ds[0], alone[0], alone[1])
 
 
 def test_autotune_under_a_tight_budget_then_compute():
@@ -94,10 +106,11 @@ def test_autotune_under_a_tight_budget_then_compute():
     handle must still compute the same result as an unconstrained one."""
     _need_gpu()
     from paper_2002_07627_gb300 import binding
-    from paper_2002_07627_gb300.batch import spectra_bytes_estimate
+    from paper_2002_07627_gb300.batch import planned_footprint
     d = _designs()[2]
     ref = _plain(d)
-    imf = binding.Imf(d.rho.shape, hbm_budget_bytes=int(spectra_bytes_estimate(d)) + (24 << 20))
+    fp = planned_footprint(d, slots=1)
+    imf = binding.Imf(d.rho.shape, hbm_budget_bytes=int(max(fp.setup_peak, fp.resident + fp.work)) + (24 << 20))
     imf.set_tools(d.tools)
     rho = torch.from_numpy(d.rho).cuda()
     fix = torch.from_numpy(d.fixture).cuda()
@@ -106,4 +119,35 @@ def test_autotune_under_a_tight_budget_then_compute():
     fb, sec = imf.compute(rho, fix)
     imf.sync()
     assert np.array_equal(fb.cpu().numpy(), ref[0]) and np.array_equal(sec.cpu().numpy(), ref[1])
+    _check_vs_oracle(d, fb.cpu().numpy(), sec.cpu().numpy())
     imf.close()
+
+
+def test_planned_footprint_equals_what_the_handle_allocates():
+    """The admission figure comes from the library's plan (plan_only handle, host only): a real
+    handle of the same design owns exactly the planned resident bytes after set-up and the
+    planned total after its first compute, and plans the same padded grid and window; one and
+    two tools, a 2D grid, a budget-free default slot count and an explicit one."""
+    _need_gpu()
+    from paper_2002_07627_gb300 import binding
+    from paper_2002_07627_gb300.batch import planned_footprint
+    ds = _designs()[:2]
+    two = synth.Design(ds[0].rho, ds[0].fixture, ds[0].tools + [synth.cylinder_tool(1, 4, 3, 3, synth.fibonacci_quats(5))])
+    for d, ob in ((ds[0], 0), (ds[1], 3), (two, 4), (synth.config_planar64(seed=1), 0)):
+        fp = planned_footprint(d, orient_batch=ob)
+        imf = binding.Imf(d.rho.shape, orient_batch=ob)
+        imf.set_tools(d.tools)
+        assert imf.stats().owned_bytes == fp.resident
+        plan = binding.Imf(d.rho.shape, orient_batch=ob, plan_only=True)
+        plan.set_tools(d.tools)
+        for i in range(len(d.tools)):
+            a, b = imf.tool_info(i), plan.tool_info(i)
+            assert (a.P, a.win, a.kmax, a.n_rt, a.n_rk, a.n_sharp) == (b.P, b.win, b.kmax, b.n_rt, b.n_rk, b.n_sharp)
+        plan.close()
+        rho = torch.from_numpy(np.ascontiguousarray(d.rho)).cuda()
+        fix = None if d.fixture is None else torch.from_numpy(np.ascontiguousarray(d.fixture)).cuda()
+        imf.compute(rho, fix)
+        imf.sync()
+        assert imf.stats().owned_bytes == fp.resident + fp.work
+        assert fp.total >= fp.resident + fp.work
+        imf.close()

@@ -40,26 +40,60 @@ def run_gpu(design, lam=0.01, tau=0.5, theta_rel=0.01, keep=False, **kw):
     return out
 
 
+def accessible_bounds(design, ref, theta_rel=0.01):
+    """Accessible sets that the contract fixes, from the oracle's per-orientation collision
+    fields (Eq. eq_conv_A per orientation, union over orientations and tools, Eq. eq_A_multi):
+    `sure` = the sweep of the translations that are free by more than the band
+    (g < theta_i - 1e-3 |T_i|), which every correct result contains; `maybe` = the sweep of the
+    translations within the band, where either classification is correct. A point in neither
+    set must be inaccessible."""
+    shape = design.rho.shape
+    sure = np.zeros(shape, bool)
+    maybe = np.zeros(shape, bool)
+    per = ref["per_orientation"]
+    i = 0
+    for tool in design.tools:
+        size = float(((tool.holder != 0) | (tool.cutter != 0)).sum())
+        theta, band = theta_rel * size, 1e-3 * size
+        for _ in tool.quats:
+            p = per[i]
+            i += 1
+            if p is None:
+                continue
+            g = p["g"]
+            sure |= oracle.sweep((g < theta - band).astype(np.uint8), p["tlo"], p["RK"], shape).astype(bool)
+            maybe |= oracle.sweep((np.abs(g - theta) <= band).astype(np.uint8), p["tlo"], p["RK"], shape).astype(bool)
+    assert i == len(per)
+    return sure, maybe
+
+
 def check_against_oracle(design, got, ref, theta_rel=0.01, lam=0.01):
-    sizes = [int(((t.holder != 0) | (t.cutter != 0)).sum()) for t in design.tools]
-    thetas = [theta_rel * s for s in sizes]
+    """The IMF contract against the oracle run `ref` (oracle.imf(design, keep=True)): raw f
+    within 1e-4 max f everywhere; the accessible set exact wherever no translation that reaches
+    the point lies within 1e-3 |T_i| of its tool's threshold (any number of tools, any sharp
+    subset); f_bar and Gamma away from the allowance discontinuity."""
     fmax = float(np.max(ref["f"][np.isfinite(ref["f"])]))
     err = np.abs(got["f"] - ref["f"])
     assert err.max() <= 1e-4 * fmax, (err.max(), fmax)
-    # accessible: exact away from the threshold of every tool (single tool: A = [f <= theta])
-    if len(design.tools) == 1:
-        band = 1e-3 * sizes[0]
-        clear = np.abs(ref["f"] - thetas[0]) > band
-        if design.fixture is not None:
-            clear &= design.fixture == 0
-        mism = (got["accessible"] != ref["accessible"]) & clear
-        assert not mism.any(), np.argwhere(mism)[:5]
-    else:
-        # for several tools compare where no tool's minimum is near its own threshold
-        pass
+    sure, maybe = accessible_bounds(design, ref, theta_rel)
+    om0 = np.ones(design.rho.shape, bool) if design.fixture is None else design.fixture == 0
+    A = got["accessible"] != 0
+    assert not (A & ~om0).any(), "fixture cells must be inaccessible"
+    missing = sure & om0 & ~A
+    assert not missing.any(), ("accessible points missing", np.argwhere(missing)[:5])
+    extra = A & ~sure & ~maybe
+    assert not extra.any(), ("points accessible only within round-off of nothing", np.argwhere(extra)[:5])
+    # the oracle's own accessible set obeys the same bounds (pins the bound computation)
+    Ao = ref["accessible"] != 0
+    assert not (sure & om0 & ~Ao).any() and not (Ao & ~sure & ~maybe).any()
     clear = np.abs(ref["fbar"] - lam) > 1e-4
     assert np.abs(got["fbar"] - ref["fbar"])[clear].max() <= 2e-4
     assert np.array_equal(got["secluded"][clear], ref["secluded"][clear])
+
+
+def oracle_ref(design, **kw):
+    """The oracle's result with the per-orientation fields the accessible-set check needs."""
+    return oracle.imf(design, keep=True, **kw)
 
 
 def test_resampled_tool_sets_match_oracle_bit_exactly():
@@ -83,7 +117,7 @@ def test_resampled_tool_sets_match_oracle_bit_exactly():
 
 def test_planar64_full_parity():
     d = synth.config_planar64(seed=0)
-    ref = oracle.imf(d)
+    ref = oracle_ref(d)
     got = run_gpu(d)
     check_against_oracle(d, got, ref)
 
@@ -93,7 +127,7 @@ def test_planar_ragged_full_parity(seed):
     d = synth.config_planar64(seed=seed)
     d.rho = np.ascontiguousarray(d.rho[:, :53, :71])
     d.fixture = np.ascontiguousarray(d.fixture[:, :53, :71])
-    ref = oracle.imf(d)
+    ref = oracle_ref(d)
     got = run_gpu(d, orient_batch=3)
     check_against_oracle(d, got, ref)
 
@@ -107,20 +141,22 @@ def _small3d(seed=0, n=(40, 36, 28), n_orient=8):
 
 def test_3d_ragged_full_parity():
     d = _small3d()
-    ref = oracle.imf(d, keep=True)
+    ref = oracle_ref(d)
     got = run_gpu(d, orient_batch=3)
     check_against_oracle(d, got, ref)
 
 
 def test_collision_field_and_free_bits_per_orientation():
-    """g of the last orientation batch against the oracle's direct FP64 sums; the free
-    classification g <= theta is exact outside the 1e-3 |T| band (and, with the re-check,
-    everywhere except within FP32 round-off of theta)."""
-    d = _small3d(seed=4, n=(33, 29, 21), n_orient=5)
+    """Every slot of the last orientation batch: the collision field g on the whole translation
+    window against the oracle's direct FP64 sums (Eq. eq_ident), and the free bits the kernels
+    wrote (threshold epilogue plus near-threshold re-check, Eq. eq_conv_D) against g <= theta of
+    the oracle: exact outside the 1e-3 |T| band and, with the re-check, everywhere except within
+    FP32 round-off of theta."""
+    d = _small3d(seed=4, n=(33, 29, 21), n_orient=6)
     binding = _gpu()
-    imf = binding.Imf(d.rho.shape, orient_batch=2)
+    imf = binding.Imf(d.rho.shape, orient_batch=3)
     imf.set_tools(d.tools)
-    imf.set_debug = True
+    imf.set_debug(True)
     rho = torch.from_numpy(d.rho).cuda()
     fix = torch.from_numpy(d.fixture).cuda()
     imf.compute(rho, fix)
@@ -129,19 +165,29 @@ def test_collision_field_and_free_bits_per_orientation():
     rhoO = oracle.rho_obstacle(d.rho, d.fixture)
     tool = d.tools[0]
     theta = info.theta
-    for slot in range(1):
+    band = 1e-3 * info.size_T
+    k = np.array(info.kmax)
+    seen = set()
+    for slot in range(3):
         o, gw = imf.last_g(slot)
+        o2, bits = imf.last_bits(slot)
+        assert o == o2
+        seen.add(o)
         rs = oracle.resample_tool(tool, tool.quats[o])
-        tlo, text = translation_box(d.rho.shape, rs["RK"], rs["sharp"])
-        g = oracle.collision(rhoO, rs["RT"], tlo, text)
-        k = np.array(info.kmax)
-        i0 = tlo + k
-        sub = gw[i0[2]:i0[2] + text[2], i0[1]:i0[1] + text[1], i0[0]:i0[0] + text[0]]
-        assert sub.shape == g.shape
-        err = np.abs(sub - g)
-        assert err.max() <= 1e-4 * g.max()
-        # re-checked classification
-        assert np.array_equal(sub <= theta, g <= theta) or np.all(np.abs(g[(sub <= theta) != (g <= theta)] - theta) < 1e-4)
+        g = oracle.collision(rhoO, rs["RT"], -k, info.win)
+        assert gw.shape == g.shape == bits.shape
+        err = np.abs(gw - g)
+        assert err.max() <= 1e-4 * g.max(), (o, err.max())
+        free = g <= theta
+        clear = np.abs(g - theta) > band
+        assert np.array_equal(bits[clear] != 0, free[clear]), o
+        diff = (bits != 0) != free
+        assert np.all(np.abs(g[diff] - theta) < 1e-4 * theta), o
+        # the kernels' bits agree with their own g (the re-check rewrites both), up to the FP32
+        # rounding of theta in the epilogue's comparison
+        own = (bits != 0) != (gw <= theta)
+        assert np.all(np.abs(gw[own] - theta) <= 1e-6 * theta), o
+    assert len(seen) == 3
 
 
 def test_3d_beams_full_size_sampled_points():
@@ -167,13 +213,26 @@ def test_3d_beams_full_size_sampled_points():
         assert abs(f[z, y, x] - fv) <= 1e-4 * M, ((x, y, z), f[z, y, x], fv)
         if abs(fv - theta) > 1e-3 * theta / 0.01:
             assert got["accessible"][z, y, x] == av, (x, y, z)
+    # eight seeded 16^3 sub-blocks computed in full by the oracle (direct FP64 sums on the
+    # translations each block needs, the whole design as obstacle)
+    band = 1e-3 * theta / 0.01
+    for seed in range(1, 9):
+        r = np.random.default_rng(seed)
+        x0 = [int(r.integers(0, 113)), int(r.integers(0, 113)), int(r.integers(0, 113))]
+        fo, Ao = oracle.imf_subblock(d, x0, [16, 16, 16])
+        sl = (slice(x0[2], x0[2] + 16), slice(x0[1], x0[1] + 16), slice(x0[0], x0[0] + 16))
+        keep = d.fixture[sl] == 0
+        assert np.abs(f[sl] - fo)[keep].max(initial=0) <= 1e-4 * M, seed
+        clear = keep & (np.abs(fo - theta) > band)
+        assert np.array_equal(got["accessible"][sl][clear], Ao[clear].astype(bool).astype(np.uint8)), seed
 
 
 def test_3d_beams_256_sampled_points():
     """256^3 beams, 128 orientations (the large 3D workload): the padded y and z lengths exceed
-    256, so the y/z passes run radix stages while the x pass (M = 160) runs two register
-    passes; f at the GPU's argmax, near the threshold and at random points against FP64 point
-    queries."""
+    256, so the y and z passes run the two-pass FFT with a factor above 16 (the 32-slot axis
+    kernel) and the x pass (M = 160) the 16 x 10 split; f at the GPU's argmax, near the
+    threshold and at random points against FP64 point queries, then eight seeded 8^3
+    sub-blocks in full."""
     d = synth.config_beams(256, 120, 128, seed=0)
     got = run_gpu(d)
     info = got["imf"].tool_info(0)
@@ -252,7 +311,7 @@ def test_multi_tool_and_sharp_subset():
     sharp[0, 0] = t2.cutter[0, 0]
     t2.sharp = sharp
     d.tools.append(t2)
-    ref = oracle.imf(d)
+    ref = oracle_ref(d)
     got = run_gpu(d)
     check_against_oracle(d, got, ref)
 
@@ -263,7 +322,7 @@ def test_degenerate_grids(shape):
     rho = rng.random(shape).astype(np.float32)
     tool = synth.cylinder_tool(1, 2, 2, 2, synth.fibonacci_quats(3)) if shape[0] > 1 else synth.planar_tool(1, 2, 3, 2, 3)
     d = synth.Design(rho, None, [tool])
-    ref = oracle.imf(d)
+    ref = oracle_ref(d)
     got = run_gpu(d)
     check_against_oracle(d, got, ref)
 
@@ -275,7 +334,7 @@ def test_empty_and_full_density():
     assert not got["f"].any() and not got["fbar"].any() and not got["secluded"].any()
     assert got["accessible"].all()
     o = synth.Design(np.ones((1, 30, 40), np.float32), None, [tool])
-    ref = oracle.imf(o)
+    ref = oracle_ref(o)
     got = run_gpu(o)
     check_against_oracle(o, got, ref)
 
@@ -331,7 +390,7 @@ def test_recheck_list_overflow_is_reported_not_faulted():
 
 def test_recheck_off_stays_inside_the_contract():
     d = _small3d(seed=6, n=(30, 26, 22), n_orient=4)
-    ref = oracle.imf(d)
+    ref = oracle_ref(d)
     got = run_gpu(d, recheck=False)
     check_against_oracle(d, got, ref)
 
@@ -342,7 +401,7 @@ def test_orientation_groups_of_the_minimum_do_not_change_the_result():
     including one group per orientation and more groups than orientations."""
     d = _small3d(seed=4, n=(37, 45, 70), n_orient=11)
     base = run_gpu(d, erode_groups=1, orient_batch=8)
-    ref = oracle.imf(d)
+    ref = oracle_ref(d)
     check_against_oracle(d, base, ref)
     for g in (2, 3, 8, 40, 0):
         got = run_gpu(d, erode_groups=g, orient_batch=8)
@@ -356,7 +415,7 @@ def test_both_fft_variants_match_oracle(stages_only):
     and the radix-stage FFT (forced) both meet the contract on a ragged grid, per orientation
     for g and the free bits and in full for f, f_bar and Gamma."""
     d = _small3d(seed=7, n=(29, 38, 45), n_orient=6)
-    ref = oracle.imf(d, keep=True)
+    ref = oracle_ref(d)
     got = run_gpu(d, orient_batch=4, fft_stages_only=stages_only)
     check_against_oracle(d, got, ref)
     info = got["imf"].tool_info(0)
@@ -370,7 +429,7 @@ def test_accessible_from_the_minimum_equals_the_sweep():
     the oracle. A sharp-point subset (or a second tool) falls back to the sweep by itself."""
     for seed, n in ((3, (31, 40, 47)), (8, (20, 26, 33))):
         d = _small3d(seed=seed, n=n, n_orient=7)
-        ref = oracle.imf(d)
+        ref = oracle_ref(d)
         a = run_gpu(d, orient_batch=4)
         b = run_gpu(d, orient_batch=4, accessible_by_sweep=True)
         check_against_oracle(d, a, ref)
@@ -385,7 +444,7 @@ def test_accessible_from_the_minimum_equals_the_sweep():
     sharp = np.zeros_like(d.tools[0].cutter)
     sharp[: sharp.shape[0] // 2] = 1
     d.tools[0].sharp = sharp
-    check_against_oracle(d, run_gpu(d, orient_batch=4), oracle.imf(d))
+    check_against_oracle(d, run_gpu(d, orient_batch=4), oracle_ref(d))
 
 def test_sweep_of_long_cutter_runs_matches_oracle():
     """Sweep of Eq. eq_conv_A with cutter runs along x of every length class: a 40-voxel cutter
@@ -398,7 +457,7 @@ def test_sweep_of_long_cutter_runs_matches_oracle():
     rho = synth.beam_density((90, 30, 26), n_beams=8, seed=11)
     fix = synth.slab_fixture(rho.shape, 2, axis="z")
     d = synth.Design(rho, fix, [synth.cylinder_tool(2, 40, 3, 4, quats)])
-    ref = oracle.imf(d)
+    ref = oracle_ref(d)
     got = run_gpu(d, orient_batch=3, accessible_by_sweep=True)
     check_against_oracle(d, got, ref)
     assert got["accessible"].any() and not got["accessible"].all()
@@ -423,7 +482,7 @@ def test_fused_yx_pass_equals_separate_passes():
     are identical, and both meet the contract against the oracle. The last case is a grid whose
     plane does not fit in shared memory, where the library falls back to the two kernels."""
     d = _small3d(seed=4, n=(37, 44, 29), n_orient=6)
-    ref = oracle.imf(d)
+    ref = oracle_ref(d)
     for kw in ({}, {"accessible_by_sweep": True}):
         a = run_gpu(d, orient_batch=4, **kw)
         b = run_gpu(d, orient_batch=4, separate_yx_passes=True, **kw)
@@ -449,7 +508,7 @@ def test_big_factor_axis_pass_matches_oracle():
     rho = synth.beam_density((24, 262, 6), n_beams=6, seed=2)
     fix = synth.slab_fixture(rho.shape, 1, axis="z")
     d = synth.Design(rho, fix, [synth.cylinder_tool(1, 4, 2, 3, synth.fibonacci_quats(3))])
-    ref = oracle.imf(d)
+    ref = oracle_ref(d)
     for kw in ({}, {"accessible_by_sweep": True}):
         got = run_gpu(d, orient_batch=2, **kw)
         assert got["imf"].tool_info(0).P[1] > 256
