@@ -541,6 +541,94 @@ def run_secondary(name, args, dev, stream, flush):
     return out
 
 
+def run_sampling(args):
+    """Accuracy against time for the sharp-point sampling modes (Sec. 2.1.5 sampling remark;
+    App. B, O(1) representative points) on the 128^3 x 64 workload: every mode is timed like the
+    benchmark step, and its IMF is compared with the exact IMF (every cutter voxel a sharp
+    point) of the FP64 oracle on seeded 16^3 sub-blocks: the sampled IMF can only be larger
+    (conservative), and the curve reports by how much."""
+    import torch
+    import oracle
+    from paper_2002_07627_gb300 import build, binding
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    d = make_design("beams128", 0)
+    shape = d.rho.shape
+    nG = int(np.prod(shape))
+    n_orient = sum(len(t.quats) for t in d.tools)
+    rho = torch.from_numpy(d.rho).to(dev)
+    fix = torch.from_numpy(d.fixture).to(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    om0 = d.fixture == 0
+    blocks = []
+    for seed in range(1, args.secondary_subblocks + 1):
+        r = np.random.default_rng(seed)
+        E = args.secondary_subblock_ext
+        x0 = [int(r.integers(0, shape[2] - E + 1)), int(r.integers(0, shape[1] - E + 1)),
+              int(r.integers(0, shape[0] - E + 1))]
+        fo, _ = oracle.imf_subblock(d, x0, (E, E, E))
+        blocks.append((x0, E, fo))
+    modes = [("all", binding.IMF_SHARP_ALL, 1), ("boundary", binding.IMF_SHARP_BOUNDARY, 1),
+             ("nearest64", binding.IMF_SHARP_NEAREST, 64), ("nearest16", binding.IMF_SHARP_NEAREST, 16),
+             ("nearest4", binding.IMF_SHARP_NEAREST, 4), ("nearest1", binding.IMF_SHARP_NEAREST, 1)]
+    curve = []
+    sec_all = None
+    for name, m, k in modes:
+        imf = binding.Imf(shape, sharp_sampling=m, sharp_k=k, accessible_by_sweep=True)
+        imf.set_tools(d.tools)
+        fbar = torch.empty_like(rho)
+        sec = torch.empty(shape, dtype=torch.uint8, device=dev)
+        acc = torch.empty(shape, dtype=torch.uint8, device=dev)
+        raw = torch.empty_like(rho)
+        for _ in range(args.warmup):
+            imf.compute(rho, fix, fbar, sec, accessible=acc, stream=stream)
+        imf.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            imf.compute(rho, fix, fbar, sec, accessible=acc, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        imf.compute(rho, fix, fbar, sec, raw=raw, accessible=acc)
+        imf.sync()
+        f = raw.cpu().numpy().astype(np.float64)
+        s = sec.cpu().numpy()
+        if sec_all is None:
+            sec_all = s
+        M = max(float(np.max(fo[om0[x0[2]:x0[2] + E, x0[1]:x0[1] + E, x0[0]:x0[0] + E]], initial=0))
+                for x0, E, fo in blocks)
+        over, under, n_over, n = 0.0, 0.0, 0, 0
+        for x0, E, fo in blocks:
+            sl = (slice(x0[2], x0[2] + E), slice(x0[1], x0[1] + E), slice(x0[0], x0[0] + E))
+            diff = (f[sl] - fo)[om0[sl]]
+            over = max(over, float(diff.max(initial=0)))
+            under = max(under, float(-diff.min(initial=0)))
+            n_over += int(np.sum(diff > 1e-4 * M))
+            n += diff.size
+        info = imf.tool_info(0)
+        curve.append({"mode": name, "sharp_points_per_orientation": info.n_sharp / info.n_orient,
+                      "ms_per_step": ms, "value": nG * n_orient / (ms * 1e-3),
+                      "max_overestimate_over_max_f": over / max(M, 1e-30),
+                      "max_underestimate_over_max_f": under / max(M, 1e-30),
+                      "overestimated_fraction": n_over / max(n, 1),
+                      "secluded_voxels": int(s.sum()), "secluded_lost_vs_all": int(np.sum((sec_all != 0) & (s == 0)))})
+        imf.close()
+    out = {"metric": METRIC, "value": curve[0]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": curve[0]["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "IMF beams128 sharp-point sampling curve: 128x128x128 grid, 64 orientations",
+                      "error_vs": f"FP64 oracle, exact IMF (all cutter voxels), {len(blocks)} seeded "
+                                  f"{args.secondary_subblock_ext}^3 sub-blocks",
+                      "step": "imf_compute (sweep route)"},
+           "curve": curve}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_setup()
@@ -687,7 +775,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="beams256", choices=sorted(WORKLOADS) + ["planar64", "batch64", "serve"])
+    ap.add_argument("--workload", default="beams256",
+                    choices=sorted(WORKLOADS) + ["planar64", "batch64", "serve", "sampling"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-block", type=int, default=24)
     ap.add_argument("--error-points", type=int, default=6)
@@ -724,6 +813,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sampling":
+        return run_sampling(args)
     return run_ours(args)
 
 

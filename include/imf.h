@@ -60,6 +60,14 @@ typedef enum {
 /* collision-convolution path */
 enum { IMF_AUTO = 0, IMF_FP32_FFT = 1, IMF_BF16_DIRECT = 2 };
 
+/* sharp-point sampling of a cutter given without a sharp_mask (Sec. 2.1.5, remark on sampling
+ * the cutter boundary; App. B, n_K = O(1) representative points); in the tool frame, before
+ * rotation, then resampled like the cutter */
+enum { IMF_SHARP_ALL = 0,       /* every cutter voxel (exact IMF)                               */
+       IMF_SHARP_BOUNDARY = 1,  /* cutter voxels with a face neighbour outside the cutter      */
+       IMF_SHARP_NEAREST = 2 }; /* the sharp_k boundary voxels nearest the tool origin
+                                   (squared distance, ties by linear index; nested in k)       */
+
 typedef struct {
     int nx, ny, nz;          /* design grid; nz = 1 is 2D                                       */
     double voxel;            /* voxel edge length; f is reported in voxel volumes (Sec. 2.1.5) */
@@ -90,6 +98,10 @@ typedef struct {
                                 host and touches no device (no allocation, no kernel); the
                                 handle then answers imf_get_tool_info and imf_footprint but
                                 refuses imf_compute (admission planning); 0 = default          */
+    int sharp_sampling;      /* IMF_SHARP_ALL (default) | IMF_SHARP_BOUNDARY | IMF_SHARP_NEAREST:
+                                sharp points of tools set without a sharp_mask; fewer points
+                                can only raise the IMF (conservative, Sec. 2.1.5)             */
+    int sharp_k;             /* points kept by IMF_SHARP_NEAREST (>= 1; default 1)             */
 } imf_options;
 
 /* Fill *opt with the defaults above (grid 0x0x0, which imf_create rejects). */
@@ -104,7 +116,8 @@ imf_status imf_create(const imf_options *opt, imf_handle *out);
  * orientation set Theta_i (Alg. 1 inputs [1_H_i], [1_K_i], Theta_i; Sec. 2.1.4-2.1.5).
  *   holder, cutter : HOST uint8 arrays [tz][ty][tx], nonzero = inside; copied.
  *   sharp_mask     : HOST uint8 [tz][ty][tx] subset of the cutter used as sharp points, or
- *                    NULL for every cutter voxel; resampled like the cutter.
+ *                    NULL for the handle's sharp_sampling rule (every cutter voxel by
+ *                    default); resampled like the cutter.
  *   origin         : tool-frame origin voxel (x, y, z); rotations are about it.
  *   quats          : HOST double [n_orient][4] unit quaternions (w, x, y, z).
  * Resamples the tool on the device, builds the conjugated FFT spectra of every orientation
@@ -173,6 +186,34 @@ imf_status imf_penalize_sensitivity(imf_handle h, float *sens, const float *rho_
 imf_status imf_penalize_sensitivity_noalloc(float *sens, const float *rho_omega, const float *imf_bar,
                                             const uint8_t *secluded, const uint8_t *fixture, long n,
                                             double w_acc, double tau, void *cuda_stream);
+
+/*
+ * Per-orientation accessible sets for machining process planning (Sec. 3.4.1). Runs
+ * imf_compute (outputs as there; the accessible set is built by the sweep of Eq. eq_conv_A) and
+ * also stores every orientation's own accessible set A_{i,R} before the union of Eq. eq_A_multi:
+ *   sets : DEVICE uint32 [n][nz][ny][(nx + 31) / 32], n = total orientations of all tools in
+ *          tool order and, within a tool, the caller's orientation order; bit x & 31 of word
+ *          x >> 5 of row (y, z) is A_{i,R}(x, y, z). Fixture cells are not masked. Caller-owned;
+ *          cleared and written asynchronously on cuda_stream.
+ * Errors: as imf_compute; IMF_ERR_INVALID_ARG for a NULL sets pointer. */
+imf_status imf_compute_accessible_sets(imf_handle h, const float *rho_omega, const uint8_t *fixture, float *imf_bar,
+                                       uint8_t *secluded, uint32_t *sets, void *cuda_stream);
+
+/*
+ * Greedy machining process plan (Sec. 3.4.1): the negative space N = Omega_0 and [rho <= tau]
+ * (the cells to machine away from the design domain) is removed step by step; each step picks
+ * the oriented tool whose accessible set covers the most of what is left of N (ties: the lowest
+ * index) and removes that part, until N is empty, no set covers any of the rest, or max_steps.
+ *   sets       : DEVICE, as written by imf_compute_accessible_sets (n_sets of them).
+ *   rho_omega, fixture (or NULL): DEVICE, the final design, as in imf_compute.
+ *   order, removed : HOST int / int64 [max_steps]: set index and voxels removed per step.
+ *   n_steps    : HOST out, steps taken; negative / left (or NULL): HOST out, |N| and the
+ *                voxels no set can reach (inaccessible negative space).
+ * Synchronous (one count per step is read back). Uses handle-owned scratch (grown on demand).
+ * Errors: IMF_ERR_INVALID_ARG (NULL, n_sets < 1, max_steps < 0), IMF_ERR_OOM, IMF_ERR_CUDA. */
+imf_status imf_process_plan(imf_handle h, const uint32_t *sets, int n_sets, const float *rho_omega,
+                            const uint8_t *fixture, int max_steps, int *order, long long *removed, int *n_steps,
+                            long long *negative, long long *left, void *cuda_stream);
 
 /*
  * Batched and served forms (not in the paper; they reshape how Alg. 1 is launched).

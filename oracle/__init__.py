@@ -17,5 +17,5 @@ geometry ("parity unpinned" for that use only; the penalty formula itself is pin
 """
 from .ref import (  # noqa: F401
     quat_to_matrix, rotate_indicator, resample_tool, collision, sweep, erode, imf, imf_subblock, finalize,
-    penalize, point_query, rho_obstacle, lib,
+    penalize, point_query, rho_obstacle, sharp_sample, process_plan, lib,
 )

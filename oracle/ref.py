@@ -133,6 +133,33 @@ def resample_tool(tool, q) -> dict:
 # the per-orientation definitions
 # ----------------------------------------------------------------------------------------
 
+def sharp_sample(cutter, origin, mode: str, k: int = 1) -> np.ndarray:
+    """Sharp-point sample of a cutter array [tz][ty][tx] in the tool frame (Sec. 2.1.5: the
+    cutter boundary may be sampled more or less densely; App. B: down to O(1) representative
+    points). mode "all": every cutter voxel; "boundary": cutter voxels with at least one of the
+    six face neighbours outside the cutter (or outside the array); "nearest": the k boundary
+    voxels with the smallest squared distance to the tool origin (x, y, z), ties broken by the
+    C-order index. Returns a uint8 mask."""
+    K = np.asarray(cutter) != 0
+    if mode == "all":
+        return K.astype(np.uint8)
+    P = np.pad(K, 1, constant_values=False)
+    inner = (P[:-2, 1:-1, 1:-1] & P[2:, 1:-1, 1:-1] & P[1:-1, :-2, 1:-1] & P[1:-1, 2:, 1:-1] &
+             P[1:-1, 1:-1, :-2] & P[1:-1, 1:-1, 2:])
+    B = K & ~inner
+    if mode == "boundary":
+        return B.astype(np.uint8)
+    if mode != "nearest":
+        raise ValueError(mode)
+    z, y, x = np.nonzero(B)
+    d2 = (x - origin[0]) ** 2 + (y - origin[1]) ** 2 + (z - origin[2]) ** 2
+    lin = np.ravel_multi_index((z, y, x), K.shape)
+    order = np.lexsort((lin, d2))[:k]
+    out = np.zeros(K.shape, np.uint8)
+    out[z[order], y[order], x[order]] = 1
+    return out
+
+
 def rho_obstacle(rho, fixture) -> np.ndarray:
     """rho_O = min(1, rho_Omega + 1_F) in FP64 (Alg. 1 "implicit union", Eq. eq_imf_4)."""
     r = np.asarray(rho, np.float64)
@@ -316,3 +343,23 @@ def imf_subblock(design, x0, ext, theta_rel: float = 0.01):
             if len(rs["sharp"]):
                 f = np.minimum(f, erode(g, tlo_rel, rs["sharp"], shape))
     return f, A.astype(np.uint8)
+
+
+def process_plan(sets, negative, max_steps=None):
+    """Greedy machining process plan (Sec. 3.4.1): starting from the whole negative space N
+    (a boolean grid), each step takes the oriented tool whose accessible set (one boolean grid
+    per orientation, `sets`) covers the most of what is left of N, lowest index on ties, and
+    removes that part; it stops when N is empty or no set covers any of the rest. Returns
+    ([(set index, voxels removed), ...], |N|, voxels left)."""
+    rem = np.asarray(negative, bool).copy()
+    total = int(rem.sum())
+    steps = []
+    limit = len(sets) if max_steps is None else max_steps
+    while rem.any() and len(steps) < limit:
+        counts = [int(np.count_nonzero(np.asarray(s, bool) & rem)) for s in sets]
+        best = int(np.argmax(counts))
+        if counts[best] == 0:
+            break
+        steps.append((best, counts[best]))
+        rem &= ~np.asarray(sets[best], bool)
+    return steps, total, int(rem.sum())

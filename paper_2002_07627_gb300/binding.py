@@ -17,6 +17,7 @@ IMF_OK = 0
 STATUS_NAMES = {0: "IMF_OK", 1: "IMF_ERR_INVALID_ARG", 2: "IMF_ERR_OOM", 3: "IMF_ERR_CUDA",
                 4: "IMF_ERR_TIMEOUT", 5: "IMF_ERR_NOT_READY", 6: "IMF_ERR_BUDGET", 7: "IMF_ERR_OVERFLOW"}
 IMF_AUTO, IMF_FP32_FFT, IMF_BF16_DIRECT = 0, 1, 2
+IMF_SHARP_ALL, IMF_SHARP_BOUNDARY, IMF_SHARP_NEAREST = 0, 1, 2
 
 # every symbol include/imf.h declares
 EXPORTS = ["imf_default_options", "imf_create", "imf_set_tool", "imf_compute", "imf_compute_host",
@@ -24,7 +25,8 @@ EXPORTS = ["imf_default_options", "imf_create", "imf_set_tool", "imf_compute", "
            "imf_get_tool_info", "imf_get_offsets", "imf_set_debug", "imf_get_last_g", "imf_get_stats",
            "imf_set_profiling", "imf_get_kernel_time", "imf_reset_kernel_times",
            "imf_penalize_sensitivity_noalloc", "imf_capture_graph", "imf_launch_graph", "imf_autotune",
-           "imf_set_path", "imf_selftest_mma", "imf_get_last_bits", "imf_footprint"]
+           "imf_set_path", "imf_selftest_mma", "imf_get_last_bits", "imf_footprint",
+           "imf_compute_accessible_sets", "imf_process_plan"]
 
 
 class ImfOptions(ctypes.Structure):
@@ -34,7 +36,8 @@ class ImfOptions(ctypes.Structure):
                 ("recheck_band", ctypes.c_double), ("orient_batch", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("erode_groups", ctypes.c_int),
                 ("fft_stages_only", ctypes.c_int), ("accessible_by_sweep", ctypes.c_int),
-                ("separate_yx_passes", ctypes.c_int), ("plan_only", ctypes.c_int)]
+                ("separate_yx_passes", ctypes.c_int), ("plan_only", ctypes.c_int),
+                ("sharp_sampling", ctypes.c_int), ("sharp_k", ctypes.c_int)]
 
 
 class ImfToolInfo(ctypes.Structure):
@@ -87,6 +90,10 @@ def load(path: str | None = None):
     L.imf_get_last_bits.argtypes = [H, I, P, Lg, ctypes.POINTER(I)]
     L.imf_get_stats.argtypes = [H, ctypes.POINTER(ImfStats)]
     L.imf_footprint.argtypes = [H, I, ctypes.POINTER(ImfFootprint)]
+    L.imf_compute_accessible_sets.argtypes = [H, P, P, P, P, P, P]
+    LL = ctypes.c_longlong
+    L.imf_process_plan.argtypes = [H, P, I, P, P, I, P, P, ctypes.POINTER(I), ctypes.POINTER(LL),
+                                   ctypes.POINTER(LL), P]
     L.imf_set_profiling.argtypes = [H, I]
     L.imf_get_kernel_time.argtypes = [H, I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(D),
                                       ctypes.POINTER(Lg)]
@@ -162,7 +169,8 @@ class Imf:
 
     def __init__(self, shape_zyx, lam=0.01, tau=0.5, theta_rel=0.01, precision=IMF_AUTO, recheck=True,
                  recheck_band=0.0, orient_batch=0, hbm_budget_bytes=0, voxel=1.0, erode_groups=0, fft_stages_only=False,
-                 accessible_by_sweep=False, separate_yx_passes=False, plan_only=False):
+                 accessible_by_sweep=False, separate_yx_passes=False, plan_only=False, sharp_sampling=IMF_SHARP_ALL,
+                 sharp_k=1):
         self.lib = load()
         opt = ImfOptions()
         self.lib.imf_default_options(ctypes.byref(opt))
@@ -176,6 +184,7 @@ class Imf:
         opt.accessible_by_sweep = int(accessible_by_sweep)
         opt.separate_yx_passes = int(separate_yx_passes)
         opt.plan_only = int(plan_only)
+        opt.sharp_sampling, opt.sharp_k = int(sharp_sampling), int(sharp_k)
         self.shape = (nz, ny, nx)
         self.opt = opt
         h = ctypes.c_void_p()
@@ -217,6 +226,7 @@ class Imf:
     def set_tools(self, tools):
         for i, t in enumerate(tools):
             self.set_tool(i, t.holder, t.cutter, t.origin, t.quats, getattr(t, "sharp", None))
+        self.n_tools = len(tools)
 
     # --- compute (torch CUDA tensors)
     def compute(self, rho, fixture=None, fbar=None, secluded=None, raw=None, accessible=None, stream=None):
@@ -251,6 +261,37 @@ class Imf:
         self._check(self.lib.imf_penalize_sensitivity(self.h, _ptr(sens), _ptr(rho), _ptr(fbar), _ptr(secluded),
                                                       _ptr(fixture), float(w_acc), s))
         return sens
+
+    def accessible_sets(self, rho, fixture=None, stream=None):
+        """Per-orientation accessible sets (imf_compute_accessible_sets) as a uint32 tensor
+        [n_orient_total][nz][ny][(nx + 31) // 32]; also returns f_bar and Gamma."""
+        import torch
+        nz, ny, nx = self.shape
+        n = sum(self.tool_info(i).n_orient for i in range(self.n_tools))
+        sets = torch.empty((n, nz, ny, (nx + 31) // 32), dtype=torch.int32, device=rho.device)
+        fbar = torch.empty_like(rho)
+        sec = torch.empty(rho.shape, dtype=torch.uint8, device=rho.device)
+        s = (stream or torch.cuda.current_stream(rho.device)).cuda_stream
+        self._check(self.lib.imf_compute_accessible_sets(self.h, _ptr(rho), _ptr(fixture), _ptr(fbar), _ptr(sec),
+                                                         _ptr(sets), s))
+        return sets, fbar, sec
+
+    def process_plan(self, sets, rho, fixture=None, max_steps=None, stream=None):
+        """Greedy process plan (imf_process_plan): list of (set index, voxels removed), |N| and
+        the inaccessible rest."""
+        import torch
+        n_sets = int(sets.shape[0])
+        max_steps = n_sets if max_steps is None else int(max_steps)
+        order = np.zeros(max(1, max_steps), np.int32)
+        removed = np.zeros(max(1, max_steps), np.int64)
+        n_steps = ctypes.c_int()
+        neg, left = ctypes.c_longlong(), ctypes.c_longlong()
+        s = (stream or torch.cuda.current_stream(rho.device)).cuda_stream
+        self._check(self.lib.imf_process_plan(self.h, _ptr(sets), n_sets, _ptr(rho), _ptr(fixture), max_steps,
+                                              order.ctypes.data, removed.ctypes.data, ctypes.byref(n_steps),
+                                              ctypes.byref(neg), ctypes.byref(left), s))
+        k = n_steps.value
+        return list(zip(order[:k].tolist(), removed[:k].tolist())), neg.value, left.value
 
     def capture_graph(self, rho, fixture, fbar, secluded, raw=None, accessible=None, stream=None):
         """Record one compute with these exact tensors into a replayable CUDA graph."""

@@ -35,12 +35,13 @@ namespace {
 enum KernelId {
     KID_ROTATE, KID_SPEC, KID_RFFT_FWD, KID_AXIS_FWD, KID_AXIS_INV_MUL, KID_AXIS_INV, KID_IRFFT_THRESH,
     KID_RECHECK, KID_SWEEP, KID_ERODE, KID_INIT, KID_MAX, KID_FINALIZE, KID_ABSMAX, KID_PENALIZE, KID_RHO_HL,
-    KID_DIRECT, KID_SWEEP_LEVELS, KID_YX, KID_COUNT
+    KID_DIRECT, KID_SWEEP_LEVELS, KID_YX, KID_PLAN, KID_COUNT
 };
 const char *kKernelNames[KID_COUNT] = {
     "rotate_resample", "tool_spectrum", "rfft_x_fwd", "fft_axis_fwd", "fft_z_inv_mul", "fft_y_inv",
     "irfft_x_threshold", "recheck_near_threshold", "sweep_dilate", "erode_min", "init", "max_omega0",
-    "finalize", "absmax_omega0", "penalize", "rho_hi_lo", "direct_corr_tcgen05", "sweep_levels", "fft_yx_inv_threshold"};
+    "finalize", "absmax_omega0", "penalize", "rho_hi_lo", "direct_corr_tcgen05", "sweep_levels", "fft_yx_inv_threshold",
+    "process_plan"};
 
 struct Tool {
     bool set = false;
@@ -67,6 +68,7 @@ struct Tool {
     int erode_bps = 1;                   // resident erosion blocks per SM
     long n_rt = 0, n_rk = 0, n_sh = 0;
     std::vector<int> perm, iperm;        // internal orientation order -> caller's index, and back
+    int *perm_dev = nullptr;             // perm on the device (per-orientation outputs)
     int path = IMF_FP32_FFT;             // collision path in use
     bool sharp_is_cutter = true;         // sharp points = every cutter voxel (no proper subset)
     bool has_spec = false;               // FFT spectra built
@@ -134,6 +136,13 @@ struct imf_handle_s {
     // captured graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    // per-orientation accessible sets (imf_compute_accessible_sets): bits of all orientations
+    uint32_t *aset = nullptr;
+    long aset_so = 0;
+    // greedy process plan work buffers
+    uint32_t *plan_rem = nullptr;
+    unsigned long long *plan_cnt = nullptr;
+    size_t plan_rem_n = 0, plan_cnt_n = 0;
     // debug
     bool keep_g = false;
     bool run_sweep = true;      // this compute builds A by the sweep (else A = [f <= theta])
@@ -300,6 +309,38 @@ void rotate_host(const uint8_t *T, const uint8_t *K, const uint8_t *S, int tx, i
     }
 }
 
+// Sharp-point sampling of the cutter (Sec. 2.1.5 remark on sampling the cutter boundary; App. B
+// on n_K = O(1) representative points), in the tool frame before rotation: IMF_SHARP_BOUNDARY
+// keeps the cutter voxels with a face neighbour outside the cutter (or outside the array);
+// IMF_SHARP_NEAREST keeps the k boundary voxels nearest the tool origin (squared distance, ties
+// by linear index), so the sets for growing k are nested. Fewer sharp points can only raise the
+// IMF (a conservative approximation).
+void sample_sharp_points(const std::vector<uint8_t> &K, int tx, int ty, int tz, const int *o, int mode, int k,
+                         std::vector<uint8_t> &S)
+{
+    auto in = [&](int x, int y, int z) {
+        return x >= 0 && y >= 0 && z >= 0 && x < tx && y < ty && z < tz && K[((long)z * ty + y) * tx + x];
+    };
+    std::vector<std::pair<long, long>> cand;   // (squared distance to the origin, linear index)
+    std::fill(S.begin(), S.end(), 0);
+    for (int z = 0; z < tz; ++z)
+        for (int y = 0; y < ty; ++y)
+            for (int x = 0; x < tx; ++x) {
+                if (!in(x, y, z)) continue;
+                const bool surf = !in(x - 1, y, z) || !in(x + 1, y, z) || !in(x, y - 1, z) || !in(x, y + 1, z) ||
+                                  !in(x, y, z - 1) || !in(x, y, z + 1);
+                if (!surf) continue;
+                const long id = ((long)z * ty + y) * tx + x;
+                if (mode == IMF_SHARP_BOUNDARY) S[id] = 1;
+                const long dx = x - o[0], dy = y - o[1], dz = z - o[2];
+                cand.push_back({dx * dx + dy * dy + dz * dz, id});
+            }
+    if (mode == IMF_SHARP_NEAREST) {
+        std::sort(cand.begin(), cand.end());
+        for (size_t i = 0; i < cand.size() && (long)i < (long)k; ++i) S[cand[i].second] = 1;
+    }
+}
+
 // Scan box of the rotated array: the tool's voxel cubes rotate into the hull of the rotated
 // corners of its voxel-edge box; one voxel of margin on every side.
 void scan_box(const double *R, int tx, int ty, int tz, const int *o, int *box)
@@ -353,6 +394,7 @@ void free_tool(imf_handle h, Tool &t)
     dfree(h, t.er_runs);
     dfree(h, t.d_taps);
     dfree(h, t.d_bmat);
+    dfree(h, t.perm_dev);
     t = Tool();
 }
 
@@ -600,6 +642,8 @@ void imf_default_options(imf_options *opt)
     opt->accessible_by_sweep = 0;
     opt->separate_yx_passes = 0;
     opt->plan_only = 0;
+    opt->sharp_sampling = IMF_SHARP_ALL;
+    opt->sharp_k = 1;
 }
 
 imf_status imf_create(const imf_options *opt, imf_handle *out)
@@ -614,6 +658,8 @@ imf_status imf_create(const imf_options *opt, imf_handle *out)
         return IMF_ERR_INVALID_ARG;
     if (opt->precision < IMF_AUTO || opt->precision > IMF_BF16_DIRECT) return IMF_ERR_INVALID_ARG;
     if (opt->erode_groups < 0) return IMF_ERR_INVALID_ARG;
+    if (opt->sharp_sampling < IMF_SHARP_ALL || opt->sharp_sampling > IMF_SHARP_NEAREST) return IMF_ERR_INVALID_ARG;
+    if (opt->sharp_sampling == IMF_SHARP_NEAREST && opt->sharp_k < 1) return IMF_ERR_INVALID_ARG;
     imf_handle h = new (std::nothrow) imf_handle_s();
     if (!h) return IMF_ERR_OOM;
     h->opt = *opt;
@@ -638,6 +684,8 @@ void imf_destroy(imf_handle h)
     dfree(h, h->A, 0);
     dfree(h, h->flags, (size_t)h->flag_cap);
     dfree(h, h->dev_small, 8);
+    dfree(h, h->plan_rem);
+    dfree(h, h->plan_cnt);
     for (float **p : {&h->h_rho, &h->h_fbar, &h->h_raw}) dfree(h, *p, 0);
     for (uint8_t **p : {&h->h_fix, &h->h_sec, &h->h_acc}) dfree(h, *p, 0);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
@@ -675,6 +723,8 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
         nT += T[i];
     }
     if (nK == 0) return fail(h, IMF_ERR_INVALID_ARG, "empty cutter");
+    if (!sharp_mask && h->opt.sharp_sampling != IMF_SHARP_ALL)
+        sample_sharp_points(K, tx, ty, tz, origin, h->opt.sharp_sampling, h->opt.sharp_k, S);
     bool sharp_all = true;
     for (long i = 0; i < tv; ++i) sharp_all = sharp_all && S[i] == K[i];
     for (int i = 0; i < n_orient; ++i) {
@@ -896,7 +946,7 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
                     vbytes((size_t)t.P[2], 8) + vbytes(rto.size(), 4) + vbytes(rts.size(), 4) +
                     vbytes(ivv.size(), sizeof(int4)) + vbytes(ivst.size(), 4) +
                     vbytes(chunks.size(), sizeof(ErodeChunk)) + vbytes(chst.size(), 4) +
-                    vbytes(eruns.size(), sizeof(int2));
+                    vbytes(eruns.size(), sizeof(int2)) + vbytes(t.perm.size(), 4);
     if (!plan_only) {
         twiddles(t.M, t.M, t.M, tw);
         if ((st = upload(h, &t.twM, tw))) return bail(st);
@@ -909,7 +959,7 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
         if ((st = upload(h, &t.rt_off, rto)) || (st = upload(h, &t.rt_start, rts)) ||
             (st = upload(h, &t.sw_pairs, ivv)) || (st = upload(h, &t.sw_start, ivst)) ||
             (st = upload(h, &t.er_chunks, chunks)) || (st = upload(h, &t.er_chunk_start, chst)) ||
-            (st = upload(h, &t.er_runs, eruns)))
+            (st = upload(h, &t.er_runs, eruns)) || (st = upload(h, &t.perm_dev, t.perm)))
             return bail(st);
     }
     // --- direct tensor-core path: groups, union taps, B matrices
@@ -1003,6 +1053,13 @@ imf_status tail_batch(imf_handle h, const Tool &t, const float *rho, const uint8
         a.bits = h->bits; a.lstride = lstride; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
         a.pairs = t.sw_pairs; a.pair_start = t.sw_start; a.nx = op.nx; a.ny = op.ny; a.nz = op.nz;
         a.awords = h->awords; a.orient_base = o0; a.nb = nb; a.A = h->A;
+        if (h->aset) {
+            long base = 0;
+            for (int i = 0; i < h->n_tools && &h->tools[i] != &t; ++i) base += h->tools[i].n_orient;
+            a.A_per = h->aset + base * h->aset_so;
+            a.a_per_so = h->aset_so;
+            a.perm = t.perm_dev;
+        }
         Launch L(h, KID_SWEEP, s);
         launch_sweep(a, s);
     }
@@ -1052,7 +1109,7 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
     // the accessible output: from the minimum when that is exact (one tool, sharp points = the
     // whole cutter), else by the sweep; neither when the caller does not ask for it
     const bool acc_from_f = acc && !op.accessible_by_sweep && h->n_tools == 1 && h->tools[0].sharp_is_cutter;
-    h->run_sweep = acc && !acc_from_f;
+    h->run_sweep = (acc && !acc_from_f) || h->aset != nullptr;
     if (h->run_sweep) CU(cudaMemsetAsync(h->A, 0, sizeof(uint32_t) * (size_t)op.nz * op.ny * h->awords, s));
     CU(cudaMemsetAsync(maxbits, 0, sizeof(unsigned), s));
     CU(cudaMemsetAsync(h->dev_small + 4, 0, sizeof(int), s));
@@ -1222,6 +1279,98 @@ imf_status imf_penalize_sensitivity(imf_handle h, float *sens, const float *rho_
         launch_penalize(sens, rho_omega, imf_bar, secluded, N, mb, w_acc, h->opt.tau, s);
     }
     CU(cudaGetLastError());
+    return IMF_OK;
+}
+
+imf_status imf_compute_accessible_sets(imf_handle h, const float *rho_omega, const uint8_t *fixture, float *imf_bar,
+                                       uint8_t *secluded, uint32_t *sets, void *cuda_stream)
+{
+    if (!h) return IMF_ERR_INVALID_ARG;
+    if (!sets) return fail(h, IMF_ERR_INVALID_ARG, "NULL sets");
+    const long words = (long)h->opt.nz * h->opt.ny * ((h->opt.nx + 31) / 32);
+    long n = 0;
+    for (int i = 0; i < h->n_tools; ++i) n += h->tools[i].n_orient;
+    h->aset = sets;
+    h->aset_so = words;
+    // every word of every set is written by the sweep; clearing first keeps orientations whose
+    // cutter vanishes (no runs) empty
+    cudaError_t e = cudaMemsetAsync(sets, 0, (size_t)std::max<long>(n, 1) * words * sizeof(uint32_t),
+                                    (cudaStream_t)cuda_stream);
+    imf_status st = e == cudaSuccess ? imf_compute(h, rho_omega, fixture, imf_bar, secluded, nullptr, nullptr, cuda_stream)
+                                     : fail(h, IMF_ERR_CUDA, "clearing the sets: %s", cudaGetErrorString(e));
+    h->aset = nullptr;
+    h->aset_so = 0;
+    return st;
+}
+
+imf_status imf_process_plan(imf_handle h, const uint32_t *sets, int n_sets, const float *rho_omega,
+                            const uint8_t *fixture, int max_steps, int *order, long long *removed, int *n_steps,
+                            long long *negative, long long *left, void *cuda_stream)
+{
+    if (!h) return IMF_ERR_INVALID_ARG;
+    if (!sets || !rho_omega || !order || !removed || !n_steps) return fail(h, IMF_ERR_INVALID_ARG, "NULL argument");
+    if (n_sets < 1 || max_steps < 0) return fail(h, IMF_ERR_INVALID_ARG, "n_sets %d / max_steps %d", n_sets, max_steps);
+    const imf_options &op = h->opt;
+    const long awords = (op.nx + 31) / 32;
+    const long words = (long)op.nz * op.ny * awords;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if ((size_t)words > h->plan_rem_n) {
+        dfree(h, h->plan_rem);
+        h->plan_rem_n = 0;
+        TRY(dalloc(h, &h->plan_rem, (size_t)words));
+        h->plan_rem_n = (size_t)words;
+    }
+    if ((size_t)n_sets + 1 > h->plan_cnt_n) {
+        dfree(h, h->plan_cnt);
+        h->plan_cnt_n = 0;
+        TRY(dalloc(h, &h->plan_cnt, (size_t)n_sets + 1));
+        h->plan_cnt_n = (size_t)n_sets + 1;
+    }
+    h->last_stream = s;
+    h->used_stream = true;
+    {
+        Launch L(h, KID_PLAN, s);
+        launch_plan_init(rho_omega, fixture, op.nx, op.ny, op.nz, (int)awords, op.tau, h->plan_rem, s);
+    }
+    std::vector<unsigned long long> cnt(n_sets);
+    auto counts = [&]() -> imf_status {
+        CU(cudaMemsetAsync(h->plan_cnt, 0, sizeof(unsigned long long) * n_sets, s));
+        {
+            Launch L(h, KID_PLAN, s);
+            launch_plan_count(sets, words, n_sets, h->plan_rem, h->plan_cnt, s);
+        }
+        CU(cudaMemcpyAsync(cnt.data(), h->plan_cnt, sizeof(unsigned long long) * n_sets, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        return IMF_OK;
+    };
+    // size of the negative space: popcount(remaining & remaining), in the counter after the sets'
+    unsigned long long total = 0;
+    CU(cudaMemsetAsync(h->plan_cnt + n_sets, 0, sizeof total, s));
+    {
+        Launch L(h, KID_PLAN, s);
+        launch_plan_count(h->plan_rem, words, 1, h->plan_rem, h->plan_cnt + n_sets, s);
+    }
+    CU(cudaMemcpyAsync(&total, h->plan_cnt + n_sets, sizeof total, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    unsigned long long rest = total;
+    int k = 0;
+    while (k < max_steps && rest > 0) {
+        TRY(counts());
+        int best = 0;
+        for (int i = 1; i < n_sets; ++i)
+            if (cnt[i] > cnt[best]) best = i;
+        if (cnt[best] == 0) break;
+        order[k] = best;
+        removed[k] = (long long)cnt[best];
+        rest -= cnt[best];
+        ++k;
+        Launch L(h, KID_PLAN, s);
+        launch_plan_remove(sets + (long)best * words, words, h->plan_rem, s);
+    }
+    CU(cudaStreamSynchronize(s));
+    *n_steps = k;
+    if (negative) *negative = (long long)total;
+    if (left) *left = (long long)rest;
     return IMF_OK;
 }
 

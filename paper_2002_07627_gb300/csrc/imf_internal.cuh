@@ -152,9 +152,24 @@ struct SweepArgs {
     int nx, ny, nz, awords;
     int orient_base, nb;
     uint32_t *A;                 // accessible bits [nz][ny][awords], OR-accumulated
+    // optional per-orientation sets: A_R of internal orientation og is stored (not OR-ed) at
+    // A_per + perm[og] * a_per_so (the caller's orientation index), or nothing when NULL
+    uint32_t *A_per;
+    long a_per_so;
+    const int *perm;
 };
 void launch_sweep_levels(const SweepLevelsArgs &a, cudaStream_t s);
 void launch_sweep(const SweepArgs &a, cudaStream_t s);
+
+// Greedy machining process plan (Sec. 3.4.1) over per-orientation accessible sets.
+// remaining[w] = bits of the negative space Omega_0 and [rho <= tau] in word w of [nz][ny][awords]
+void launch_plan_init(const float *rho, const uint8_t *fix, int nx, int ny, int nz, int awords, double tau,
+                      uint32_t *remaining, cudaStream_t s);
+// counts[s] += popcount(sets[s] & remaining) for s < n_sets (counts zeroed by the caller)
+void launch_plan_count(const uint32_t *sets, long set_words, int n_sets, const uint32_t *remaining,
+                       unsigned long long *counts, cudaStream_t s);
+// remaining &= ~sets[pick]
+void launch_plan_remove(const uint32_t *set, long words, uint32_t *remaining, cudaStream_t s);
 
 
 // Tiled minimum over sharp points: erode.cuh.

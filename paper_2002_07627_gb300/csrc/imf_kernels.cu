@@ -123,9 +123,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a)
         uint32_t *dstw = a.A + ((long)z * a.ny + y) * a.awords + q;
         const int rem = a.nx - 32 * q;
         const uint32_t full = rem < 32 ? (1u << rem) - 1u : 0xffffffffu;
-        // A only grows: words already fully accessible need no more work
+        // A only grows: words already fully accessible need no more work (unless this
+        // orientation's own set is wanted, which starts empty)
         const uint32_t old = live ? *dstw : full;
-        uint32_t acc = old;
+        const bool per = a.A_per != nullptr;
+        uint32_t acc = per ? 0u : old;
         for (int c0 = m0; c0 < m1; c0 += kSweepStage) {
             const int cn = min(kSweepStage, m1 - c0);
             __syncthreads();
@@ -142,8 +144,55 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a)
         if (live) {
             const uint32_t add = acc & full & ~old;
             if (add) atomicOr(dstw, add);
+            if (per) a.A_per[(long)a.perm[og] * a.a_per_so + ((long)z * a.ny + y) * a.awords + q] = acc & full;
         }
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// Greedy process plan (Sec. 3.4.1): the negative space as bits, the part of it each
+// orientation's accessible set covers, and its removal.
+// ---------------------------------------------------------------------------------------
+__global__ void plan_init_kernel(const float *rho, const uint8_t *fix, int nx, int ny, int nz, int awords,
+                                 float tau, uint32_t *rem)
+{
+    const long total = (long)awords * ny * nz;
+    for (long w = blockIdx.x * (long)blockDim.x + threadIdx.x; w < total; w += (long)gridDim.x * blockDim.x) {
+        const int q = (int)(w % awords);
+        const long row = w / awords;
+        uint32_t bits = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int x = 32 * q + b;
+            if (x >= nx) break;
+            const long idx = row * nx + x;
+            if (!(fix && fix[idx]) && rho[idx] <= tau) bits |= 1u << b;
+        }
+        rem[w] = bits;
+    }
+}
+
+__global__ void __launch_bounds__(256) plan_count_kernel(const uint32_t *sets, long set_words, const uint32_t *rem,
+                                                         unsigned long long *counts)
+{
+    __shared__ unsigned long long part[8];
+    const uint32_t *s = sets + (long)blockIdx.y * set_words;
+    unsigned long long c = 0;
+    for (long w = blockIdx.x * (long)blockDim.x + threadIdx.x; w < set_words; w += (long)gridDim.x * blockDim.x)
+        c += __popc(s[w] & rem[w]);
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += part[i];
+        if (t) atomicAdd(counts + blockIdx.y, t);
+    }
+}
+
+__global__ void plan_remove_kernel(const uint32_t *set, long words, uint32_t *rem)
+{
+    for (long w = blockIdx.x * (long)blockDim.x + threadIdx.x; w < words; w += (long)gridDim.x * blockDim.x)
+        rem[w] &= ~set[w];
 }
 
 // Block-per-point variant of the re-check: 256 threads split the tool voxels of one flagged
@@ -304,6 +353,25 @@ void launch_sweep(const SweepArgs &a, cudaStream_t s)
 {
     dim3 grid(blocks_for((long)a.awords * a.ny * a.nz, kThreads, 152 * 4), a.nb);
     sweep_kernel<<<grid, kThreads, 0, s>>>(a);
+}
+
+void launch_plan_init(const float *rho, const uint8_t *fix, int nx, int ny, int nz, int awords, double tau,
+                      uint32_t *remaining, cudaStream_t s)
+{
+    plan_init_kernel<<<blocks_for((long)awords * ny * nz), kThreads, 0, s>>>(rho, fix, nx, ny, nz, awords, (float)tau,
+                                                                            remaining);
+}
+
+void launch_plan_count(const uint32_t *sets, long set_words, int n_sets, const uint32_t *remaining,
+                       unsigned long long *counts, cudaStream_t s)
+{
+    dim3 grid(blocks_for(set_words, 256, 152 * 2), n_sets);
+    plan_count_kernel<<<grid, 256, 0, s>>>(sets, set_words, remaining, counts);
+}
+
+void launch_plan_remove(const uint32_t *set, long words, uint32_t *remaining, cudaStream_t s)
+{
+    plan_remove_kernel<<<blocks_for(words), kThreads, 0, s>>>(set, words, remaining);
 }
 
 void launch_recheck_blocks(const RecheckArgs &a, int max_points, cudaStream_t s)

@@ -528,3 +528,93 @@ def test_orientation_order_does_not_change_the_result():
         b = run_gpu(d, orient_batch=4, **kw)
         for k in ("f", "fbar", "secluded", "accessible"):
             assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("mode,k", [("boundary", 1), ("nearest", 1), ("nearest", 6)])
+def test_sharp_sampling_modes_match_oracle(mode, k):
+    """The library's sharp-point sampling options (Sec. 2.1.5 sampling remark; App. B, O(1)
+    representative points) against the oracle given the oracle's own sample of the cutter: the
+    resampled sharp sets are identical for every orientation and the IMF meets the contract."""
+    import dataclasses
+    from paper_2002_07627_gb300 import binding
+    d = _small3d(seed=12, n=(30, 28, 26), n_orient=6)
+    tool = d.tools[0]
+    mask = oracle.sharp_sample(tool.cutter, tool.origin, mode, k)
+    sampled = dataclasses.replace(tool, sharp=mask)
+    ref_design = synth.Design(d.rho, d.fixture, [sampled])
+    ref = oracle_ref(ref_design)
+    mode_id = {"boundary": binding.IMF_SHARP_BOUNDARY, "nearest": binding.IMF_SHARP_NEAREST}[mode]
+    got = run_gpu(d, sharp_sampling=mode_id, sharp_k=k, orient_batch=4)
+    for r, q in enumerate(tool.quats):
+        want = sorted(map(tuple, oracle.resample_tool(sampled, q)["sharp"].tolist()))
+        have = sorted(map(tuple, got["imf"].offsets(0, r, 2).tolist()))
+        assert have == want, r
+    check_against_oracle(ref_design, got, ref)
+
+
+def test_sharp_sampling_is_conservative_and_monotone():
+    """Fewer sharp points can only raise the IMF (Sec. 2.1.5): on one plan (same padded grid,
+    same collision fields) f(all) <= f(boundary) <= f(16 nearest) <= f(4 nearest) <= f(1 nearest)
+    pointwise and exactly, the secluded set can only shrink along the chain, and the accessible
+    set (a sweep by the whole cutter) does not depend on the sampling."""
+    from paper_2002_07627_gb300 import binding
+    d = _small3d(seed=13, n=(34, 30, 28), n_orient=7)
+    chain = [(binding.IMF_SHARP_ALL, 1), (binding.IMF_SHARP_BOUNDARY, 1), (binding.IMF_SHARP_NEAREST, 16),
+             (binding.IMF_SHARP_NEAREST, 4), (binding.IMF_SHARP_NEAREST, 1)]
+    res = [run_gpu(d, sharp_sampling=m, sharp_k=k, orient_batch=4, accessible_by_sweep=True) for m, k in chain]
+    om = d.fixture == 0
+    for a, b in zip(res, res[1:]):
+        assert a["imf"].tool_info(0).P == b["imf"].tool_info(0).P
+        assert np.all(a["f"][om] <= b["f"][om])
+        assert np.array_equal(a["accessible"], b["accessible"])
+    assert np.any(res[0]["f"][om] < res[-1]["f"][om])
+    n_sharp = [r["imf"].tool_info(0).n_sharp for r in res]
+    assert n_sharp == sorted(n_sharp, reverse=True) and n_sharp[-1] == 7
+
+
+def _unpack_sets(sets, shape):
+    nz, ny, nx = shape
+    w = sets.cpu().numpy().view(np.uint32)
+    bits = np.unpackbits(w.view(np.uint8).reshape(w.shape[0], nz, ny, -1), axis=-1, bitorder="little")
+    return bits[..., :nx].astype(bool)
+
+
+def test_accessible_sets_and_greedy_process_plan_match_oracle():
+    """Per-orientation accessible sets (Eq. eq_conv_A per orientation) and the greedy machining
+    process plan of Sec. 3.4.1 on a binary design: g is an integer there, and theta sits half a
+    voxel between integers, so every translation is classified exactly (farther than the
+    1e-3 |T| band from theta) and both the sets and the plan must equal the oracle's bit for
+    bit and step for step; two tools, so the set index runs over both tools' orientations."""
+    binding = _gpu()
+    rho = (synth.beam_density((34, 38, 30), n_beams=9, seed=21) > 0.5).astype(np.float32)
+    fix = synth.slab_fixture(rho.shape, 2, axis="z")
+    t1 = synth.cylinder_tool(2, 6, 4, 5, synth.fibonacci_quats(7))
+    t2 = synth.cylinder_tool(1, 4, 3, 3, synth.fibonacci_quats(3))
+    d = synth.Design(rho, fix, [t1, t2])
+    size = int(((t1.holder != 0) | (t1.cutter != 0)).sum())
+    size2 = int(((t2.holder != 0) | (t2.cutter != 0)).sum())
+    theta_rel = (np.floor(0.01 * size) + 0.5) / size
+    # the second tool's threshold must sit between integers too
+    assert abs(theta_rel * size2 - np.round(theta_rel * size2)) > 1e-3 * size2 + 1e-9
+    ref = oracle.imf(d, keep=True, theta_rel=theta_rel)
+    imf = binding.Imf(rho.shape, theta_rel=theta_rel, orient_batch=3)
+    imf.set_tools(d.tools)
+    r = torch.from_numpy(rho).cuda()
+    f = torch.from_numpy(fix).cuda()
+    sets, fbar, sec = imf.accessible_sets(r, f)
+    imf.sync()
+    got = _unpack_sets(sets, rho.shape)
+    per = ref["per_orientation"]
+    assert got.shape[0] == len(per) == 10
+    want = np.stack([p["A"].astype(bool) for p in per])
+    assert np.array_equal(got, want)
+    steps, neg, left = imf.process_plan(sets, r, f)
+    negative = (fix == 0) & (rho <= 0.5)
+    osteps, oneg, oleft = oracle.process_plan(list(want), negative)
+    assert steps == osteps and neg == oneg and left == oleft
+    assert len(steps) >= 2 and left < neg
+    # the union of the sets is the accessible output of imf_compute (on Omega_0)
+    acc = torch.empty(rho.shape, dtype=torch.uint8, device="cuda")
+    imf.compute(r, f, accessible=acc)
+    imf.sync()
+    assert np.array_equal(acc.cpu().numpy() != 0, want.any(0) & (fix == 0))

@@ -411,3 +411,110 @@ def test_subblock_equals_slice_of_full_grid():
     assert np.array_equal(f, full["f"][:, 13:42, 7:40])
     acc = (full["f"][:, 13:42, 7:40] <= 0.01 * 126)
     assert np.array_equal(A.astype(bool), acc)
+
+
+# ---------------------------------------------------------------------------------------------
+# Sharp-point sampling (Sec. 2.1.5 sampling remark; App. B, O(1) representative points)
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("ext", [(3, 4, 5), (2, 6, 7), (1, 5, 5), (6, 6, 6)])
+def test_sharp_boundary_of_a_box_cutter_closed_form(ext):
+    """A solid a x b x c box: the boundary has abc - (a-2)(b-2)(c-2) voxels (every voxel when
+    an extent is at most 2), and the interior voxels are exactly the box shrunk by one."""
+    a, b, c = ext
+    K = np.ones((c, b, a), np.uint8)
+    B = oracle.sharp_sample(K, (0, 0, 0), "boundary")
+    inner = max(a - 2, 0) * max(b - 2, 0) * max(c - 2, 0)
+    assert B.sum() == a * b * c - inner
+    if inner:
+        assert not B[1:-1, 1:-1, 1:-1].any()
+    assert np.array_equal(oracle.sharp_sample(K, (0, 0, 0), "all"), K)
+
+
+def test_sharp_nearest_points_are_nested_and_start_at_the_origin():
+    """On the cylinder cutter (origin at the centre of the tip face, a boundary voxel): k = 1
+    gives the origin voxel itself; the k-sets are nested in k and lie in the boundary; k above
+    the boundary size gives the whole boundary; a hand-checked k = 5 set is the origin and its
+    four face neighbours in the tip face (all at squared distance 1)."""
+    from paper_2002_07627_gb300 import synth
+    t = synth.cylinder_tool(3, 20, 8, 16, synth.fibonacci_quats(1))
+    ox, oy, oz = t.origin
+    B = oracle.sharp_sample(t.cutter, t.origin, "boundary")
+    assert B[oz, oy, ox] == 1 and t.cutter[oz, oy, ox]
+    one = oracle.sharp_sample(t.cutter, t.origin, "nearest", 1)
+    assert one.sum() == 1 and one[oz, oy, ox] == 1
+    prev = one
+    for k in (2, 5, 9, 40, 200):
+        cur = oracle.sharp_sample(t.cutter, t.origin, "nearest", k)
+        assert cur.sum() == min(k, B.sum())
+        assert np.all(cur >= prev) and np.all(B >= cur)
+        prev = cur
+    five = oracle.sharp_sample(t.cutter, t.origin, "nearest", 5)
+    want = np.zeros_like(five)
+    for dx, dy, dz in ((0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0)):
+        want[oz + dz, oy + dy, ox + dx] = 1
+    assert oz == 0 or not t.cutter[oz - 1, oy, ox]          # the origin lies on the tip face
+    assert np.array_equal(five, want)
+    assert np.array_equal(oracle.sharp_sample(t.cutter, t.origin, "nearest", 10 ** 6), B)
+
+
+def test_sharp_boundary_of_a_cylinder_excludes_its_core():
+    """The interior of the r=3 cylinder cutter (voxels whose six neighbours are all cutter) is
+    not sampled; a one-voxel-thick cutter is all boundary."""
+    from paper_2002_07627_gb300 import synth
+    t = synth.cylinder_tool(3, 20, 8, 16, synth.fibonacci_quats(1))
+    K = t.cutter != 0
+    B = oracle.sharp_sample(t.cutter, t.origin, "boundary") != 0
+    z, y, x = np.nonzero(K & ~B)
+    assert len(z) > 0
+    for zz, yy, xx in zip(z, y, x):
+        assert all(K[zz + dz, yy + dy, xx + dx] for dz, dy, dx in
+                   ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)))
+    thin = np.zeros((5, 1, 1), np.uint8)
+    thin[:, 0, 0] = 1
+    assert oracle.sharp_sample(thin, (0, 0, 0), "boundary").sum() == 5
+
+
+# ---------------------------------------------------------------------------------------------
+# Greedy process plan (Sec. 3.4.1)
+# ---------------------------------------------------------------------------------------------
+
+def test_process_plan_golden():
+    """Hand-worked greedy set cover (tests/golden/process_plan_greedy.json)."""
+    g = json.load(open(os.path.join(GOLD, "process_plan_greedy.json")))
+    n = g["universe"]
+    neg = np.zeros(n, bool)
+    neg[g["negative"]] = True
+    sets = []
+    for s in g["sets"]:
+        m = np.zeros(n, bool)
+        m[s] = True
+        sets.append(m)
+    steps, total, left = oracle.process_plan(sets, neg)
+    assert [list(s) for s in steps] == g["steps"]
+    assert total == len(g["negative"]) and left == g["left"]
+
+
+def test_process_plan_invariants_on_random_sets():
+    """Removed volumes never grow from step to step (greedy on a shrinking remainder); the
+    chosen sets cover exactly |N| - left voxels of N; every uncovered voxel of N lies in no set;
+    no set is chosen twice; a full set finishes in one step."""
+    rng = np.random.default_rng(5)
+    for trial in range(20):
+        n = int(rng.integers(20, 200))
+        neg = rng.random(n) < 0.6
+        sets = [rng.random(n) < rng.uniform(0.05, 0.5) for _ in range(int(rng.integers(1, 12)))]
+        steps, total, left = oracle.process_plan(sets, neg)
+        rem = [c for _, c in steps]
+        assert rem == sorted(rem, reverse=True)
+        assert sum(rem) + left == total == neg.sum()
+        chosen = [i for i, _ in steps]
+        assert len(set(chosen)) == len(chosen)
+        covered = np.zeros(n, bool)
+        for i in chosen:
+            covered |= sets[i]
+        unreached = neg & ~covered
+        assert unreached.sum() == left
+        assert not any((s & unreached).any() for s in sets)
+    full = np.ones(10, bool)
+    assert oracle.process_plan([full & False, full], full)[0] == [(1, 10)]
