@@ -478,7 +478,8 @@ class Workload:
         from paper_2002_07627_gb300 import binding
         a = self.args
         imf = binding.Imf(self.shape, orient_batch=a.orient_batch, precision=self.prec, erode_groups=a.erode_groups,
-                          fft_stages_only=a.fft_stages_only, accessible_by_sweep=by_sweep)
+                          fft_stages_only=a.fft_stages_only, accessible_by_sweep=by_sweep,
+                          fft_wide_pencils=a.fft_wide_pencils)
         imf.set_tools(self.d.tools)
         return imf
 
@@ -795,6 +796,8 @@ def main():
     ap.add_argument("--accessible-from-imf", action="store_true",
                     help="time the library's default route for the accessible set (A = [f <= theta] where "
                          "exact) instead of the sweep")
+    ap.add_argument("--fft-wide-pencils", type=int, default=-1,
+                    help="launch shape of the big-factor FFT passes (imf_options.fft_wide_pencils; -1 default)")
     ap.add_argument("--fft-stages-only", action="store_true",
                     help="radix-stage FFT passes everywhere (comparison with the two-pass register FFT)")
     ap.add_argument("--precision", choices=["auto", "fft", "direct"], default="fft",

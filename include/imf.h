@@ -102,6 +102,17 @@ typedef struct {
                                 sharp points of tools set without a sharp_mask; fewer points
                                 can only raise the IMF (conservative, Sec. 2.1.5)             */
     int sharp_k;             /* points kept by IMF_SHARP_NEAREST (>= 1; default 1)             */
+    int fft_wide_pencils;    /* launch shape of the y / z FFT passes whose padded length has a
+                                factor above 16 (same arithmetic, same results): bit 0 = 16
+                                pencils per block (128-byte rows) for the z pass with the
+                                spectral product, bit 1 = for the other passes, else 8 per
+                                block; -1 = library default (imf_default_options)              */
+    int fft_tma;             /* two-pass y / z FFT passes as persistent kernels fed by
+                                tensor-memory-accelerator copies through a two-stage shared-
+                                memory pipeline instead of one-shot blocks that load their
+                                pencils into registers (same arithmetic, same results): bit 0 =
+                                the z pass with the spectral product, bit 1 = the other passes;
+                                -1 = library default (bit 0 only)                              */
 } imf_options;
 
 /* Fill *opt with the defaults above (grid 0x0x0, which imf_create rejects). */

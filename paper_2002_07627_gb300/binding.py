@@ -37,7 +37,8 @@ class ImfOptions(ctypes.Structure):
                 ("hbm_budget_bytes", ctypes.c_size_t), ("erode_groups", ctypes.c_int),
                 ("fft_stages_only", ctypes.c_int), ("accessible_by_sweep", ctypes.c_int),
                 ("separate_yx_passes", ctypes.c_int), ("plan_only", ctypes.c_int),
-                ("sharp_sampling", ctypes.c_int), ("sharp_k", ctypes.c_int)]
+                ("sharp_sampling", ctypes.c_int), ("sharp_k", ctypes.c_int), ("fft_wide_pencils", ctypes.c_int),
+                ("fft_tma", ctypes.c_int)]
 
 
 class ImfToolInfo(ctypes.Structure):
@@ -170,7 +171,7 @@ class Imf:
     def __init__(self, shape_zyx, lam=0.01, tau=0.5, theta_rel=0.01, precision=IMF_AUTO, recheck=True,
                  recheck_band=0.0, orient_batch=0, hbm_budget_bytes=0, voxel=1.0, erode_groups=0, fft_stages_only=False,
                  accessible_by_sweep=False, separate_yx_passes=False, plan_only=False, sharp_sampling=IMF_SHARP_ALL,
-                 sharp_k=1):
+                 sharp_k=1, fft_wide_pencils=-1, fft_tma=-1):
         self.lib = load()
         opt = ImfOptions()
         self.lib.imf_default_options(ctypes.byref(opt))
@@ -185,6 +186,8 @@ class Imf:
         opt.separate_yx_passes = int(separate_yx_passes)
         opt.plan_only = int(plan_only)
         opt.sharp_sampling, opt.sharp_k = int(sharp_sampling), int(sharp_k)
+        opt.fft_wide_pencils = int(fft_wide_pencils)
+        opt.fft_tma = int(fft_tma)
         self.shape = (nz, ny, nx)
         self.opt = opt
         h = ctypes.c_void_p()

@@ -20,7 +20,12 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libimf.so")
 HOSTLIB = os.path.join(BUILD, "libimf_hosttest.so")
 
-CUDA_SOURCES = ["imf_api.cu", "fft_kernels.cu", "fft2_kernels.cu", "imf_kernels.cu", "erode.cu", "direct_tc.cu", "noalloc.cu"]
+CUDA_SOURCES = ["imf_api.cu", "fft_kernels.cu", "fft2_kernels.cu", "fft_tma.cu", "imf_kernels.cu", "erode.cu",
+                "direct_tc.cu", "noalloc.cu"]
+# sources compiled more than once with different defines: (source, object name, defines); the
+# six instances of the TMA-fed axis pass build in parallel
+CUDA_VARIANTS = [("fft_tma_inst.cu", f"fft_tma_{'b' if big else 's'}{v}.o", [f"-DIMF_TMA_BIG={big}", f"-DIMF_TMA_VARIANT={v}"])
+                 for big in (0, 1) for v in (0, 1, 2)]
 HOST_TEST_SOURCES = ["hosttest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -59,9 +64,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if force or _stale(LIB):
         cc = nvcc()
         objs, procs = [], []
-        for src in CUDA_SOURCES:
-            obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-            cmd = [cc, *ARCH, *_flags(), "-c", os.path.join(CSRC, src), "-o", obj]
+        units = [(s, s.replace(".cu", ".o"), []) for s in CUDA_SOURCES] + CUDA_VARIANTS
+        for src, oname, defs in units:
+            obj = os.path.join(BUILD, oname)
+            cmd = [cc, *ARCH, *_flags(), *defs, "-c", os.path.join(CSRC, src), "-o", obj]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT), src))

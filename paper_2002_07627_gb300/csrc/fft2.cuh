@@ -118,20 +118,29 @@ template <int S, int N> __host__ __device__ __forceinline__ void dft_reg(float2 
 // Split of L for the two passes: A (pass-1 DFT size) >= B (pass-2 DFT size), both supported
 // with factors up to maxA (kMaxFactor or kMaxFactorBig), as balanced as possible. Returns false
 // when L has no such split.
-inline bool choose_split(int L, int *A, int *B, int maxA = kMaxFactor)
+__host__ __device__ constexpr bool choose_split(int L, int *A, int *B, int maxA = kMaxFactor)
 {
-    auto ok = [&](int n) { return n <= maxA && (supported(n) || supported_big(n)); };
     int bestA = 0, bestB = 0;
     for (int b = 2; b <= maxA; ++b) {
         if (L % b) continue;
         const int a = L / b;
-        if (a < b || !ok(a) || !ok(b)) continue;
+        const bool oka = a <= maxA && (supported(a) || supported_big(a));
+        const bool okb = b <= maxA && (supported(b) || supported_big(b));
+        if (a < b || !oka || !okb) continue;
         if (!bestA || a < bestA) { bestA = a; bestB = b; }
     }
     if (!bestA) return false;
     *A = bestA;
     *B = bestB;
     return true;
+}
+
+// Whether (a, b) is the split choose_split returns for L = a b: the pairs the kernels that
+// take both factors at compile time instantiate.
+__host__ __device__ constexpr bool is_split_choice(int a, int b, int maxA)
+{
+    int A = 0, B = 0;
+    return choose_split(a * b, &A, &B, maxA) && A == a && B == b;
 }
 
 // Pass-1 arithmetic of one thread: A-point DFT of v (the samples x[n1 + B n2], n2 < A), then

@@ -22,12 +22,17 @@ constexpr int kT2 = 256;         // threads per block: kW2 pencils x 16 slots
 
 // Columns [z][y][kx] of W consecutive kx per block; a pencil is one (batch row b, kx) pair.
 // With factors up to 16 a block has W = 16 pencils of 16 slots; with factors up to 24 (BIG)
-// W = 8 pencils of 32 slots. When nx is not a multiple of W, the last grid column of blocks
-// takes the remaining ntail kx columns of W batch rows at a time, so no block transforms empty
-// pencils.
-template <bool BIG> struct AxisShape {
-    static constexpr int W = BIG ? 8 : kW2;       // pencils per block
-    static constexpr int LOGW = BIG ? 3 : 4;
+// W = 8 pencils of 32 slots, or 16 (WIDE: 512 threads, 128-byte rows of kx per load instead of
+// 64). When nx is not a multiple of W, the last grid column of blocks takes the remaining ntail
+// kx columns of W batch rows at a time, so no block transforms empty pencils.
+// Grid: x = kx chunk (fastest), y = orientation, z = batch row: the chunks of one row run
+// together (adjacent 64 / 128-byte pieces of the same DRAM pages), and the orientations of one
+// batch row follow each other, so a pointwise factor shared by the orientations (the design
+// spectrum of the z pass) is read from DRAM once and from L2 after.
+template <bool BIG, bool WIDE = false> struct AxisShape {
+    static constexpr int W = BIG ? (WIDE ? 16 : 8) : kW2;       // pencils per block
+    static constexpr int LOGW = BIG ? (WIDE ? 4 : 3) : 4;
+    static constexpr int T = BIG ? W * 32 : kT2;                 // threads per block
     template <typename F> __device__ __forceinline__ static void with(int n, F &&f)
     {
         if constexpr (BIG) fft2::with_size_big(n, f);
@@ -39,32 +44,33 @@ template <bool BIG> struct AxisShape {
 // 0 never, -1 decided at run time. The small shape (axis2_kernel) decides at run time (62
 // registers, four blocks per SM); the big shape (axis2_big_kernel) is specialised, so that
 // without the factor it fits three blocks per SM (80 registers) while the z pass keeps its 120.
-template <int S, bool BIG, int MUL>
+template <int S, bool BIG, int MUL, bool WIDE = false>
 __device__ __forceinline__ void axis2_body(const AxisArgs &a, int nbatch, int nfull, int ntail)
 {
-    using Sh = AxisShape<BIG>;
+    using Sh = AxisShape<BIG, WIDE>;
     constexpr int kW = Sh::W;
     extern __shared__ float2 sm[];
     const int A = a.A2, B = a.B2, L = A * B;
     float2 *tile = sm, *tw = sm + (size_t)L * kW;
     const int w = threadIdx.x & (kW - 1), p = threadIdx.x >> Sh::LOGW;
+    const int chunk = blockIdx.x, row = blockIdx.z;
     long b;
     int c;
     bool ok;
-    if ((int)blockIdx.x < nfull) {
-        b = blockIdx.y;
-        c = (int)blockIdx.x * kW + w;
+    if (chunk < nfull) {
+        b = row;
+        c = chunk * kW + w;
         ok = true;
     } else {
-        const long f0 = (long)blockIdx.y * kW;
+        const long f0 = (long)row * kW;
         if (f0 >= (long)nbatch * ntail) return;  // whole block idle (uniform)
         const long f = f0 + w;
         b = f / ntail;
         c = nfull * kW + (int)(f - b * ntail);
         ok = b < nbatch;
     }
-    for (int i = threadIdx.x; i < L; i += kT2) tw[i] = a.tw[i];
-    const long o = blockIdx.z;
+    for (int i = threadIdx.x; i < L; i += Sh::T) tw[i] = a.tw[i];
+    const long o = blockIdx.y;
     // pass 1: slot p = n1 < B loads x[n1 + B n2] (times the pointwise factor) and runs the
     // A-point DFT while the twiddle table is still being staged; after the barrier it applies
     // the twiddles and stores tile element (n1, k2) of pencil w at (n1 A + k2) W + w. Every
@@ -138,6 +144,13 @@ template <int S, int MUL>
 __global__ void __launch_bounds__(kT2, MUL == 0 ? 3 : 1) axis2_big_kernel(AxisArgs a, int nbatch, int nfull, int ntail)
 {
     axis2_body<S, true, MUL>(a, nbatch, nfull, ntail);
+}
+
+// 16 pencils of 32 slots (512 threads): rows of 16 kx (128 bytes) per load
+template <int S, int MUL>
+__global__ void __launch_bounds__(512, 1) axis2_big_wide_kernel(AxisArgs a, int nbatch, int nfull, int ntail)
+{
+    axis2_body<S, true, MUL, true>(a, nbatch, nfull, ntail);
 }
 
 // Pass-1 input of the inverse x pass for thread p of a row: the half spectrum X[0..M] of the
@@ -434,11 +447,10 @@ template <typename K> void set_smem2(K kernel, size_t bytes)
 
 } // namespace
 
-// the BIG kernel has half the pencils per block and lengths up to 24 x 24
-static size_t axis2_smem_for(int A, int B)
+// the BIG kernel has lengths up to 24 x 24 and 8 (or 16, wide) pencils per block
+static size_t axis2_smem_for(int A, int B, int W)
 {
-    const bool big = A > fft2::kMaxFactor;
-    return (size_t)(A * B * (big ? AxisShape<true>::W : kW2) + A * B) * sizeof(float2);
+    return (size_t)(A * B * W + A * B) * sizeof(float2);
 }
 
 size_t irfft2_smem(int M, int A, int B) { return (size_t)x_layout(2 * M + 1, kT2, M, A, B).end * sizeof(float2); }
@@ -448,17 +460,24 @@ size_t yx2_smem(int Ly, int hs, int M, int rows)
     return (size_t)(yx2_flags_offset(Ly, hs, M) + ((long)rows * ((2 * M + 31) & ~31) + 7) / 8) * sizeof(float2);
 }
 
-template <bool BIG> static void launch_axis2_shape(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s)
+template <bool BIG, bool WIDE>
+static void launch_axis2_shape(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s)
 {
-    constexpr int kW = AxisShape<BIG>::W;
-    const size_t smem = axis2_smem_for(a.A2, a.B2);
+    using Sh = AxisShape<BIG, WIDE>;
+    constexpr int kW = Sh::W;
+    const size_t smem = axis2_smem_for(a.A2, a.B2, kW);
     const int nfull = a.nx / kW, ntail = a.nx % kW;
-    dim3 grid(nfull + (ntail ? 1 : 0), nbatch, norient);
+    // the tail column handles ntail kx of kW rows at a time (nbatch blocks cover them)
+    dim3 grid(nfull + (ntail ? 1 : 0), norient, nbatch);
     auto go = [&](auto kernel) {
         set_smem2(kernel, smem);
-        kernel<<<grid, kT2, smem, s>>>(a, nbatch, nfull, ntail);
+        kernel<<<grid, Sh::T, smem, s>>>(a, nbatch, nfull, ntail);
     };
-    if constexpr (BIG) {
+    if constexpr (BIG && WIDE) {
+        if (sign < 0) go(axis2_big_wide_kernel<-1, 0>);
+        else if (a.mul) go(axis2_big_wide_kernel<1, 1>);
+        else go(axis2_big_wide_kernel<1, 0>);
+    } else if constexpr (BIG) {
         if (sign < 0) go(axis2_big_kernel<-1, 0>);
         else if (a.mul) go(axis2_big_kernel<1, 1>);
         else go(axis2_big_kernel<1, 0>);
@@ -470,8 +489,16 @@ template <bool BIG> static void launch_axis2_shape(int sign, const AxisArgs &a, 
 
 void launch_axis2(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s)
 {
-    if (a.A2 > fft2::kMaxFactor) launch_axis2_shape<true>(sign, a, nbatch, norient, s);
-    else launch_axis2_shape<false>(sign, a, nbatch, norient, s);
+    if (a.tma && launch_axis2_tma(sign, a, nbatch, norient, s)) return;
+    if (a.A2 > fft2::kMaxFactor) {
+        // big factors: 16 pencils per block where the option asks for it (wider rows of kx per
+        // load, one 512-thread block per SM), else 8
+        const bool wide = a.mul ? (a.wide & 1) != 0 : (a.wide & 2) != 0;
+        if (wide) launch_axis2_shape<true, true>(sign, a, nbatch, norient, s);
+        else launch_axis2_shape<true, false>(sign, a, nbatch, norient, s);
+    } else {
+        launch_axis2_shape<false, false>(sign, a, nbatch, norient, s);
+    }
 }
 
 void launch_irfft2_threshold(const IrfftArgs &a, int norient, cudaStream_t s)

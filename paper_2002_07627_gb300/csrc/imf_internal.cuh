@@ -37,6 +37,10 @@ struct AxisArgs {
     const float2 *tw;            // exp(-2 pi i m / L), m < L
     FftPlan plan;
     int A2, B2;                  // two-pass split L = A2 B2 (fft2.cuh), or 0: Stockham stages
+    int wide;                    // big-factor shape: bit 0 = 16 pencils per block for passes with
+                                 // a pointwise factor, bit 1 = for the others (else 8)
+    int tma;                     // 1: the persistent TMA-fed kernel (fft_tma.cu) where it applies
+    int *status;                 // device status word for bounded-wait timeouts, or NULL
 };
 
 // Real-to-complex FFT along x (rows of a real grid), packed as a half-length complex FFT.
@@ -85,6 +89,9 @@ void launch_rfft_fwd(const RfftArgs &a, cudaStream_t s);
 void launch_irfft_threshold(const IrfftArgs &a, int norient, cudaStream_t s);
 // two-pass register variants (fft2_kernels.cu); the dispatchers above call them when A2 > 0
 void launch_axis2(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s);
+// The same pass as a persistent kernel fed by tensor copies; false (nothing launched) where
+// a tensor map cannot describe the arrays or the stages do not fit.
+bool launch_axis2_tma(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s);
 void launch_irfft2_threshold(const IrfftArgs &a, int norient, cudaStream_t s);
 // the inverse y and x passes of one z-plane per block (fft2_kernels.cu); yx2_fits says whether
 // the plane (and the x pass scratch) fits in shared memory for these arguments

@@ -45,8 +45,13 @@ def _check_vs_oracle(d, fbar, sec, lam=0.01):
     """f_bar and Gamma of one design against the FP64 oracle, away from the allowance
     discontinuity (the IMF contract of the plain form)."""
     ref = oracle.imf(d)
-    clear = np.abs(ref["fbar"] - lam) > 1e-4
-    assert np.abs(fbar.astype(np.float64) - ref["fbar"])[clear].max() <= 2e-4
+    # away from the allowance discontinuity, judged on f / M before the allowance
+    M = float(ref["M"])
+    pre = ref["f"] / M if M > 0 else np.zeros_like(ref["f"])
+    clear = np.abs(pre - lam) > 1e-4
+    if d.fixture is not None:
+        clear |= d.fixture != 0
+    assert np.abs(fbar.astype(np.float64) - ref["fbar"])[clear].max(initial=0) <= 2e-4
     assert np.array_equal(sec[clear], ref["secluded"][clear])
 
 

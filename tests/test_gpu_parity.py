@@ -86,8 +86,12 @@ def check_against_oracle(design, got, ref, theta_rel=0.01, lam=0.01):
     # the oracle's own accessible set obeys the same bounds (pins the bound computation)
     Ao = ref["accessible"] != 0
     assert not (sure & om0 & ~Ao).any() and not (Ao & ~sure & ~maybe).any()
-    clear = np.abs(ref["fbar"] - lam) > 1e-4
-    assert np.abs(got["fbar"] - ref["fbar"])[clear].max() <= 2e-4
+    # f_bar and Gamma away from the allowance discontinuity, judged on the normalised IMF before
+    # the allowance (f / M): after it, a point just below lambda reads 0 and would look clear
+    M = float(ref["M"])
+    pre = ref["f"] / M if M > 0 else np.zeros_like(ref["f"])
+    clear = (np.abs(pre - lam) > 1e-4) | ~om0
+    assert np.abs(got["fbar"] - ref["fbar"])[clear].max(initial=0) <= 2e-4
     assert np.array_equal(got["secluded"][clear], ref["secluded"][clear])
 
 
@@ -618,3 +622,26 @@ def test_accessible_sets_and_greedy_process_plan_match_oracle():
     imf.compute(r, f, accessible=acc)
     imf.sync()
     assert np.array_equal(acc.cpu().numpy() != 0, want.any(0) & (fix == 0))
+
+
+def test_tma_fed_axis_passes_equal_the_one_shot_kernels():
+    """The persistent y / z FFT passes fed by tensor copies (the default for the z pass, optional
+    for the others) run the same arithmetic as the one-shot kernels (fft_tma 0): f, f_bar, Gamma
+    and A are bit-identical with either choice, on grids whose
+    padded lengths use the 16-slot shape, the 32-slot shape (a y length above 256) and lengths
+    below the persistent kernel's minimum (which keep the one-shot kernel); and the result meets
+    the contract against the oracle."""
+    rho = synth.beam_density((24, 262, 6), n_beams=6, seed=2)
+    big = synth.Design(rho, synth.slab_fixture(rho.shape, 1, axis="z"),
+                       [synth.cylinder_tool(1, 4, 2, 3, synth.fibonacci_quats(3))])
+    cases = [(_small3d(seed=4, n=(70, 66, 64), n_orient=5), {}), (big, {}),
+             (_small3d(seed=5, n=(20, 18, 16), n_orient=4), {"accessible_by_sweep": True})]
+    for d, kw in cases:
+        b = run_gpu(d, orient_batch=3, fft_tma=0, **kw)
+        for mode in (-1, 3):          # the default (z pass only) and every pass
+            a = run_gpu(d, orient_batch=3, fft_tma=mode, **kw)
+            for k in ("f", "fbar", "secluded", "accessible"):
+                assert np.array_equal(a[k], b[k]), (mode, k)
+    d = cases[0][0]
+    check_against_oracle(d, run_gpu(d, orient_batch=3), oracle_ref(d))
+    assert max(run_gpu(big, orient_batch=2)["imf"].tool_info(0).P) > 256
