@@ -27,6 +27,9 @@ EXPORTS = ["imf_default_options", "imf_create", "imf_set_tool", "imf_compute", "
            "imf_penalize_sensitivity_noalloc", "imf_capture_graph", "imf_launch_graph", "imf_autotune",
            "imf_set_path", "imf_selftest_mma", "imf_get_last_bits", "imf_footprint",
            "imf_compute_accessible_sets", "imf_process_plan"]
+# every symbol include/imf_to.h declares
+EXPORTS_TO = ["imf_to2d_default_options", "imf_to2d_create", "imf_to2d_destroy", "imf_to2d_last_error",
+              "imf_to2d_project", "imf_to2d_analyze", "imf_to2d_sensitivity", "imf_to2d_update", "imf_to2d_result"]
 
 
 class ImfOptions(ctypes.Structure):
@@ -51,6 +54,12 @@ class ImfToolInfo(ctypes.Structure):
 class ImfStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_long), ("computes", ctypes.c_long), ("flagged", ctypes.c_long),
                 ("flagged_total", ctypes.c_long), ("n_kernels", ctypes.c_int), ("owned_bytes", ctypes.c_size_t)]
+
+
+class To2dOptions(ctypes.Structure):
+    _fields_ = [("nelx", ctypes.c_int), ("nely", ctypes.c_int), ("E0", ctypes.c_double), ("Emin", ctypes.c_double),
+                ("nu", ctypes.c_double), ("penal", ctypes.c_double), ("beta", ctypes.c_double),
+                ("rmin", ctypes.c_double), ("cg_tol", ctypes.c_double), ("cg_max_iter", ctypes.c_int)]
 
 
 class ImfFootprint(ctypes.Structure):
@@ -105,8 +114,21 @@ def load(path: str | None = None):
     L.imf_autotune.argtypes = [H, P, P, P, P, P, ctypes.POINTER(I)]
     L.imf_set_path.argtypes = [H, I, I]
     L.imf_selftest_mma.argtypes = [I, I, P, P, P]
-    for name in EXPORTS:
-        if name not in ("imf_default_options", "imf_destroy", "imf_last_error"):
+    L.imf_to2d_default_options.argtypes = [ctypes.POINTER(To2dOptions)]
+    L.imf_to2d_default_options.restype = None
+    L.imf_to2d_create.argtypes = [ctypes.POINTER(To2dOptions), ctypes.POINTER(H)]
+    L.imf_to2d_destroy.argtypes = [H]
+    L.imf_to2d_destroy.restype = None
+    L.imf_to2d_last_error.argtypes = [H]
+    L.imf_to2d_last_error.restype = ctypes.c_char_p
+    L.imf_to2d_project.argtypes = [H, P, P, P]
+    L.imf_to2d_analyze.argtypes = [H, P, P, P, P, P]
+    L.imf_to2d_sensitivity.argtypes = [H, P, P, P, P]
+    L.imf_to2d_update.argtypes = [H, P, P, P, D, D, D, P, ctypes.POINTER(D), ctypes.POINTER(D), P]
+    L.imf_to2d_result.argtypes = [H, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(D)]
+    for name in EXPORTS + EXPORTS_TO:
+        if name not in ("imf_default_options", "imf_destroy", "imf_last_error", "imf_to2d_default_options",
+                        "imf_to2d_destroy", "imf_to2d_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -402,3 +424,66 @@ class Imf:
             raise ValueError("libimf takes CUDA tensors (device memory); use compute_host for host arrays")
         if t.dtype != dtype or not t.is_contiguous():
             raise ValueError(f"expected a contiguous {dtype} tensor")
+
+
+class To2d:
+    """The SIMP steps of the topology-optimisation loop (include/imf_to.h) for a 2D grid of
+    nelx x nely unit elements on the current CUDA device; mirrors the C ABI one-to-one."""
+
+    def __init__(self, nelx, nely, **kw):
+        self.lib = load()
+        o = To2dOptions()
+        self.lib.imf_to2d_default_options(ctypes.byref(o))
+        o.nelx, o.nely = int(nelx), int(nely)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        self.opt = o
+        h = ctypes.c_void_p()
+        st = self.lib.imf_to2d_create(ctypes.byref(o), ctypes.byref(h))
+        if st != IMF_OK:
+            raise ImfError(st, "imf_to2d_create")
+        self.h = h
+
+    def _check(self, st):
+        if st != IMF_OK:
+            raise ImfError(st, self.lib.imf_to2d_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.imf_to2d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _s(stream, t):
+        import torch
+        return (stream or torch.cuda.current_stream(t.device)).cuda_stream
+
+    def project(self, xi, rho, stream=None):
+        self._check(self.lib.imf_to2d_project(self.h, _ptr(xi), _ptr(rho), self._s(stream, xi)))
+        return rho
+
+    def analyze(self, rho, force, fixed, u=None, stream=None):
+        """FEA; returns (compliance, CG iterations, relative residual)."""
+        self._check(self.lib.imf_to2d_analyze(self.h, _ptr(rho), _ptr(force), _ptr(fixed), _ptr(u),
+                                              self._s(stream, rho)))
+        c, it, res = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.imf_to2d_result(self.h, ctypes.byref(c), ctypes.byref(it), ctypes.byref(res)))
+        return c.value, it.value, res.value
+
+    def sensitivity(self, xi, rho, sens, stream=None):
+        self._check(self.lib.imf_to2d_sensitivity(self.h, _ptr(xi), _ptr(rho), _ptr(sens), self._s(stream, xi)))
+        return sens
+
+    def update(self, xi, S, passive, volfrac, xi_new, move=0.2, eta=0.5, stream=None):
+        """OC update; returns (mean |xi_new - xi| over free elements, mean projected density)."""
+        chg, vol = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.imf_to2d_update(self.h, _ptr(xi), _ptr(S), _ptr(passive), float(volfrac), float(move),
+                                             float(eta), _ptr(xi_new), ctypes.byref(chg), ctypes.byref(vol),
+                                             self._s(stream, xi)))
+        return chg.value, vol.value

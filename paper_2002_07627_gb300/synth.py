@@ -244,3 +244,30 @@ def config_batch(n_designs=64, seed=0, lo=48, hi=192, r_lo=2, r_hi=6, nr_lo=16, 
         tool = cylinder_tool(rc, 20, rh, 16, fibonacci_quats(nr))
         out.append(Design(rho, fix, [tool], name=f"batch{d}_{edge}_R{nr}_r{rc}"))
     return out
+
+
+def cantilever2d(nelx=256, nely=128, fixture_cols=2):
+    """Load case of the 2D cantilever beam (Sec. 3.1, Fig. of the beam boundary conditions; a
+    reading of the figure): nelx x nely unit elements, every node of the left edge clamped, a
+    unit downward force at the middle node of the right edge, and the leftmost `fixture_cols`
+    element columns the clamping fixture (passive solid in the optimisation, fixture of the
+    IMF). Nodes are numbered j (nelx + 1) + i with dofs (2 n, 2 n + 1) = (x, y). Returns
+    (force float64 [2 (nelx+1)(nely+1)], clamped-dof mask uint8, fixture uint8 [nely][nelx])."""
+    ndof = 2 * (nelx + 1) * (nely + 1)
+    force = np.zeros(ndof)
+    node = (nely // 2) * (nelx + 1) + nelx
+    force[2 * node + 1] = -1.0
+    fixed = np.zeros(ndof, np.uint8)
+    for j in range(nely + 1):
+        n = j * (nelx + 1)
+        fixed[2 * n] = fixed[2 * n + 1] = 1
+    fixture = np.zeros((nely, nelx), np.uint8)
+    fixture[:, :fixture_cols] = 1
+    return force, fixed, fixture
+
+
+def to2d_tools(n_orient=8):
+    """Two planar tool assemblies for the 2D optimisation (Sec. 3.1 uses one thin and one thick
+    cutter): a 1-voxel-wide and a 3-voxel-wide cutter, 12 tall, with 7- and 9-wide holders; the
+    orientations are spread over 0-180 degrees."""
+    return [planar_tool(1, 12, 7, 10, n_orient=n_orient), planar_tool(3, 12, 9, 10, n_orient=n_orient)]

@@ -23,8 +23,12 @@ def test_header_declares_exactly_the_exported_symbols(lib):
     hdr = open(os.path.join(ROOT, "include", "imf.h")).read()
     declared = set(re.findall(r"\b(imf_[a-z_]+)\s*\(", hdr))
     assert declared == set(binding.EXPORTS)
+    hdr_to = open(os.path.join(ROOT, "include", "imf_to.h")).read()
+    declared_to = set(re.findall(r"\b(imf_[a-z0-9_]+)\s*\(", hdr_to))
+    assert declared_to == set(binding.EXPORTS_TO)
+    declared |= declared_to
     out = os.popen(f"nm -D --defined-only {build.LIB}").read()
-    exported = set(re.findall(r" T (imf_[a-z_]+)", out))
+    exported = set(re.findall(r" T (imf_[a-z0-9_]+)", out))
     assert declared <= exported
 
 
