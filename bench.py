@@ -479,7 +479,7 @@ class Workload:
         a = self.args
         imf = binding.Imf(self.shape, orient_batch=a.orient_batch, precision=self.prec, erode_groups=a.erode_groups,
                           fft_stages_only=a.fft_stages_only, accessible_by_sweep=by_sweep,
-                          fft_wide_pencils=a.fft_wide_pencils)
+                          fft_wide_pencils=a.fft_wide_pencils, erode_levels=a.erode_levels)
         imf.set_tools(self.d.tools)
         return imf
 
@@ -842,6 +842,8 @@ def main():
                          "exact) instead of the sweep")
     ap.add_argument("--fft-wide-pencils", type=int, default=-1,
                     help="launch shape of the big-factor FFT passes (imf_options.fft_wide_pencils; -1 default)")
+    ap.add_argument("--erode-levels", action="store_true",
+                    help="minimum over sharp points with dyadic min levels instead of pairwise minima per run")
     ap.add_argument("--fft-stages-only", action="store_true",
                     help="radix-stage FFT passes everywhere (comparison with the two-pass register FFT)")
     ap.add_argument("--precision", choices=["auto", "fft", "direct"], default="fft",

@@ -113,6 +113,11 @@ typedef struct {
                                 pencils into registers (same arithmetic, same results): bit 0 =
                                 the z pass with the spectral product, bit 1 = the other passes;
                                 -1 = library default (bit 0 only)                              */
+    int erode_levels;        /* minimum over sharp points: 1 = dyadic min levels built in the
+                                shared-memory tile (one three-input minimum per output and run
+                                of any length, but every row's levels rebuilt per chunk), 0
+                                (default) = pairwise minima over each run; same results. Tiles
+                                with rows above 128 cells use 0                                */
 } imf_options;
 
 /* Fill *opt with the defaults above (grid 0x0x0, which imf_create rejects). */

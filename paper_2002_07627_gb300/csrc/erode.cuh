@@ -14,6 +14,11 @@ namespace imf {
 // threads 4.17 ms per step against 4.77 ms for 64 x 8 x 8 in 512 threads and 7.2 ms for
 // 32 x 8 x 8 in 256 threads).
 constexpr int kErTX = 64, kErTY = 16, kErTZ = 8, kErXT = 8, kErMaxL = 16;
+// runs of the level kernel (erode3_kernel) are split at 31: any length up to 2^5 - 1 is two
+// windows of one dyadic level
+constexpr int kErMaxL3 = 31;
+// longest tile row the level kernel builds levels for (four cells per lane of a warp)
+constexpr int kErMaxRow3 = 128;
 constexpr int kErThreads = (kErTX / kErXT) * kErTY * kErTZ;
 constexpr int kErBlocksPerSM = 1024 / kErThreads;            // 64 registers per thread
 constexpr int kErMaxRunsPerChunk = 2 * kErThreads;
@@ -22,7 +27,7 @@ constexpr int kErMaxRunsPerChunk = 2 * kErThreads;
 constexpr size_t kErodeBudget = (kErThreads >= 1024 ? 208 : kErThreads >= 512 ? 104 : 50) * 1024;
 struct ErodeChunk {
     int run0, run1;              // runs of this chunk, sorted by length
-    int lend[kErMaxL + 1];       // runs of length L are run0 + lend[L-1] .. run0 + lend[L] - 1
+    int lend[kErMaxL3 + 1];      // runs of length L are run0 + lend[L-1] .. run0 + lend[L] - 1
     int txh, tyh, tzh;           // tile extents
     int pitch_y, pitch_z;        // shared-memory row and plane pitch (floats)
     int ox, oy, oz;              // tile origin = block output origin + (ox, oy, oz) in window index
@@ -42,5 +47,9 @@ struct Erode2Args {
 };
 void launch_erode2(const Erode2Args &a, size_t smem, cudaStream_t s);
 int erode2_blocks_per_sm(size_t smem);
+// The same minimum with dyadic min levels built in place in the tile (runs up to kErMaxL3, tile
+// rows up to kErMaxRow3); planned with plan_erode(..., kErMaxL3).
+void launch_erode3(const Erode2Args &a, size_t smem, cudaStream_t s);
+int erode3_blocks_per_sm(size_t smem);
 
 } // namespace imf

@@ -26,13 +26,13 @@ inline bool bank_free(int P, int Q)
     return true;
 }
 
-// Runs along x of the sharp points `sh` (offset triples) of one orientation, grouped in
-// dz-chunks whose g tile fits kErodeBudget bytes; appends the chunks and their (tile offset,
+// Runs along x (at most maxL long) of the sharp points `sh` (offset triples) of one orientation,
+// grouped in dz-chunks whose g tile fits kErodeBudget bytes; appends the chunks and their (tile offset,
 // length) runs and raises smem_max to the largest tile. K = kmax of the tool's cutter offsets
 // (the translation window starts at t = -K).
 
 inline void plan_erode(const std::vector<int32_t> &sh, const int K[3], std::vector<ErodeChunk> &chunks,
-                std::vector<int2> &runs, size_t &smem_max)
+                std::vector<int2> &runs, size_t &smem_max, int maxL = kErMaxL)
 {
     if (sh.empty()) return;
     int kmn[3] = {1 << 30, 1 << 30, 1 << 30}, kmx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
@@ -50,8 +50,8 @@ inline void plan_erode(const std::vector<int32_t> &sh, const int K[3], std::vect
         while (i < v.size()) {
             size_t j = i;
             while (j + 1 < v.size() && v[j + 1] == v[j] + 1) ++j;
-            for (int a0 = v[i]; a0 <= v[j]; a0 += kErMaxL)
-                rr.push_back({kv.first.first, kv.first.second, a0, std::min(kErMaxL, v[j] - a0 + 1)});
+            for (int a0 = v[i]; a0 <= v[j]; a0 += maxL)
+                rr.push_back({kv.first.first, kv.first.second, a0, std::min(maxL, v[j] - a0 + 1)});
             i = j + 1;
         }
     }
@@ -80,7 +80,7 @@ inline void plan_erode(const std::vector<int32_t> &sh, const int K[3], std::vect
             for (size_t i = b; i < e; ++i) runs.push_back(cr[i]);
             ch.run1 = (int)runs.size();
             ch.lend[0] = 0;
-            for (int L = 1; L <= kErMaxL; ++L) {
+            for (int L = 1; L <= kErMaxL3; ++L) {
                 int c = ch.lend[L - 1];
                 while (ch.run0 + c < ch.run1 && runs[ch.run0 + c].y == L) ++c;
                 ch.lend[L] = c;

@@ -66,28 +66,28 @@ extern "C" int imf_host_fft2(int L, int sign, const float *in, float *out)
 }
 
 // The plan of the tiled minimum over sharp points for one orientation's sharp offsets
-// (n_pts triples x, y, z) and window origin K. Writes per chunk 28 ints (run0, run1, txh, tyh,
-// tzh, pitch_y, pitch_z, ox, oy, oz, lend[0..16], 0) and per run 2 ints (tile offset, length).
-// Returns the number of chunks, or -1 when the output arrays are too small; *smem gets the
-// largest tile in bytes and *nruns the number of runs.
-extern "C" int imf_host_plan_erode(const int *sh, int n_pts, const int *K, int max_chunks, int *chunk_out,
+// (n_pts triples x, y, z), window origin K and longest run maxL (16 or 31). Writes per chunk 44
+// ints (run0, run1, txh, tyh, tzh, pitch_y, pitch_z, ox, oy, oz, lend[0..31], 0, 0) and per run
+// 2 ints (tile offset, length). Returns the number of chunks, or -1 when the output arrays are
+// too small; *smem gets the largest tile in bytes and *nruns the number of runs.
+extern "C" int imf_host_plan_erode(const int *sh, int n_pts, const int *K, int maxL, int max_chunks, int *chunk_out,
                                    int max_runs, int *runs_out, long *smem, int *nruns)
 {
     std::vector<int32_t> v(sh, sh + 3 * (size_t)n_pts);
     std::vector<imf::ErodeChunk> chunks;
     std::vector<int2> runs;
     size_t sm = 0;
-    imf::plan_erode(v, K, chunks, runs, sm);
+    imf::plan_erode(v, K, chunks, runs, sm, maxL);
     *smem = (long)sm;
     *nruns = (int)runs.size();
     if ((int)chunks.size() > max_chunks || (int)runs.size() > max_runs) return -1;
     for (size_t c = 0; c < chunks.size(); ++c) {
         const imf::ErodeChunk &ch = chunks[c];
-        int *o = chunk_out + 28 * c;
+        int *o = chunk_out + 44 * c;
         const int head[10] = {ch.run0, ch.run1, ch.txh, ch.tyh, ch.tzh, ch.pitch_y, ch.pitch_z, ch.ox, ch.oy, ch.oz};
         for (int i = 0; i < 10; ++i) o[i] = head[i];
-        for (int i = 0; i <= imf::kErMaxL; ++i) o[10 + i] = ch.lend[i];
-        o[27] = 0;
+        for (int i = 0; i <= imf::kErMaxL3; ++i) o[10 + i] = ch.lend[i];
+        o[42] = o[43] = 0;
     }
     for (size_t r = 0; r < runs.size(); ++r) {
         runs_out[2 * r] = runs[r].x;

@@ -70,6 +70,7 @@ struct Tool {
     int2 *er_runs = nullptr;
     size_t erode_smem = 0;
     int erode_bps = 1;                   // resident erosion blocks per SM
+    bool erode_levels = false;           // plan and kernel of the dyadic-level minimum (erode3)
     long n_rt = 0, n_rk = 0, n_sh = 0;
     std::vector<int> perm, iperm;        // internal orientation order -> caller's index, and back
     int *perm_dev = nullptr;             // perm on the device (per-orientation outputs)
@@ -665,6 +666,7 @@ void imf_default_options(imf_options *opt)
     opt->sharp_k = 1;
     opt->fft_wide_pencils = -1;
     opt->fft_tma = -1;
+    opt->erode_levels = 0;
 }
 
 imf_status imf_create(const imf_options *opt, imf_handle *out)
@@ -944,10 +946,21 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
     std::vector<ErodeChunk> chunks;
     std::vector<int2> eruns;
     std::vector<int> chst(n_orient + 1, 0);
-    t.erode_smem = 0;
-    for (int i = 0; i < n_orient; ++i) {
-        plan_erode(t.sh[i], t.kmax, chunks, eruns, t.erode_smem);
-        chst[i + 1] = (int)chunks.size();
+    // the dyadic-level kernel (runs up to kErMaxL3) where every tile row fits its level build,
+    // else the pairwise kernel (runs up to kErMaxL)
+    t.erode_levels = h->opt.erode_levels != 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        chunks.clear();
+        eruns.clear();
+        t.erode_smem = 0;
+        for (int i = 0; i < n_orient; ++i) {
+            plan_erode(t.sh[i], t.kmax, chunks, eruns, t.erode_smem, t.erode_levels ? kErMaxL3 : kErMaxL);
+            chst[i + 1] = (int)chunks.size();
+        }
+        bool rows_fit = true;
+        for (const ErodeChunk &c : chunks) rows_fit = rows_fit && c.txh <= kErMaxRow3;
+        if (!t.erode_levels || rows_fit) break;
+        t.erode_levels = false;
     }
     if (t.erode_smem + kErMaxRunsPerChunk * sizeof(int2) > 227 * 1024) {
         free_tool(h, t);
@@ -959,7 +972,7 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
             h->nsm = n;
-        t.erode_bps = erode2_blocks_per_sm(t.erode_smem);
+        t.erode_bps = t.erode_levels ? erode3_blocks_per_sm(t.erode_smem) : erode2_blocks_per_sm(t.erode_smem);
     }
     st = IMF_OK;
     auto bail = [&](imf_status s2) { free_tool(h, t); return s2; };
@@ -1102,7 +1115,8 @@ imf_status tail_batch(imf_handle h, const Tool &t, const float *rho, const uint8
                                     : (int)std::max((12 * slots + tiles - 1) / tiles, (long)(nb + 15) / 16);
         a.ngroups = std::max(1, std::min(G, nb));
         Launch L(h, KID_ERODE, s);
-        launch_erode2(a, t.erode_smem, s);
+        if (t.erode_levels) launch_erode3(a, t.erode_smem, s);
+        else launch_erode2(a, t.erode_smem, s);
     }
     h->last_batch_base = o0;
     h->last_batch_n = nb;

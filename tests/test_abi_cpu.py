@@ -172,7 +172,7 @@ def test_stage_reciprocals_are_exact(lib):
     assert L.imf_host_check_div(4096, 1 << 20) == 0
 
 
-def _host_plan(sh, K):
+def _host_plan(sh, K, maxl=16):
     import ctypes
     from paper_2002_07627_gb300 import build
     L = ctypes.CDLL(build.HOSTLIB)
@@ -180,18 +180,19 @@ def _host_plan(sh, K):
     Ka = np.ascontiguousarray(np.asarray(K, np.int32))
     consts = np.zeros(7, np.int64)
     L.imf_host_erode_constants(consts.ctypes.data_as(ctypes.c_void_p))
-    chunks = np.zeros((4096, 28), np.int32)
+    chunks = np.zeros((4096, 44), np.int32)
     runs = np.zeros((1 << 16, 2), np.int32)
     smem = ctypes.c_long(0)
     nruns = ctypes.c_int(0)
-    L.imf_host_plan_erode.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
-                                      ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_long),
+    L.imf_host_plan_erode.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_long),
                                       ctypes.POINTER(ctypes.c_int)]
-    n = L.imf_host_plan_erode(sh.ctypes.data, len(sh), Ka.ctypes.data, len(chunks), chunks.ctypes.data, len(runs),
-                              runs.ctypes.data, ctypes.byref(smem), ctypes.byref(nruns))
+    n = L.imf_host_plan_erode(sh.ctypes.data, len(sh), Ka.ctypes.data, maxl, len(chunks), chunks.ctypes.data,
+                              len(runs), runs.ctypes.data, ctypes.byref(smem), ctypes.byref(nruns))
     assert n >= 0
-    return chunks[:n], runs[:nruns.value], smem.value, dict(zip(["tx", "ty", "tz", "xt", "maxl", "budget", "maxruns"],
-                                                                  consts.tolist()))
+    c = dict(zip(["tx", "ty", "tz", "xt", "maxl", "budget", "maxruns"], consts.tolist()))
+    c["maxl"] = maxl
+    return chunks[:n], runs[:nruns.value], smem.value, c
 
 
 def _plan_cases():
@@ -210,21 +211,23 @@ def _plan_cases():
     return cases
 
 
+@pytest.mark.parametrize("maxl", [16, 31])
 @pytest.mark.parametrize("case", range(10))
-def test_erosion_plan_covers_every_sharp_point_once_within_the_tile(lib, case):
+def test_erosion_plan_covers_every_sharp_point_once_within_the_tile(lib, case, maxl):
     """The plan of the tiled minimum over sharp points (Eq. eq_imf_2), decoded with only the
     window origin K and each chunk's tile origin: its runs cover every sharp point exactly once,
-    sit in length groups of at most 16, every thread position reads inside its chunk's tile,
-    the tile fits the budget and the 32 lanes of a warp (8 rows x 4 planes) hit 32 banks."""
+    sit in length groups of at most 16 (the pairwise kernel) or 31 (the level kernel), every
+    thread position reads inside its chunk's tile, the tile fits the budget and the 32 lanes of
+    a warp (8 rows x 4 planes) hit 32 banks."""
     sh = np.asarray(_plan_cases()[case], np.int64)
     rng = np.random.default_rng(case)
     K = sh.max(0) + rng.integers(0, 5, size=3)      # any window origin at or beyond the largest offset
-    chunks, runs, smem, c = _host_plan(sh, K)
+    chunks, runs, smem, c = _host_plan(sh, K, maxl)
     covered = []
     nxt = c["tx"] // c["xt"]
     for ch in chunks:
         run0, run1, txh, tyh, tzh, P, Q, ox, oy, oz = ch[:10]
-        lend = ch[10:27]
+        lend = ch[10:42]
         assert P % 2 == 1 and P >= txh and Q >= tyh * P
         banks = {(tz * Q + ty * P) % 32 for tz in range(4) for ty in range(8)}
         assert len(banks) == 32

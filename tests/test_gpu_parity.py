@@ -645,3 +645,28 @@ def test_tma_fed_axis_passes_equal_the_one_shot_kernels():
     d = cases[0][0]
     check_against_oracle(d, run_gpu(d, orient_batch=3), oracle_ref(d))
     assert max(run_gpu(big, orient_batch=2)["imf"].tool_info(0).P) > 256
+
+
+
+@pytest.mark.parametrize("seed,n", [(4, (37, 45, 70)), (9, (61, 23, 50))])
+def test_level_minimum_equals_pairwise_minimum(seed, n):
+    """The minimum over sharp points with dyadic min levels built in the tile (option) and with
+    pairwise minima per run (default) select the same minimum (min is exact): f, f_bar, Gamma and A are
+    bit-identical, for every orientation-group split, and the result meets the contract; runs
+    longer than 16 (a 40-voxel cutter laid along x) exercise levels 3 and 4."""
+    d = _small3d(seed=seed, n=n, n_orient=9)
+    base = run_gpu(d, orient_batch=5, erode_levels=False)
+    for g in (0, 1, 3):
+        got = run_gpu(d, orient_batch=5, erode_groups=g, erode_levels=True)
+        for k in ("f", "fbar", "secluded", "accessible"):
+            assert np.array_equal(got[k], base[k]), (g, k)
+    check_against_oracle(d, base, oracle_ref(d))
+    c, s_ = np.cos(np.pi / 4), np.sin(np.pi / 4)
+    quats = np.array([[c, 0, s_, 0], [c, 0, -s_, 0], [1, 0, 0, 0]])
+    rho = synth.beam_density((90, 30, 26), n_beams=8, seed=11)
+    d2 = synth.Design(rho, synth.slab_fixture(rho.shape, 2, axis="z"), [synth.cylinder_tool(2, 40, 3, 4, quats)])
+    a = run_gpu(d2, orient_batch=3, erode_levels=True)
+    b = run_gpu(d2, orient_batch=3, erode_levels=False)
+    for k in ("f", "fbar", "secluded", "accessible"):
+        assert np.array_equal(a[k], b[k]), k
+    check_against_oracle(d2, a, oracle_ref(d2))
