@@ -47,11 +47,13 @@ WORKLOADS = {
 }
 
 
-def make_design(name, seed):
+def make_design(name, seed, n_orient=0):
     from paper_2002_07627_gb300 import synth
     if name == "planar64":
         return synth.config_planar64(seed=seed)
-    w = WORKLOADS[name]
+    w = dict(WORKLOADS[name])
+    if n_orient > 0:
+        w["n_orient"] = n_orient
     if "tool" in w:
         rc, lc, rh, lh = w["tool"]
         return synth.config_beams(w["n"], w["n_beams"], w["n_orient"], seed=seed, r_cut=rc, l_cut=lc, r_hold=rh,
@@ -451,7 +453,7 @@ class Workload:
         import torch
         from paper_2002_07627_gb300 import binding
         self.name = name
-        self.d = make_design(name, seed)
+        self.d = make_design(name, seed, args.orientations if name == args.workload else 0)
         self.shape = self.d.rho.shape
         self.nG = int(np.prod(self.shape))
         self.n_orient = sum(len(t.quats) for t in self.d.tools)
@@ -848,6 +850,8 @@ def main():
                     help="radix-stage FFT passes everywhere (comparison with the two-pass register FFT)")
     ap.add_argument("--precision", choices=["auto", "fft", "direct"], default="fft",
                     help="collision path: FP32 FFT, BF16-hi/lo tcgen05 direct, or autotuned")
+    ap.add_argument("--orientations", type=int, default=0,
+                    help="orientation count of the workload (0: the workload's own; smaller cases for profiling)")
     ap.add_argument("--to-grid", type=int, nargs=2, default=[256, 128], help="2D optimisation grid (nelx nely)")
     ap.add_argument("--to-iters", type=int, default=40)
     ap.add_argument("--batch-designs", type=int, default=64)
