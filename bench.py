@@ -481,7 +481,7 @@ class Workload:
         a = self.args
         imf = binding.Imf(self.shape, orient_batch=a.orient_batch, precision=self.prec, erode_groups=a.erode_groups,
                           fft_stages_only=a.fft_stages_only, accessible_by_sweep=by_sweep,
-                          fft_wide_pencils=a.fft_wide_pencils, erode_levels=a.erode_levels)
+                          fft_wide_pencils=a.fft_wide_pencils, erode_levels=a.erode_levels, fft_tma=a.fft_tma)
         imf.set_tools(self.d.tools)
         return imf
 
@@ -844,6 +844,8 @@ def main():
                          "exact) instead of the sweep")
     ap.add_argument("--fft-wide-pencils", type=int, default=-1,
                     help="launch shape of the big-factor FFT passes (imf_options.fft_wide_pencils; -1 default)")
+    ap.add_argument("--fft-tma", type=int, default=-1,
+                    help="launch form of the y / z FFT passes (imf_options.fft_tma; -1 default)")
     ap.add_argument("--erode-levels", action="store_true",
                     help="minimum over sharp points with dyadic min levels instead of pairwise minima per run")
     ap.add_argument("--fft-stages-only", action="store_true",

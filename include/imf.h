@@ -104,15 +104,17 @@ typedef struct {
     int sharp_k;             /* points kept by IMF_SHARP_NEAREST (>= 1; default 1)             */
     int fft_wide_pencils;    /* launch shape of the y / z FFT passes whose padded length has a
                                 factor above 16 (same arithmetic, same results): bit 0 = 16
-                                pencils per block (128-byte rows) for the z pass with the
-                                spectral product, bit 1 = for the other passes, else 8 per
-                                block; -1 = library default (imf_default_options)              */
-    int fft_tma;             /* two-pass y / z FFT passes as persistent kernels fed by
+                                pencils per block or per copy-fed item (128-byte rows) for the z
+                                pass with the spectral product, bit 1 = for the other passes,
+                                else 8; -1 = library default (16 for every pass)               */
+    int fft_tma;             /* launch form of the two-pass y / z FFT passes (same arithmetic,
+                                same results): bits 0-1 for the z pass with the spectral
+                                product, bits 2-3 for the other passes; 0 = one-shot blocks that
+                                load their pencils into registers, 1 = persistent blocks fed by
                                 tensor-memory-accelerator copies through a two-stage shared-
-                                memory pipeline instead of one-shot blocks that load their
-                                pencils into registers (same arithmetic, same results): bit 0 =
-                                the z pass with the spectral product, bit 1 = the other passes;
-                                -1 = library default (bit 0 only)                              */
+                                memory pipeline, 2 = the same with a producer warp and consumer
+                                warps that meet once per item; -1 = library default (1 for
+                                every pass)                                                    */
     int erode_levels;        /* minimum over sharp points: 1 = dyadic min levels built in the
                                 shared-memory tile (one three-input minimum per output and run
                                 of any length, but every row's levels rebuilt per chunk), 0

@@ -73,7 +73,10 @@ bool launch_axis2_tma(int sign, const AxisArgs &a, int nbatch, int norient, cuda
     if (a.A2 <= 0 || a.B2 <= 0) return false;
     const bool big = a.A2 > fft2::kMaxFactor;
     if (!fft2::is_split_choice(a.A2, a.B2, big ? fft2::kMaxFactorBig : fft2::kMaxFactor)) return false;
-    const int W = big ? 8 : 16;
+    const bool ws = a.tma == 2;            // warp-specialised: 8 pencils per item for both shapes
+    // big factors: 16 pencils per item (128-byte rows per copy) where the option asks for it
+    const bool wide = a.mul ? (a.wide & 1) != 0 : (a.wide & 2) != 0;
+    const int W = ws ? 8 : big ? (wide ? 16 : 8) : 16;
     const int L = a.A2 * a.B2;
     if (!big && L < kMinLength) return false;
     Params P{};
@@ -105,10 +108,11 @@ bool launch_axis2_tma(int sign, const AxisArgs &a, int nbatch, int norient, cuda
     }
     if (sign < 0 && mul) return false;
     const int v = sign < 0 ? 0 : mul ? 2 : 1;
-    if (big) return v == 0 ? launch_tma_b0(in_map, mul_map, P, s) : v == 1 ? launch_tma_b1(in_map, mul_map, P, s)
-                                                                         : launch_tma_b2(in_map, mul_map, P, s);
-    return v == 0 ? launch_tma_s0(in_map, mul_map, P, s) : v == 1 ? launch_tma_s1(in_map, mul_map, P, s)
-                                                                  : launch_tma_s2(in_map, mul_map, P, s);
+    if (big) return v == 0 ? launch_tma_b0(in_map, mul_map, P, ws, W, s)
+                  : v == 1 ? launch_tma_b1(in_map, mul_map, P, ws, W, s)
+                           : launch_tma_b2(in_map, mul_map, P, ws, W, s);
+    return v == 0 ? launch_tma_s0(in_map, mul_map, P, ws, W, s) : v == 1 ? launch_tma_s1(in_map, mul_map, P, ws, W, s)
+                                                                         : launch_tma_s2(in_map, mul_map, P, ws, W, s);
 }
 
 } // namespace imf

@@ -30,6 +30,8 @@ namespace imf {
 namespace tma_fft {
 
 constexpr int kStages = 2;
+
+int sm_count();   // multiprocessors of the current device (fft_tma.cu)
 // shortest pencil of the 16-slot shape the persistent kernel is built for (shorter ones, on
 // tiny grids, keep the one-shot kernel; fewer instances keep the build short)
 constexpr int kMinLength = 64;
@@ -43,6 +45,7 @@ struct Params {
 };
 
 template <int W> __host__ __device__ constexpr int threads(bool big) { return W * (big ? 32 : 16); }
+static_assert(threads<16>(true) == 512, "the wide big-factor shape runs 512 threads");
 
 __device__ __forceinline__ void decode_item(const Params &P, long it, int &chunk, int &o, int &b)
 {
@@ -188,10 +191,198 @@ __global__ void __launch_bounds__(threads<W>(BIG))
     else fft2::with_size(A, outer);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Warp-specialised variant: warp 0 is the producer (one lane issues the tensor copies), the
+// other warps are consumers, 8 NA threads of them (pencil w = thread & 7, slot p = thread >> 3),
+// so no warp idles through both DFT passes. Each stage has a "full" mbarrier (the copy's bytes)
+// and an "empty" one (one arrival per consumer warp once it has read the stage), so the producer
+// refills a stage as soon as it is free instead of at a block-wide barrier. Consumers meet once
+// per item, at a named reduction barrier after writing the tile, which also makes them agree on a
+// timed-out copy; the tile is double-buffered where shared memory allows (else a second named
+// barrier guards it). Block barriers are never used after the set-up.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool bar_red_or(int id, int nthreads, bool v)
+{
+    uint32_t r;
+    asm volatile("{\n.reg .pred pi, po;\nsetp.ne.u32 pi, %1, 0;\nbar.red.or.pred po, %2, %3, pi;\nselp.u32 %0, 1, 0, po;\n}\n"
+                 : "=r"(r)
+                 : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+                 : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void bar_named(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+struct WsLayout {
+    int ntiles;           // 1 or 2 tile buffers
+};
+
+template <int S, int MUL, int W, int NA, int NB>
+__device__ __forceinline__ void ws_items(const Params &P, const void *in_map, const void *mul_map, float2 *st,
+                                         size_t half, size_t stage, float2 *tile, int ntiles, const float2 *tw,
+                                         uint64_t *full, uint64_t *empty)
+{
+    constexpr int LOGW = W == 8 ? 3 : 4;
+    const AxisArgs &a = P.a;
+    const long G = gridDim.x, first = blockIdx.x;
+    const long mine = (P.items - first + G - 1) / G;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncons = (int)blockDim.x - 32;
+    const size_t tsz = (size_t)NA * NB * W;
+    if (warp == 0) {
+        // producer: one lane issues every copy of this block, refilling a stage once its empty
+        // barrier shows that every consumer warp has read it
+        if (lane != 0) return;
+        for (long k = 0; k < mine; ++k) {
+            const int s = (int)(k % kStages);
+            if (k >= kStages && !tc::mbar_wait(&empty[s], (uint32_t)((k / kStages - 1) & 1))) {
+                if (a.status) atomicCAS(a.status, 0, (int)IMF_ERR_TIMEOUT);
+                // the consumers time out on the stage this copy would have filled
+                for (long q = k - kStages + 1; q < k; ++q)
+                    if (q >= 0) tc::mbar_wait(&full[q % kStages], (uint32_t)((q / kStages) & 1));
+                return;
+            }
+            tc::fence_async_smem();
+            issue_item<MUL, W>(P, in_map, mul_map, first + k * G, st + s * stage, st + s * stage + half, &full[s]);
+        }
+        return;
+    }
+    const int ct = threadIdx.x - 32, w = ct & (W - 1), p = ct >> LOGW;
+    for (long k = 0; k < mine; ++k) {
+        const int s = (int)(k % kStages);
+        const bool timeout = !tc::mbar_wait(&full[s], (uint32_t)((k / kStages) & 1));
+        const float2 *sin_ = st + s * stage, *smul = sin_ + half;
+        float2 v[NA];
+        const bool act = p < NB;
+        if (act) {
+#pragma unroll
+            for (int n2 = 0; n2 < NA; ++n2) {
+                const int j = p + NB * n2;
+                v[n2] = sin_[j * W + w];
+                if (MUL) v[n2] = c_mul(v[n2], smul[j * W + w]);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&empty[s]);
+        float2 *tl = tile + (ntiles == 2 ? (size_t)(k & 1) * tsz : 0);
+        if (act) {
+            fft2::dft_reg<S, NA>(v);
+            fft2::twiddle<S, NA>(v, p, tw);
+#pragma unroll
+            for (int k2 = 0; k2 < NA; ++k2) tl[(p * NA + k2) * W + w] = v[k2];
+        }
+        if (bar_red_or(1, ncons, timeout)) {
+            if (a.status) atomicCAS(a.status, 0, (int)IMF_ERR_TIMEOUT);
+            return;
+        }
+        int chunk, o, b;
+        decode_item(P, first + k * G, chunk, o, b);
+        const int c = chunk * W + w;
+        if (p < NA && c < a.nx) {
+            float2 u[NB];
+#pragma unroll
+            for (int n1 = 0; n1 < NB; ++n1) u[n1] = tl[(n1 * NA + p) * W + w];
+            fft2::dft_reg<S, NB>(u);
+            float2 *out = a.out + (long)o * a.out_so + (long)b * a.out_sb + c;
+#pragma unroll
+            for (int k1 = 0; k1 < NB; ++k1) {
+                const int j = p + NA * k1 - a.j0;
+                if (j >= 0 && j < a.lout) {
+                    float2 y = c_scale(u[k1], a.scale);
+                    if (a.conj_out) y.y = -y.y;
+                    out[(long)j * a.out_sl] = y;
+                }
+            }
+        }
+        // one tile: its readers finish before the next item's pass 1 rewrites it
+        if (ntiles == 1) bar_named(2, ncons);
+    }
+}
+
+template <int S, bool BIG, int MUL, int W>
+__global__ void __launch_bounds__(256) axis2_ws_kernel(const __grid_constant__ CUtensorMap in_map,
+                                                       const __grid_constant__ CUtensorMap mul_map, Params P, int ntiles)
+{
+    extern __shared__ unsigned char smraw[];
+    const int A = P.a.A2, B = P.a.B2, L = A * B;
+    unsigned char *base = smraw + ((128 - (tc::smem_addr(smraw) & 127)) & 127);
+    const size_t half = (size_t)P.lrows * W;
+    const size_t stage = half * (MUL ? 2 : 1);
+    float2 *st = reinterpret_cast<float2 *>(base);
+    float2 *tile = st + kStages * stage;
+    float2 *tw = tile + (size_t)ntiles * L * W;
+    uint64_t *full = reinterpret_cast<uint64_t *>(tw + L), *empty = full + kStages;
+    const int ncw = ((int)blockDim.x - 32) / 32;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = P.a.tw[i];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], ncw);
+        }
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    constexpr int maxA = BIG ? fft2::kMaxFactorBig : fft2::kMaxFactor;
+    auto outer = [&](auto AA) {
+        constexpr int NA = decltype(AA)::value;
+        auto inner = [&](auto BB) {
+            constexpr int NB = decltype(BB)::value;
+            if constexpr (fft2::is_split_choice(NA, NB, maxA) &&
+                          (BIG ? NA > fft2::kMaxFactor : NA * NB >= kMinLength))
+                ws_items<S, MUL, W, NA, NB>(P, &in_map, &mul_map, st, half, stage, tile, ntiles, tw, full, empty);
+        };
+        if constexpr (BIG) fft2::with_size_big(B, inner);
+        else fft2::with_size(B, inner);
+    };
+    if constexpr (BIG) fft2::with_size_big(A, outer);
+    else fft2::with_size(A, outer);
+}
+
+// threads of the warp-specialised block: the producer warp and 8 NA consumer threads in warps
+inline int ws_threads(int A) { return 32 + ((8 * A + 31) / 32) * 32; }
+
+inline size_t ws_smem_bytes(const Params &P, int W, bool mul, int ntiles)
+{
+    const int L = P.a.A2 * P.a.B2;
+    return 128 + (size_t)kStages * P.lrows * W * 8 * (mul ? 2 : 1) + (size_t)ntiles * L * W * 8 + (size_t)L * 8 +
+           2 * kStages * 8;
+}
+
+template <int S, bool BIG, int MUL, int W>
+bool launch_ws(const CUtensorMap &in_map, const CUtensorMap &mul_map, Params &P, cudaStream_t s)
+{
+    static_assert(W == 8, "the warp-specialised pass maps 8 pencils per thread row");
+    const int T = ws_threads(P.a.A2);
+    if (T > 256) return false;
+    auto kernel = axis2_ws_kernel<S, BIG, MUL, W>;
+    // two tiles when two blocks of that size still fit an SM, else one
+    int ntiles = 2;
+    size_t smem = ws_smem_bytes(P, W, MUL != 0, 2);
+    if (2 * (smem + 1024) > 228 * 1024) {
+        ntiles = 1;
+        smem = ws_smem_bytes(P, W, MUL != 0, 1);
+    }
+    if (smem > 227 * 1024) return false;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, T, smem) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    const long blocks = P.items < (long)per * sm_count() ? P.items : (long)per * sm_count();
+    kernel<<<(unsigned)blocks, T, smem, s>>>(in_map, mul_map, P, ntiles);
+    return true;
+}
+
 // The six instances (16-slot shape s*, 32-slot shape b*; variant 0 = forward, 1 = inverse,
 // 2 = inverse with the pointwise factor), each compiled from fft_tma_inst.cu in its own
 // translation unit; false when nothing was launched.
-#define IMF_TMA_DECL(name) bool name(const CUtensorMap &in_map, const CUtensorMap &mul_map, Params &P, cudaStream_t s);
+#define IMF_TMA_DECL(name) bool name(const CUtensorMap &in_map, const CUtensorMap &mul_map, Params &P, bool ws, int W, cudaStream_t s);
 IMF_TMA_DECL(launch_tma_s0)
 IMF_TMA_DECL(launch_tma_s1)
 IMF_TMA_DECL(launch_tma_s2)
@@ -200,7 +391,6 @@ IMF_TMA_DECL(launch_tma_b1)
 IMF_TMA_DECL(launch_tma_b2)
 #undef IMF_TMA_DECL
 
-int sm_count();
 
 // Shared memory of one block: 128 bytes of alignment slack, the stages, the tile, the twiddles
 // and the barriers.

@@ -19,12 +19,14 @@
 namespace imf {
 namespace tma_fft {
 
-bool IMF_TMA_NAME(const CUtensorMap &in_map, const CUtensorMap &mul_map, Params &P, cudaStream_t s)
+bool IMF_TMA_NAME(const CUtensorMap &in_map, const CUtensorMap &mul_map, Params &P, bool ws, int W, cudaStream_t s)
 {
     constexpr int S = IMF_TMA_VARIANT == 0 ? -1 : 1;
     constexpr int MUL = IMF_TMA_VARIANT == 2 ? 1 : 0;
     constexpr bool BIG = IMF_TMA_BIG != 0;
-    return launch_shape<S, BIG, MUL, BIG ? 8 : 16>(in_map, mul_map, P, s);
+    if (ws) return W == 8 && launch_ws<S, BIG, MUL, 8>(in_map, mul_map, P, s);
+    if (BIG && W == 16) return launch_shape<S, true, MUL, 16>(in_map, mul_map, P, s);
+    return W == (BIG ? 8 : 16) && launch_shape<S, BIG, MUL, BIG ? 8 : 16>(in_map, mul_map, P, s);
 }
 
 } // namespace tma_fft

@@ -32,9 +32,12 @@ using namespace imf;
 
 namespace {
 
-// default of imf_options::fft_wide_pencils: 16 pencils per block for the big-factor z pass with
-// the spectral product, 8 for the other big-factor passes
-constexpr int kFftWideDefault = 1;
+// defaults of imf_options::fft_wide_pencils and fft_tma: every big-factor y / z pass fed by
+// tensor copies with 16 pencils per item (128-byte rows per copy). Measured at 256^3 x 128 on one
+// box: z pass 10.6 ms (copies, 8 pencils) -> 7.8 ms (16 pencils); y pass 9.0 ms (one-shot, 8
+// pencils) -> 6.4 ms (copies, 16 pencils); the warp-specialised form with 8 pencils was slower
+constexpr int kFftWideDefault = 3;
+constexpr int kFftTmaDefault = 5;
 
 enum KernelId {
     KID_ROTATE, KID_SPEC, KID_RFFT_FWD, KID_AXIS_FWD, KID_AXIS_INV_MUL, KID_AXIS_INV, KID_IRFFT_THRESH,
@@ -595,11 +598,11 @@ int fft_wide(imf_handle h) { return h->opt.fft_wide_pencils >= 0 ? h->opt.fft_wi
 void axis_opts(imf_handle h, AxisArgs &a)
 {
     a.wide = fft_wide(h);
-    // bit 0: passes with the pointwise factor (the z pass of the collision convolution), bit 1:
-    // the others. Measured at 256^3 x 128: z pass 12.6 -> 8.8 ms with tensor copies; the y pass
-    // is faster as one-shot blocks (8.2 against 10.1 ms), so the default feeds only the z pass
-    const int m = h->opt.fft_tma < 0 ? 1 : h->opt.fft_tma;
-    a.tma = (a.mul ? (m & 1) : (m & 2)) != 0;
+    // bits 0-1: the pass with the pointwise factor (the z pass of the collision convolution),
+    // bits 2-3: the others; 0 = one-shot blocks, 1 = tensor-copy pipeline with block barriers,
+    // 2 = warp-specialised tensor-copy pipeline
+    const int m = h->opt.fft_tma < 0 ? kFftTmaDefault : h->opt.fft_tma;
+    a.tma = a.mul ? (m & 3) : ((m >> 2) & 3);
     a.status = h->dev_small;
 }
 
@@ -683,7 +686,8 @@ imf_status imf_create(const imf_options *opt, imf_handle *out)
     if (opt->erode_groups < 0) return IMF_ERR_INVALID_ARG;
     if (opt->sharp_sampling < IMF_SHARP_ALL || opt->sharp_sampling > IMF_SHARP_NEAREST) return IMF_ERR_INVALID_ARG;
     if (opt->fft_wide_pencils < -1 || opt->fft_wide_pencils > 3) return IMF_ERR_INVALID_ARG;
-    if (opt->fft_tma < -1 || opt->fft_tma > 3) return IMF_ERR_INVALID_ARG;
+    if (opt->fft_tma < -1 || opt->fft_tma > 15 || (opt->fft_tma >= 0 && ((opt->fft_tma & 3) == 3 || (opt->fft_tma >> 2) == 3)))
+        return IMF_ERR_INVALID_ARG;
     if (opt->sharp_sampling == IMF_SHARP_NEAREST && opt->sharp_k < 1) return IMF_ERR_INVALID_ARG;
     imf_handle h = new (std::nothrow) imf_handle_s();
     if (!h) return IMF_ERR_OOM;

@@ -638,7 +638,7 @@ def test_tma_fed_axis_passes_equal_the_one_shot_kernels():
              (_small3d(seed=5, n=(20, 18, 16), n_orient=4), {"accessible_by_sweep": True})]
     for d, kw in cases:
         b = run_gpu(d, orient_batch=3, fft_tma=0, **kw)
-        for mode in (-1, 3):          # the default (z pass only) and every pass
+        for mode in (-1, 5, 10):      # the default, every pass block-synchronous, every pass warp-specialised
             a = run_gpu(d, orient_batch=3, fft_tma=mode, **kw)
             for k in ("f", "fbar", "secluded", "accessible"):
                 assert np.array_equal(a[k], b[k]), (mode, k)
