@@ -481,7 +481,8 @@ class Workload:
         a = self.args
         imf = binding.Imf(self.shape, orient_batch=a.orient_batch, precision=self.prec, erode_groups=a.erode_groups,
                           fft_stages_only=a.fft_stages_only, accessible_by_sweep=by_sweep,
-                          fft_wide_pencils=a.fft_wide_pencils, erode_levels=a.erode_levels, fft_tma=a.fft_tma)
+                          fft_wide_pencils=a.fft_wide_pencils, erode_levels=a.erode_levels, fft_tma=a.fft_tma,
+                          fft_tma_x=a.fft_tma_x)
         imf.set_tools(self.d.tools)
         return imf
 
@@ -846,6 +847,8 @@ def main():
                     help="launch shape of the big-factor FFT passes (imf_options.fft_wide_pencils; -1 default)")
     ap.add_argument("--fft-tma", type=int, default=-1,
                     help="launch form of the y / z FFT passes (imf_options.fft_tma; -1 default)")
+    ap.add_argument("--fft-tma-x", type=int, default=-1,
+                    help="inverse x pass fed by tensor copies (imf_options.fft_tma_x; -1 default)")
     ap.add_argument("--erode-levels", action="store_true",
                     help="minimum over sharp points with dyadic min levels instead of pairwise minima per run")
     ap.add_argument("--fft-stages-only", action="store_true",

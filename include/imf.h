@@ -120,6 +120,10 @@ typedef struct {
                                 of any length, but every row's levels rebuilt per chunk), 0
                                 (default) = pairwise minima over each run; same results. Tiles
                                 with rows above 128 cells use 0                                */
+    int fft_tma_x;           /* the inverse x pass with the threshold, where it runs on its own
+                                (planes too large for the fused y + x pass): 1 = persistent
+                                blocks fed by tensor copies of whole rows, 0 = one-shot blocks;
+                                same results; -1 = library default (1)                        */
 } imf_options;
 
 /* Fill *opt with the defaults above (grid 0x0x0, which imf_create rejects). */

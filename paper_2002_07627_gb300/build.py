@@ -20,8 +20,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libimf.so")
 HOSTLIB = os.path.join(BUILD, "libimf_hosttest.so")
 
-CUDA_SOURCES = ["imf_api.cu", "fft_kernels.cu", "fft2_kernels.cu", "fft_tma.cu", "imf_kernels.cu", "erode.cu",
-                "direct_tc.cu", "noalloc.cu", "topopt2d.cu"]
+CUDA_SOURCES = ["imf_api.cu", "fft_kernels.cu", "fft2_kernels.cu", "fft_tma.cu", "fft_tma_x.cu", "imf_kernels.cu",
+                "erode.cu", "direct_tc.cu", "noalloc.cu", "topopt2d.cu"]
 # sources compiled more than once with different defines: (source, object name, defines); the
 # six instances of the TMA-fed axis pass build in parallel
 CUDA_VARIANTS = [("fft_tma_inst.cu", f"fft_tma_{'b' if big else 's'}{v}.o", [f"-DIMF_TMA_BIG={big}", f"-DIMF_TMA_VARIANT={v}"])

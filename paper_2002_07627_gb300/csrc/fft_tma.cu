@@ -56,6 +56,29 @@ bool encode(CUtensorMap *m, const void *ptr, int rank, int nx, long rows, long r
 
 } // namespace
 
+bool encode_tiled(CUtensorMap *m, const void *ptr, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
+                  const uint32_t *box)
+{
+    EncodeFn fn = encode_fn();
+    if (!fn || rank < 1 || rank > 5 || (reinterpret_cast<uint64_t>(ptr) & 15)) return false;
+    cuuint64_t dim[5], stride[4];
+    cuuint32_t bx[5], es[5];
+    for (int i = 0; i < rank; ++i) {
+        dim[i] = dims[i];
+        bx[i] = box[i];
+        es[i] = 1;
+        if (box[i] < 1 || box[i] > 256) return false;
+    }
+    for (int i = 0; i < rank - 1; ++i) {
+        stride[i] = strides_bytes[i];
+        if (stride[i] == 0 || stride[i] % 16 || stride[i] >= (1ull << 40)) return false;
+    }
+    if ((box[0] * 8) % 16) return false;
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)rank, const_cast<void *>(ptr), dim, stride, bx, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int sm_count()
 {
     static int n[64] = {0};

@@ -32,6 +32,10 @@ namespace tma_fft {
 constexpr int kStages = 2;
 
 int sm_count();   // multiprocessors of the current device (fft_tma.cu)
+// Tiled tensor map of 8-byte elements (complex64): dims innermost first, strides of dims 1.. in
+// bytes, box in elements; false when a tensor map cannot describe it (fft_tma.cu).
+bool encode_tiled(CUtensorMap *m, const void *ptr, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
+                  const uint32_t *box);
 // shortest pencil of the 16-slot shape the persistent kernel is built for (shorter ones, on
 // tiny grids, keep the one-shot kernel; fewer instances keep the build short)
 constexpr int kMinLength = 64;

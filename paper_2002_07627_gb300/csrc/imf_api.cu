@@ -670,6 +670,7 @@ void imf_default_options(imf_options *opt)
     opt->fft_wide_pencils = -1;
     opt->fft_tma = -1;
     opt->erode_levels = 0;
+    opt->fft_tma_x = -1;
 }
 
 imf_status imf_create(const imf_options *opt, imf_handle *out)
@@ -686,6 +687,7 @@ imf_status imf_create(const imf_options *opt, imf_handle *out)
     if (opt->erode_groups < 0) return IMF_ERR_INVALID_ARG;
     if (opt->sharp_sampling < IMF_SHARP_ALL || opt->sharp_sampling > IMF_SHARP_NEAREST) return IMF_ERR_INVALID_ARG;
     if (opt->fft_wide_pencils < -1 || opt->fft_wide_pencils > 3) return IMF_ERR_INVALID_ARG;
+    if (opt->fft_tma_x < -1 || opt->fft_tma_x > 1) return IMF_ERR_INVALID_ARG;
     if (opt->fft_tma < -1 || opt->fft_tma > 15 || (opt->fft_tma >= 0 && ((opt->fft_tma & 3) == 3 || (opt->fft_tma >> 2) == 3)))
         return IMF_ERR_INVALID_ARG;
     if (opt->sharp_sampling == IMF_SHARP_NEAREST && opt->sharp_k < 1) return IMF_ERR_INVALID_ARG;
@@ -1232,7 +1234,8 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
                     launch_axis_fft(1, ay, t.win[2], nb, s);
                 }
                 Launch L(h, KID_IRFFT_THRESH, s);
-                launch_irfft_threshold(ax, nb, s);
+                const int tx = h->opt.fft_tma_x < 0 ? 1 : h->opt.fft_tma_x;
+                if (!(tx && launch_irfft2_tma(ax, t.Hs, nb, s))) launch_irfft_threshold(ax, nb, s);
             }
             TRY(tail_batch(h, t, rho, fix, o0, nb, s));
             h->last_batch_base = o0;

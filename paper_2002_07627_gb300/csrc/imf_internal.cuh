@@ -87,6 +87,9 @@ struct IrfftArgs {
 void launch_axis_fft(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s);
 void launch_rfft_fwd(const RfftArgs &a, cudaStream_t s);
 void launch_irfft_threshold(const IrfftArgs &a, int norient, cudaStream_t s);
+// The same inverse x pass as a persistent kernel fed by tensor copies of whole rows (hs complex
+// each, contiguous); false (nothing launched) where it does not apply.
+bool launch_irfft2_tma(const IrfftArgs &a, int hs, int norient, cudaStream_t s);
 // two-pass register variants (fft2_kernels.cu); the dispatchers above call them when A2 > 0
 void launch_axis2(int sign, const AxisArgs &a, int nbatch, int norient, cudaStream_t s);
 // The same pass as a persistent kernel fed by tensor copies; false (nothing launched) where

@@ -625,9 +625,10 @@ def test_accessible_sets_and_greedy_process_plan_match_oracle():
 
 
 def test_tma_fed_axis_passes_equal_the_one_shot_kernels():
-    """The persistent y / z FFT passes fed by tensor copies (the default for the z pass, optional
-    for the others) run the same arithmetic as the one-shot kernels (fft_tma 0): f, f_bar, Gamma
-    and A are bit-identical with either choice, on grids whose
+    """The persistent y / z FFT passes fed by tensor copies (block-synchronous or warp-
+    specialised, 8 or 16 pencils per item) and the copy-fed x pass run the same arithmetic as
+    the one-shot kernels (fft_tma 0, fft_tma_x 0): f, f_bar, Gamma and A are bit-identical with
+    every choice (the y and x passes forced into separate kernels), on grids whose
     padded lengths use the 16-slot shape, the 32-slot shape (a y length above 256) and lengths
     below the persistent kernel's minimum (which keep the one-shot kernel); and the result meets
     the contract against the oracle."""
@@ -635,16 +636,24 @@ def test_tma_fed_axis_passes_equal_the_one_shot_kernels():
     big = synth.Design(rho, synth.slab_fixture(rho.shape, 1, axis="z"),
                        [synth.cylinder_tool(1, 4, 2, 3, synth.fibonacci_quats(3))])
     cases = [(_small3d(seed=4, n=(70, 66, 64), n_orient=5), {}), (big, {}),
-             (_small3d(seed=5, n=(20, 18, 16), n_orient=4), {"accessible_by_sweep": True})]
+             (_small3d(seed=5, n=(20, 18, 16), n_orient=4), {"accessible_by_sweep": True}),
+             (_small3d(seed=6, n=(150, 24, 20), n_orient=4), {"accessible_by_sweep": True})]
     for d, kw in cases:
-        b = run_gpu(d, orient_batch=3, fft_tma=0, **kw)
+        b = run_gpu(d, orient_batch=3, fft_tma=0, fft_tma_x=0, **kw)
         for mode in (-1, 5, 10):      # the default, every pass block-synchronous, every pass warp-specialised
-            a = run_gpu(d, orient_batch=3, fft_tma=mode, **kw)
-            for k in ("f", "fbar", "secluded", "accessible"):
-                assert np.array_equal(a[k], b[k]), (mode, k)
+            for wide in (-1, 0):
+                a = run_gpu(d, orient_batch=3, fft_tma=mode, fft_wide_pencils=wide, separate_yx_passes=True, **kw)
+                for k in ("f", "fbar", "secluded", "accessible"):
+                    assert np.array_equal(a[k], b[k]), (mode, wide, k)
     d = cases[0][0]
     check_against_oracle(d, run_gpu(d, orient_batch=3), oracle_ref(d))
     assert max(run_gpu(big, orient_batch=2)["imf"].tool_info(0).P) > 256
+    # the long x axis pads to M >= 64, where the copy-fed x pass applies; oracle parity too
+    d = cases[3][0]
+    got = run_gpu(d, orient_batch=3, separate_yx_passes=True)
+    assert got["imf"].tool_info(0).P[0] // 2 >= 64
+    assert "irfft_x_threshold" in _kernels_run(got["imf"], d)
+    check_against_oracle(d, got, oracle_ref(d))
 
 
 
