@@ -482,7 +482,7 @@ class Workload:
         imf = binding.Imf(self.shape, orient_batch=a.orient_batch, precision=self.prec, erode_groups=a.erode_groups,
                           fft_stages_only=a.fft_stages_only, accessible_by_sweep=by_sweep,
                           fft_wide_pencils=a.fft_wide_pencils, erode_levels=a.erode_levels, fft_tma=a.fft_tma,
-                          fft_tma_x=a.fft_tma_x)
+                          fft_tma_x=a.fft_tma_x, sweep_loop=a.sweep_loop)
         imf.set_tools(self.d.tools)
         return imf
 
@@ -849,6 +849,8 @@ def main():
                     help="launch form of the y / z FFT passes (imf_options.fft_tma; -1 default)")
     ap.add_argument("--fft-tma-x", type=int, default=-1,
                     help="inverse x pass fed by tensor copies (imf_options.fft_tma_x; -1 default)")
+    ap.add_argument("--sweep-loop", action="store_true",
+                    help="sweep with each thread walking the batch's orientations (early exit per word)")
     ap.add_argument("--erode-levels", action="store_true",
                     help="minimum over sharp points with dyadic min levels instead of pairwise minima per run")
     ap.add_argument("--fft-stages-only", action="store_true",

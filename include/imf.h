@@ -124,6 +124,10 @@ typedef struct {
                                 (planes too large for the fused y + x pass): 1 = persistent
                                 blocks fed by tensor copies of whole rows, 0 = one-shot blocks;
                                 same results; -1 = library default (1)                        */
+    int sweep_loop;          /* the sweep of Eq. eq_conv_A: 0 (default) = one thread per output
+                                word and orientation of the batch; 1 = each thread walks the
+                                batch's orientations for its word and stops once the word is
+                                fully accessible (same results; slower where measured)         */
 } imf_options;
 
 /* Fill *opt with the defaults above (grid 0x0x0, which imf_create rejects). */

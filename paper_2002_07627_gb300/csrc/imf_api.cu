@@ -671,6 +671,7 @@ void imf_default_options(imf_options *opt)
     opt->fft_tma = -1;
     opt->erode_levels = 0;
     opt->fft_tma_x = -1;
+    opt->sweep_loop = 0;
 }
 
 imf_status imf_create(const imf_options *opt, imf_handle *out)
@@ -1103,7 +1104,10 @@ imf_status tail_batch(imf_handle h, const Tool &t, const float *rho, const uint8
             a.perm = t.perm_dev;
         }
         Launch L(h, KID_SWEEP, s);
-        launch_sweep(a, s);
+        // per-orientation sets need every orientation's own sweep (no early exit); the loop form
+        // (early exit per word) measured slower: 9.5 against 5.1 ms at 256^3 x 128
+        if (h->opt.sweep_loop && !h->aset) launch_sweep_loop(a, h->nsm, s);
+        else launch_sweep(a, s);
     }
     {
         Erode2Args a{};

@@ -170,6 +170,8 @@ struct SweepArgs {
 };
 void launch_sweep_levels(const SweepLevelsArgs &a, cudaStream_t s);
 void launch_sweep(const SweepArgs &a, cudaStream_t s);
+// the sweep with the batch's orientations walked inside each thread (early exit per word)
+void launch_sweep_loop(const SweepArgs &a, int nsm, cudaStream_t s);
 
 // Greedy machining process plan (Sec. 3.4.1) over per-orientation accessible sets.
 // remaining[w] = bits of the negative space Omega_0 and [rho <= tau] in word w of [nz][ny][awords]

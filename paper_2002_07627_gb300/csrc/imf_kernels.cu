@@ -1,6 +1,7 @@
 // IMF kernels other than the FFT passes: tool resampling, the exact near-threshold
 // re-check, the sweep of the cutter over the free translations, the minimum over sharp
 // points and orientations, and the normalisation / penalty tail of Alg. 1 and Alg. 2.
+#include <algorithm>
 #include <cfloat>
 
 #include "imf_internal.cuh"
@@ -145,6 +146,55 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a)
             const uint32_t add = acc & full & ~old;
             if (add) atomicOr(dstw, add);
             if (per) a.A_per[(long)a.perm[og] * a.a_per_so + ((long)z * a.ny + y) * a.awords + q] = acc & full;
+        }
+    }
+}
+
+// The same sweep with the orientations of the batch walked inside the thread: one thread per
+// output word and orientation group (blockIdx.y of `ngroups`), which stops as soon as its word
+// is fully accessible, so most words of the air around a part leave after a few orientations
+// instead of being swept by every orientation of the batch in parallel. A block stages each
+// orientation's runs and leaves the group's loop once all its words are full. The groups of a
+// word merge with an atomic OR; A only grows, so the result does not depend on the grouping.
+__global__ void __launch_bounds__(256) sweep_loop_kernel(SweepArgs a, int ngroups)
+{
+    __shared__ int4 sp[kSweepStage];
+    const long total = (long)a.awords * a.ny * a.nz;
+    const int grp = blockIdx.y;
+    const int ob0 = grp * a.nb / ngroups, ob1 = (grp + 1) * a.nb / ngroups;
+    const long tstride = (long)gridDim.x * blockDim.x;
+    for (long tb = (long)blockIdx.x * blockDim.x; tb < total; tb += tstride) {
+        const long t = tb + threadIdx.x;
+        const bool live = t < total;
+        const int q = live ? (int)(t % a.awords) : 0;
+        const int y = live ? (int)((t / a.awords) % a.ny) : 0;
+        const int z = live ? (int)(t / ((long)a.awords * a.ny)) : 0;
+        uint32_t *dstw = a.A + ((long)z * a.ny + y) * a.awords + q;
+        const int rem = a.nx - 32 * q;
+        const uint32_t full = rem < 32 ? (1u << rem) - 1u : 0xffffffffu;
+        const uint32_t old = live ? *dstw : full;
+        uint32_t acc = old;
+        for (int ob = ob0; ob < ob1; ++ob) {
+            if (__syncthreads_and((acc & full) == full)) break;
+            const int og = a.orient_base + ob;
+            const int m0 = a.pair_start[og], m1 = a.pair_start[og + 1];
+            const uint32_t *base = a.bits + ob * a.b_so + (long)z * a.b_sz + (long)y * a.b_sy + q;
+            for (int c0 = m0; c0 < m1; c0 += kSweepStage) {
+                const int cn = min(kSweepStage, m1 - c0);
+                __syncthreads();
+                for (int i = threadIdx.x; i < cn; i += blockDim.x) sp[i] = a.pairs[c0 + i];
+                __syncthreads();
+                if ((acc & full) == full) continue;
+#pragma unroll 4
+                for (int i = 0; i < cn; ++i) {
+                    const int4 d = sp[i];
+                    acc |= sweep_pair_bits(base + (long)d.w * a.lstride + d.x, d);
+                }
+            }
+        }
+        if (live) {
+            const uint32_t add = acc & full & ~old;
+            if (add) atomicOr(dstw, add);
         }
     }
 }
@@ -347,6 +397,16 @@ void launch_scatter_tool(float *dst, int Px, int Py, int Pz, const uint32_t *off
 void launch_sweep_levels(const SweepLevelsArgs &a, cudaStream_t s)
 {
     sweep_levels_kernel<<<blocks_for(a.n, kThreads, 152 * 8), kThreads, 0, s>>>(a);
+}
+
+void launch_sweep_loop(const SweepArgs &a, int nsm, cudaStream_t s)
+{
+    // about 2048 resident threads per SM: as many orientation groups as that takes
+    const long words = (long)a.awords * a.ny * a.nz;
+    const long want = (long)nsm * 2048;
+    int groups = (int)std::min<long>(a.nb, std::max<long>(1, (want + words - 1) / words));
+    dim3 grid(blocks_for(words, kThreads, 1 << 20), groups);
+    sweep_loop_kernel<<<grid, kThreads, 0, s>>>(a, groups);
 }
 
 void launch_sweep(const SweepArgs &a, cudaStream_t s)

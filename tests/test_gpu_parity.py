@@ -679,3 +679,17 @@ def test_level_minimum_equals_pairwise_minimum(seed, n):
     for k in ("f", "fbar", "secluded", "accessible"):
         assert np.array_equal(a[k], b[k]), k
     check_against_oracle(d2, a, oracle_ref(d2))
+
+
+
+def test_sweep_loop_equals_parallel_sweep():
+    """The sweep of Eq. eq_conv_A with the batch's orientations walked inside each thread (early
+    exit once a word is fully accessible, option) and with one thread per word and orientation
+    (default) give the same accessible set (A only grows), on several batch splits; both meet the contract."""
+    d = _small3d(seed=11, n=(45, 38, 33), n_orient=13)
+    ref = oracle_ref(d)
+    for ob in (4, 13):
+        a = run_gpu(d, orient_batch=ob, accessible_by_sweep=True, sweep_loop=True)
+        b = run_gpu(d, orient_batch=ob, accessible_by_sweep=True)
+        assert np.array_equal(a["accessible"], b["accessible"]), ob
+        check_against_oracle(d, a, ref)
