@@ -280,6 +280,11 @@ def run_batch(args):
     br.check()
     tb = statistics.median(times)
     chosen = sorted(e.batch for e in br.entries)
+    tuned = {}
+    for e in br.entries:
+        for k, v in (e.tuned or {}).items():
+            tuned.setdefault(k, {})
+            tuned[k][str(v)] = tuned[k].get(str(v), 0) + 1
     br.close()
     out = {"metric": METRIC, "value": units / tb, "unit": UNIT, "n_gpus": 1, "steps": len(times),
            "warmup": 1, "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -288,7 +293,7 @@ def run_batch(args):
                                   f"16-128 orientations, cutter radius 2-6 (holder 2.5x)",
                       "designs": len(ds), "voxel_orientations_per_pass": units,
                       "form": f"resident handles, autotuned orientation batch, CUDA graphs, {args.streams} streams",
-                      "autotuned_batches": chosen},
+                      "autotuned_batches": chosen, "autotuned_options": tuned},
            "plain": {"value": units / tp, "ms_per_pass": tp * 1e3,
                      "form": "one design at a time on one stream, default options, no graphs, the batched "
                              "form's memory cap per handle"},

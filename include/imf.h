@@ -84,7 +84,8 @@ typedef struct {
                                 (work-unit granularity only; the result does not depend on it);
                                 0 = chosen from the grid and the SM count                      */
     int fft_stages_only;     /* 1: every FFT pass uses radix stages (2..8) even where a two-pass
-                                register split exists (comparisons and tests); 0 = default    */
+                                register split exists (comparisons, tests, the autotuner); read
+                                at every launch; 0 = default                                  */
     int accessible_by_sweep; /* the accessible output of imf_compute: 0 = with one tool whose
                                 sharp points are its whole cutter, A = [f <= theta] (exact:
                                 both say "some cutter point lies on a free translation"; the
@@ -256,11 +257,19 @@ imf_status imf_launch_graph(imf_handle h, void *cuda_stream);
 
 /*
  * Autotuner: times imf_compute on these arrays for each orientation-batch size in
- * {4, 8, 16, 32, 64} (capped by the orientation count and the HBM budget), keeps the fastest in
- * the handle's options and returns it in *best (NULL allowed). Synchronous; it replaces a
- * captured graph, which must be captured again. */
+ * {4, 8, 16, 32, 64, 128} (capped by the orientation count and the HBM budget) and keeps the
+ * fastest; then, by coordinate descent from the handle's options, the FFT form (two-pass
+ * register splits or radix stages), the launch form of the y / z passes (fft_tma), their
+ * pencils per block (fft_wide_pencils), the x pass's form (fft_tma_x) and the orientation groups
+ * of the minimum over sharp points (erode_groups), keeping a change only when it is 3 % faster;
+ * then, with IMF_AUTO, the collision path. Every choice selects among equivalent kernels, so
+ * the results do not change. The chosen batch goes to *best (NULL allowed); imf_get_options
+ * reads the rest. Synchronous; it replaces a captured graph, which must be captured again. */
 imf_status imf_autotune(imf_handle h, const float *rho_omega, const uint8_t *fixture, float *imf_bar,
                         uint8_t *secluded, void *cuda_stream, int *best);
+
+/* The handle's current options (after imf_autotune: the tuned ones). */
+imf_status imf_get_options(imf_handle h, imf_options *out);
 
 /* Wait for the last stream used by the handle and return the device-side status
  * (IMF_OK, IMF_ERR_OVERFLOW, IMF_ERR_TIMEOUT) or IMF_ERR_CUDA; clears it. */

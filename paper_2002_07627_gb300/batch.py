@@ -1,8 +1,9 @@
 """Batched IMF evaluation of many designs of uneven size (the batched form).
 
-Each design keeps a resident libimf handle (tool spectra stay on the device), its orientation
-batch size is chosen by the library's autotuner for its grid and tool, and its imf_compute is
-captured once as a CUDA graph. A run replays every design's graph over a pool of streams, so
+Each design keeps a resident libimf handle (tool spectra stay on the device); the library's
+autotuner picks, for its grid and tool, the orientation batch, the FFT form (two-pass splits or
+radix stages), the launch forms of the FFT passes and the work units of the minimum over sharp
+points; and its imf_compute is captured once as a CUDA graph. A run replays every design's graph over a pool of streams, so
 small designs overlap on the device and launch gaps disappear. The plain form for comparison
 runs the designs one after another on one stream with default options and no graphs.
 
@@ -48,6 +49,7 @@ class _Entry:
     sec: object
     units: int
     batch: int = 0
+    tuned: dict | None = None
 
 
 class BatchRunner:
@@ -72,6 +74,9 @@ class BatchRunner:
             s = self.streams[len(self.entries) % len(self.streams)]
             if autotune:
                 e.batch = imf.autotune(rho, fix, stream=s)
+                o = imf.options()
+                e.tuned = {k: o[k] for k in ("orient_batch", "fft_stages_only", "fft_tma", "fft_wide_pencils",
+                                             "fft_tma_x", "erode_groups")}
             if graphs:
                 imf.capture_graph(rho, fix, fbar, sec, stream=s)
             self.entries.append(e)

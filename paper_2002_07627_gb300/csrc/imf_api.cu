@@ -594,6 +594,14 @@ imf_status ensure_work(imf_handle h)
 // Pencils per block of the big-factor axis kernel (AxisArgs::wide): the option, or the default.
 int fft_wide(imf_handle h) { return h->opt.fft_wide_pencils >= 0 ? h->opt.fft_wide_pencils : kFftWideDefault; }
 
+// the two-pass split of a pass, or none (radix stages) when the handle asks for stages only
+template <typename Args> void set_split(imf_handle h, Args &a, const int *sp)
+{
+    const bool stages = h->opt.fft_stages_only != 0;
+    a.A2 = stages ? 0 : sp[0];
+    a.B2 = stages ? 0 : sp[1];
+}
+
 // launch options shared by every axis pass of the handle
 void axis_opts(imf_handle h, AxisArgs &a)
 {
@@ -624,7 +632,7 @@ imf_status forward_real_3d(imf_handle h, const Tool &t, const float *src, const 
         a.in = X1; a.in_sb = (long)ny * t.Hs; a.in_sl = t.Hs;
         a.out = X2; a.out_sb = (long)t.P[1] * t.Hs; a.out_sl = t.Hs;
         a.nx = t.Hx; a.lin = ny; a.j0 = 0; a.lout = t.P[1]; a.scale = 1.f; a.tw = t.twy; a.plan = t.ply;
-        a.A2 = t.sy[0]; a.B2 = t.sy[1]; axis_opts(h, a);
+        set_split(h, a, t.sy); axis_opts(h, a);
         Launch L(h, KID_AXIS_FWD, s);
         launch_axis_fft(-1, a, nz, 1, s);
     }
@@ -634,7 +642,7 @@ imf_status forward_real_3d(imf_handle h, const Tool &t, const float *src, const 
         a.out = out; a.out_sb = t.Hs; a.out_sl = (long)t.P[1] * t.Hs;
         a.nx = t.Hx; a.lin = nz; a.j0 = 0; a.lout = t.P[2]; a.scale = scale; a.conj_out = conj_out;
         a.tw = t.twz; a.plan = t.plz;
-        a.A2 = t.sz[0]; a.B2 = t.sz[1]; axis_opts(h, a);
+        set_split(h, a, t.sz); axis_opts(h, a);
         Launch L(h, KID_AXIS_FWD, s);
         launch_axis_fft(-1, a, t.P[1], 1, s);
     }
@@ -911,10 +919,11 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
     t.Hs = (t.Hx + 1) & ~1;
     t.gpx = (t.win[0] + 3) & ~3;
     t.wpr = (t.win[0] + 31) / 32 + 2;
-    const bool split = !h->opt.fft_stages_only;
-    if (!split || !fft2::choose_split(t.M, &t.sM[0], &t.sM[1])) t.sM[0] = t.sM[1] = 0;
-    if (!split || !fft2::choose_split(t.P[1], &t.sy[0], &t.sy[1], fft2::kMaxFactorBig)) t.sy[0] = t.sy[1] = 0;
-    if (!split || !fft2::choose_split(t.P[2], &t.sz[0], &t.sz[1], fft2::kMaxFactorBig)) t.sz[0] = t.sz[1] = 0;
+    // two-pass splits where they exist; launches use them unless fft_stages_only is set (then
+    // every pass runs radix stages), so the choice can change after planning
+    if (!fft2::choose_split(t.M, &t.sM[0], &t.sM[1])) t.sM[0] = t.sM[1] = 0;
+    if (!fft2::choose_split(t.P[1], &t.sy[0], &t.sy[1], fft2::kMaxFactorBig)) t.sy[0] = t.sy[1] = 0;
+    if (!fft2::choose_split(t.P[2], &t.sz[0], &t.sz[1], fft2::kMaxFactorBig)) t.sz[0] = t.sz[1] = 0;
     if (!make_plan(t.M, &t.plM) || !make_plan(t.P[1], &t.ply) || !make_plan(t.P[2], &t.plz)) {
         free_tool(h, t);
         return fail(h, IMF_ERR_INVALID_ARG, "no FFT plan for %d x %d x %d", t.P[0], t.P[1], t.P[2]);
@@ -1209,7 +1218,7 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
                 a.mul = h->rho_spec; a.mul_so = 0; a.mul_sb = t.Hs; a.mul_sl = (long)t.P[1] * t.Hs;
                 a.out = h->Y1; a.out_so = y1so; a.out_sb = t.Hs; a.out_sl = (long)t.P[1] * t.Hs;
                 a.nx = t.Hx; a.lin = t.P[2]; a.j0 = 0; a.lout = t.win[2]; a.scale = 1.f; a.tw = t.twz; a.plan = t.plz;
-                a.A2 = t.sz[0]; a.B2 = t.sz[1]; axis_opts(h, a);
+                set_split(h, a, t.sz); axis_opts(h, a);
                 Launch L(h, KID_AXIS_INV_MUL, s);
                 launch_axis_fft(1, a, t.P[1], nb, s);
             }
@@ -1217,7 +1226,7 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
             ay.in = h->Y1; ay.in_so = y1so; ay.in_sb = (long)t.P[1] * t.Hs; ay.in_sl = t.Hs;
             ay.out = h->Y2; ay.out_so = y2so; ay.out_sb = (long)t.win[1] * t.Hs; ay.out_sl = t.Hs;
             ay.nx = t.Hx; ay.lin = t.P[1]; ay.j0 = 0; ay.lout = t.win[1]; ay.scale = 1.f; ay.tw = t.twy; ay.plan = t.ply;
-            ay.A2 = t.sy[0]; ay.B2 = t.sy[1]; axis_opts(h, ay);
+            set_split(h, ay, t.sy); axis_opts(h, ay);
             IrfftArgs ax{};
             ax.in = h->Y2; ax.in_sy = t.Hs; ax.in_sz = (long)t.win[1] * t.Hs; ax.in_so = y2so;
             ax.rows_y = t.win[1]; ax.rows = t.win[1] * t.win[2]; ax.nout = t.win[0];
@@ -1227,7 +1236,7 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
             ax.flags = h->flags; ax.flag_count = fcount; ax.flag_total = h->dev_small + 4; ax.flag_cap = h->flag_cap;
             ax.status = status;
             ax.orient_base = o0; ax.M = t.M; ax.twM = t.twM; ax.twP = t.twP; ax.plan = t.plM;
-            ax.A2 = t.sM[0]; ax.B2 = t.sM[1];
+            set_split(h, ax, t.sM);
             ax.write_bits = h->run_sweep || h->keep_g;
             if (!op.separate_yx_passes && yx2_fits(ay, ax, t.Hs)) {
                 Launch L(h, KID_YX, s);
@@ -1496,11 +1505,56 @@ imf_status imf_autotune(imf_handle h, const float *rho_omega, const uint8_t *fix
         }
         if (st == IMF_OK && ms < best_ms) { best_ms = ms; best_nb = nb; }
     }
+    if (st != IMF_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return st;
+    }
+    h->opt.orient_batch = best_nb;
+    TRY(ensure_work(h));
+    // launch forms of the FFT passes and the work units of the minimum over sharp points:
+    // coordinate descent from the current options, every candidate timed like the batches above
+    // (same results whatever is chosen: each knob selects among equivalent kernels)
+    auto time_now = [&](float *ms) -> imf_status {
+        imf_status s1 = imf_compute(h, rho_omega, fixture, imf_bar, secluded, nullptr, nullptr, cuda_stream);
+        if (s1 != IMF_OK) return s1;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 2 && s1 == IMF_OK; ++r)
+            s1 = imf_compute(h, rho_omega, fixture, imf_bar, secluded, nullptr, nullptr, cuda_stream);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+            return fail(h, IMF_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+        return s1;
+    };
+    {
+        struct Knob {
+            int *field;
+            std::vector<int> values;
+        };
+        const Knob knobs[5] = {{&h->opt.fft_stages_only, {0, 1}},
+                               {&h->opt.fft_tma, {-1, 1, 0, 10}},
+                               {&h->opt.fft_wide_pencils, {-1, 0}},
+                               {&h->opt.fft_tma_x, {-1, 0}},
+                               {&h->opt.erode_groups, {0, 2, 4, 8, 16}}};
+        float cur = 1e30f;
+        st = time_now(&cur);
+        for (int k = 0; k < 5 && st == IMF_OK; ++k) {
+            const int keep = *knobs[k].field;
+            int best_v = keep;
+            for (int v : knobs[k].values) {
+                if (v == keep) continue;
+                *knobs[k].field = v;
+                float ms = 1e30f;
+                st = time_now(&ms);
+                if (st != IMF_OK) break;
+                if (ms < 0.97f * cur) { cur = ms; best_v = v; }
+            }
+            *knobs[k].field = best_v;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != IMF_OK) return st;
-    h->opt.orient_batch = best_nb;
-    TRY(ensure_work(h));
     // collision path: time the direct tensor-core path against the FFT path where both exist
     for (int ti = 0; ti < h->n_tools; ++ti) {
         Tool &t = h->tools[ti];
@@ -1655,6 +1709,13 @@ imf_status imf_get_last_bits(imf_handle h, int slot, uint32_t *bits_out, long ca
     if (cap < n) return fail(h, IMF_ERR_INVALID_ARG, "capacity %ld < %ld", cap, n);
     if (h->used_stream) CU(cudaStreamSynchronize(h->last_stream));
     CU(cudaMemcpy(bits_out, h->bits + (size_t)slot * h->bits_n, n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    return IMF_OK;
+}
+
+imf_status imf_get_options(imf_handle h, imf_options *out)
+{
+    if (!h || !out) return IMF_ERR_INVALID_ARG;
+    *out = h->opt;
     return IMF_OK;
 }
 

@@ -56,6 +56,9 @@ def _check_vs_oracle(d, fbar, sec, lam=0.01):
 
 
 def test_batch_runner_graphs_and_autotune_match_plain_compute():
+    """The batched form (autotuned orientation batch, FFT form, pass launch forms and erosion
+    work units; CUDA graphs; a stream pool) gives results bit-identical to a plain compute with
+    default options, and meets the contract against the oracle."""
     _need_gpu()
     from paper_2002_07627_gb300.batch import BatchRunner
     ds = _designs()
@@ -63,6 +66,8 @@ def test_batch_runner_graphs_and_autotune_match_plain_compute():
     br = BatchRunner(ds, n_streams=3, autotune=True, graphs=True)
     for e in br.entries:
         assert e.batch in (4, 8, 16, 32, 64)
+        assert e.tuned["fft_stages_only"] in (0, 1) and e.tuned["fft_tma"] in (-1, 0, 1, 10)
+        assert e.tuned["fft_wide_pencils"] in (-1, 0) and e.tuned["erode_groups"] in (0, 2, 4, 8, 16)
     for _ in range(2):
         br.run()
     br.check()
