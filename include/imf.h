@@ -278,7 +278,16 @@ imf_status imf_sync_status(imf_handle h);
 /* Last error message of the handle (static storage owned by the handle; never NULL). */
 const char *imf_last_error(imf_handle h);
 
-/* Free every library-owned device buffer and the handle. NULL is a no-op. */
+/* A second handle for the same grid and tools, for concurrent computes of one design (the
+ * served form runs several requests of a design at once): it shares the tool spectra and tables
+ * (read-only) and owns its own work buffers, allocated at its first imf_compute. The shared
+ * tools are freed with the last handle that holds them, whichever is destroyed last; imf_set_tool
+ * is refused on a handle whose tools are shared. Computes on the handles may overlap on the GPU.
+ * Synchronous. Errors: IMF_ERR_INVALID_ARG, IMF_ERR_NOT_READY (no tool), IMF_ERR_OOM. */
+imf_status imf_clone(imf_handle h, imf_handle *out);
+
+/* Free every library-owned device buffer and the handle (tools shared with a clone stay until
+ * the last handle holding them is destroyed). NULL is a no-op. */
 void imf_destroy(imf_handle h);
 
 /* ---------------------------------------------------------------------------------------

@@ -26,7 +26,7 @@ EXPORTS = ["imf_default_options", "imf_create", "imf_set_tool", "imf_compute", "
            "imf_set_profiling", "imf_get_kernel_time", "imf_reset_kernel_times",
            "imf_penalize_sensitivity_noalloc", "imf_capture_graph", "imf_launch_graph", "imf_autotune",
            "imf_set_path", "imf_selftest_mma", "imf_get_last_bits", "imf_footprint",
-           "imf_compute_accessible_sets", "imf_process_plan", "imf_get_options"]
+           "imf_compute_accessible_sets", "imf_process_plan", "imf_get_options", "imf_clone"]
 # every symbol include/imf_to.h declares
 EXPORTS_TO = ["imf_to2d_default_options", "imf_to2d_create", "imf_to2d_destroy", "imf_to2d_last_error",
               "imf_to2d_project", "imf_to2d_analyze", "imf_to2d_sensitivity", "imf_to2d_update", "imf_to2d_result"]
@@ -103,6 +103,7 @@ def load(path: str | None = None):
     L.imf_footprint.argtypes = [H, I, ctypes.POINTER(ImfFootprint)]
     L.imf_compute_accessible_sets.argtypes = [H, P, P, P, P, P, P]
     L.imf_get_options.argtypes = [H, ctypes.POINTER(ImfOptions)]
+    L.imf_clone.argtypes = [H, ctypes.POINTER(H)]
     LL = ctypes.c_longlong
     L.imf_process_plan.argtypes = [H, P, I, P, P, I, P, P, ctypes.POINTER(I), ctypes.POINTER(LL),
                                    ctypes.POINTER(LL), P]
@@ -351,6 +352,15 @@ class Imf:
         o = ImfOptions()
         self._check(self.lib.imf_get_options(self.h, ctypes.byref(o)))
         return {name: getattr(o, name) for name, _ in ImfOptions._fields_}
+
+    def clone(self) -> "Imf":
+        """A second handle sharing this one's tools, with its own work buffers (imf_clone)."""
+        h = ctypes.c_void_p()
+        self._check(self.lib.imf_clone(self.h, ctypes.byref(h)))
+        c = Imf.__new__(Imf)
+        c.lib, c.opt, c.shape, c.h = self.lib, self.opt, self.shape, h
+        c.n_tools = getattr(self, "n_tools", 1)
+        return c
 
     def set_path(self, tool_id, path):
         self._check(self.lib.imf_set_path(self.h, tool_id, path))

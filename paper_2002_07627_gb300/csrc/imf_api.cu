@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <map>
+#include <memory>
 #include <unordered_map>
 #include <cstdio>
 #include <cstring>
@@ -151,6 +152,8 @@ struct imf_handle_s {
     uint32_t *plan_rem = nullptr;
     unsigned long long *plan_cnt = nullptr;
     size_t plan_rem_n = 0, plan_cnt_n = 0;
+    // tools shared with clones (imf_clone): the last handle holding a reference frees them
+    std::shared_ptr<int> tool_refs;
     // debug
     bool keep_g = false;
     bool run_sweep = true;      // this compute builds A by the sweep (else A = [f <= theta])
@@ -707,11 +710,37 @@ imf_status imf_create(const imf_options *opt, imf_handle *out)
     return IMF_OK;
 }
 
+imf_status imf_clone(imf_handle h, imf_handle *out)
+{
+    if (!out) return IMF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!h) return IMF_ERR_INVALID_ARG;
+    if (h->n_tools == 0) return fail(h, IMF_ERR_NOT_READY, "imf_clone before imf_set_tool");
+    for (int i = 0; i < h->n_tools; ++i)
+        if (h->tools[i].planned_only)
+            return fail(h, IMF_ERR_INVALID_ARG, "a plan-only handle has no device tools to share");
+    if (h->used_stream) CU(cudaStreamSynchronize(h->last_stream));
+    imf_handle c = new (std::nothrow) imf_handle_s();
+    if (!c) return IMF_ERR_OOM;
+    if (!h->tool_refs) h->tool_refs = std::make_shared<int>(0);
+    c->opt = h->opt;
+    c->n_tools = h->n_tools;
+    for (int i = 0; i < h->n_tools; ++i) c->tools[i] = h->tools[i];   // device pointers shared
+    c->tool_refs = h->tool_refs;
+    c->nsm = h->nsm;
+    *out = c;
+    return IMF_OK;
+}
+
 void imf_destroy(imf_handle h)
 {
     if (!h) return;
     if (h->used_stream) cudaStreamSynchronize(h->last_stream);
-    for (auto &t : h->tools) free_tool(h, t);
+    // tools shared with a clone stay for the handles that still hold them
+    const bool last_owner = !h->tool_refs || h->tool_refs.use_count() == 1;
+    if (last_owner)
+        for (auto &t : h->tools) free_tool(h, t);
+    h->tool_refs.reset();
     dfree(h, h->rho_spec, h->rho_spec_n);
     dfree(h, h->rhohl);
     dfree(h, h->X1, h->X1_n);
@@ -772,6 +801,8 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
         const double nn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
         if (!(nn > 1e-300) || !std::isfinite(nn)) return fail(h, IMF_ERR_INVALID_ARG, "quaternion %d is zero or not finite", i);
     }
+    if (h->tool_refs && h->tool_refs.use_count() > 1)
+        return fail(h, IMF_ERR_INVALID_ARG, "the tools of this handle are shared with a clone (imf_clone)");
     if (h->used_stream) CU(cudaStreamSynchronize(h->last_stream));
     Tool &t = h->tools[tool_id];
     if (t.set) free_tool(h, t);

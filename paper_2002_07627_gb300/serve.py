@@ -6,10 +6,13 @@ design id (its tool spectra stay on the device between iterations), admits reque
 HBM footprint of the resident designs fits the budget (evicting idle designs, least recently
 used first), and runs admitted requests on a pool of CUDA streams. Continuous batching: a
 request that arrives while others are on the GPU starts as soon as a stream slot is free and
-its design is resident and idle, so work from different loops overlaps on the device.
+its design is resident and has an idle context (or room for one more), so work from different
+loops, and several requests of one design, overlap on the device.
 
 The scheduler is written against an executor interface; `GpuExecutor` drives libimf through
-its C ABI, and the tests drive the same scheduler with a fake executor on the CPU.
+its C ABI, and the tests drive the same scheduler with a fake executor on the CPU. Up to
+`max_inflight` requests of one design run at once, each on a context of its own (a clone of the
+design's handle: shared tool spectra, own work buffers), admitted against the same budget.
 """
 from __future__ import annotations
 
@@ -48,9 +51,19 @@ class _Req:
 @dataclass
 class _Resident:
     state: object
-    bytes: int
-    busy: bool = False
+    bytes: int                    # the design's footprint with its first context
+    ctx_bytes: int = 0            # each further context
+    contexts: int = 1
+    free: list = field(default_factory=lambda: [0])   # idle context indices
     last_used: float = 0.0
+
+    @property
+    def busy(self) -> bool:
+        return len(self.free) < self.contexts
+
+    @property
+    def total(self) -> int:
+        return self.bytes + (self.contexts - 1) * self.ctx_bytes
 
 
 @dataclass
@@ -63,17 +76,31 @@ class ServerStats:
     creations: int = 0
     max_resident_bytes: int = 0
     max_running: int = 0
+    max_contexts: int = 1
     units: int = 0
 
     def percentile(self, q):
         return float(np.percentile(self.latencies, q)) if self.latencies else float("nan")
 
 
+@dataclass
+class _Token:
+    inner: object
+    ctx: int
+
+
+def token_ctx(tok):
+    return tok.ctx
+
+
 class ImfServer:
-    def __init__(self, executor, hbm_budget: int, slots: int = 4, poll_s: float = 2e-4):
+    def __init__(self, executor, hbm_budget: int, slots: int = 4, poll_s: float = 2e-4, max_inflight: int = 2):
         self.ex = executor
         self.budget = int(hbm_budget)
         self.slots = max(1, int(slots))
+        # requests of one design in flight at once: each runs on a context of its own (shared
+        # tool spectra, own work buffers) where the executor can add contexts, else one
+        self.max_inflight = max(1, int(max_inflight)) if hasattr(executor, "add_context") else 1
         self.poll_s = poll_s
         self.specs = {}
         self.resident = collections.OrderedDict()   # design_id -> _Resident (LRU order)
@@ -124,7 +151,7 @@ class ImfServer:
 
     # ------------------------------------------------------------------ scheduler
     def _resident_bytes(self):
-        return sum(r.bytes for r in self.resident.values())
+        return sum(r.total for r in self.resident.values())
 
     def _make_room(self, need: int) -> bool:
         """Evict idle designs (least recently used first) until `need` more bytes fit."""
@@ -139,13 +166,33 @@ class ImfServer:
             self.stats.evictions += 1
         return True
 
+    def _grow(self, design_id, r) -> bool:
+        """One more context for a resident design, within the budget (idle designs evicted
+        first, never this one); False when it does not fit."""
+        if self._resident_bytes() + r.ctx_bytes > self.budget:
+            pinned = self.resident.pop(design_id)      # keep the growing design out of eviction
+            ok = self._make_room(r.ctx_bytes + pinned.total)
+            self.resident[design_id] = pinned
+            self.resident.move_to_end(design_id)
+            if not ok or self._resident_bytes() + r.ctx_bytes > self.budget:
+                return False
+        try:
+            self.ex.add_context(r.state)
+        except Exception:
+            return False
+        r.free.append(r.contexts)
+        r.contexts += 1
+        self.stats.max_contexts = max(self.stats.max_contexts, r.contexts)
+        self.stats.max_resident_bytes = max(self.stats.max_resident_bytes, self._resident_bytes())
+        return True
+
     def _complete(self):
         now = time.perf_counter()
         for slot, (req, token) in list(self.running.items()):
             try:
-                if not self.ex.done(token):
+                if not self.ex.done(token.inner):
                     continue
-                out = self.ex.result(token)
+                out = self.ex.result(token.inner)
                 req.future.set_result(out)
                 self.stats.completed += 1
                 self.stats.latencies.append(now - req.t_submit)
@@ -156,7 +203,7 @@ class ImfServer:
             del self.running[slot]
             r = self.resident.get(req.design_id)
             if r is not None:
-                r.busy = False
+                r.free.append(token_ctx(token))
                 r.last_used = now
 
     def _admit(self):
@@ -167,9 +214,11 @@ class ImfServer:
         while self.pending and free:
             req = self.pending.popleft()
             r = self.resident.get(req.design_id)
-            if r is not None and r.busy:
-                keep.append(req)          # one request per design at a time (its buffers)
-                continue
+            if r is not None and not r.free:
+                # every context of the design is busy: add one if allowed and it fits
+                if r.contexts >= self.max_inflight or not self._grow(req.design_id, r):
+                    keep.append(req)
+                    continue
             if r is None:
                 spec = self.specs[req.design_id]
                 need = int(self.ex.footprint(spec))
@@ -187,21 +236,25 @@ class ImfServer:
                     req.future.set_exception(exc)
                     self.stats.failed += 1
                     continue
-                r = _Resident(state, need)
+                ctx_need = int(self.ex.context_footprint(spec)) if self.max_inflight > 1 else 0
+                r = _Resident(state, need, ctx_need)
                 self.resident[req.design_id] = r
                 self.stats.creations += 1
                 self.stats.max_resident_bytes = max(self.stats.max_resident_bytes, self._resident_bytes())
             slot = free.pop(0)
             self.resident.move_to_end(req.design_id)
+            ctx = r.free.pop(0)
             try:
                 req.t_start = time.perf_counter()
-                token = self.ex.launch(r.state, req.rho, slot)
+                token = self.ex.launch(r.state, req.rho, slot) if self.max_inflight == 1 else \
+                    self.ex.launch(r.state, req.rho, slot, ctx)
             except Exception as exc:
                 req.future.set_exception(exc)
                 self.stats.failed += 1
                 free.insert(0, slot)
+                r.free.insert(0, ctx)
                 continue
-            r.busy = True
+            token = _Token(token, ctx)
             self.stats.queue_waits.append(req.t_start - req.t_submit)
             self.running[slot] = (req, token)
             self.stats.max_running = max(self.stats.max_running, len(self.running))
@@ -252,6 +305,25 @@ class GpuExecutor:
         return int(planned_footprint(Design(np.zeros(spec.shape, np.float32), spec.fixture, spec.tools),
                                      orient_batch=self.orient_batch).total)
 
+    def context_footprint(self, spec: DesignSpec) -> int:
+        """Device bytes of one more concurrent context of a resident design: the work buffers
+        of `orient_batch` slots (the tool spectra are shared) and the request buffers."""
+        from .batch import planned_footprint
+        from .synth import Design
+        fp = planned_footprint(Design(np.zeros(spec.shape, np.float32), spec.fixture, spec.tools),
+                               orient_batch=self.orient_batch)
+        return int(fp.work) + int(np.prod(spec.shape)) * (4 + 4 + 1)
+
+    def _buffers(self, spec: DesignSpec, imf):
+        torch = self.torch
+        return {"imf": imf,
+                "rho": torch.empty(spec.shape, dtype=torch.float32, device=self.dev),
+                "fbar": torch.empty(spec.shape, dtype=torch.float32, device=self.dev),
+                "sec": torch.empty(spec.shape, dtype=torch.uint8, device=self.dev),
+                "h_rho": torch.empty(spec.shape, dtype=torch.float32).pin_memory(),
+                "h_fbar": torch.empty(spec.shape, dtype=torch.float32).pin_memory(),
+                "h_sec": torch.empty(spec.shape, dtype=torch.uint8).pin_memory()}
+
     def create(self, design_id, spec: DesignSpec):
         from . import binding
         torch = self.torch
@@ -260,37 +332,38 @@ class GpuExecutor:
         imf = binding.Imf(spec.shape, lam=spec.lam, tau=spec.tau, theta_rel=spec.theta_rel,
                           orient_batch=self.orient_batch, hbm_budget_bytes=self.library_budget(spec))
         imf.set_tools(spec.tools)
-        st = {"imf": imf,
-              "rho": torch.empty(spec.shape, dtype=torch.float32, device=self.dev),
-              "fix": None if spec.fixture is None else torch.from_numpy(np.ascontiguousarray(spec.fixture, np.uint8)).to(self.dev),
-              "fbar": torch.empty(spec.shape, dtype=torch.float32, device=self.dev),
-              "sec": torch.empty(spec.shape, dtype=torch.uint8, device=self.dev),
-              "h_rho": torch.empty(spec.shape, dtype=torch.float32).pin_memory(),
-              "h_fbar": torch.empty(spec.shape, dtype=torch.float32).pin_memory(),
-              "h_sec": torch.empty(spec.shape, dtype=torch.uint8).pin_memory()}
-        return st
+        fix = None if spec.fixture is None else torch.from_numpy(np.ascontiguousarray(spec.fixture, np.uint8)).to(self.dev)
+        return {"spec": spec, "fix": fix, "ctxs": [self._buffers(spec, imf)]}
+
+    def add_context(self, st):
+        """A further context of a resident design: a clone of its handle (shared tool spectra,
+        own work buffers) with its own request buffers."""
+        self.torch.cuda.set_device(self.dev)
+        st["ctxs"].append(self._buffers(st["spec"], st["ctxs"][0]["imf"].clone()))
 
     def destroy(self, st):
-        st["imf"].close()
+        for c in reversed(st["ctxs"]):
+            c["imf"].close()
 
-    def launch(self, st, rho: np.ndarray, slot: int):
+    def launch(self, st, rho: np.ndarray, slot: int, ctx: int = 0):
         torch = self.torch
         s = self.streams[slot]
-        st["h_rho"].numpy()[...] = rho
+        c = st["ctxs"][ctx]
+        c["h_rho"].numpy()[...] = rho
         with torch.cuda.stream(s):
-            st["rho"].copy_(st["h_rho"], non_blocking=True)
-            st["imf"].compute(st["rho"], st["fix"], st["fbar"], st["sec"], stream=s)
-            st["h_fbar"].copy_(st["fbar"], non_blocking=True)
-            st["h_sec"].copy_(st["sec"], non_blocking=True)
+            c["rho"].copy_(c["h_rho"], non_blocking=True)
+            c["imf"].compute(c["rho"], st["fix"], c["fbar"], c["sec"], stream=s)
+            c["h_fbar"].copy_(c["fbar"], non_blocking=True)
+            c["h_sec"].copy_(c["sec"], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
-        return (ev, st)
+        return (ev, c)
 
     def done(self, token) -> bool:
         return token[0].query()
 
     def result(self, token):
-        ev, st = token
+        ev, c = token
         ev.synchronize()
-        st["imf"].sync()
-        return st["h_fbar"].numpy().copy(), st["h_sec"].numpy().copy()
+        c["imf"].sync()
+        return c["h_fbar"].numpy().copy(), c["h_sec"].numpy().copy()

@@ -161,3 +161,52 @@ def test_planned_footprint_equals_what_the_handle_allocates():
         assert imf.stats().owned_bytes == fp.resident + fp.work
         assert fp.total >= fp.resident + fp.work
         imf.close()
+
+
+def test_concurrent_requests_of_one_design_on_clones_match_plain():
+    """Several requests of one design in flight at once run on clones of its handle (shared tool
+    spectra, own work buffers, imf_clone): every result equals a plain compute of the same
+    density, and the server did run more than one context of the design."""
+    _need_gpu()
+    from paper_2002_07627_gb300 import binding
+    from paper_2002_07627_gb300.serve import DesignSpec, GpuExecutor, ImfServer
+    d = _designs()[0]
+    spec = DesignSpec(d.rho.shape, d.tools, d.fixture)
+    srv = ImfServer(GpuExecutor(4), hbm_budget=8 << 30, slots=4, max_inflight=3)
+    srv.register(0, spec)
+    rhos = [np.clip(d.rho + 0.02 * k, 0, 1).astype(np.float32) for k in range(9)]
+    futs = [srv.submit(0, r) for r in rhos]
+    outs = [f.result(timeout=120) for f in futs]
+    assert srv.stats.max_contexts >= 2
+    srv.close()
+    imf = binding.Imf(d.rho.shape, orient_batch=16)
+    imf.set_tools(d.tools)
+    fix = torch.from_numpy(d.fixture).cuda()
+    for r, (fb, sec) in zip(rhos, outs):
+        a, b = imf.compute(torch.from_numpy(r).cuda(), fix)
+        imf.sync()
+        assert np.array_equal(fb, a.cpu().numpy()) and np.array_equal(sec, b.cpu().numpy())
+    imf.close()
+
+
+def test_clone_shares_tools_and_outlives_its_parent():
+    """A clone computes the same result as its parent; destroying the parent first leaves the
+    clone's shared tools intact; set_tool on a handle whose tools are shared is refused."""
+    _need_gpu()
+    from paper_2002_07627_gb300 import binding
+    d = _designs()[1]
+    imf = binding.Imf(d.rho.shape)
+    imf.set_tools(d.tools)
+    c = imf.clone()
+    with pytest.raises(binding.ImfError):
+        imf.set_tools(d.tools)
+    rho = torch.from_numpy(d.rho).cuda()
+    fix = torch.from_numpy(d.fixture).cuda()
+    a, b = imf.compute(rho, fix)
+    imf.sync()
+    ref = a.cpu().numpy(), b.cpu().numpy()
+    imf.close()
+    x, y = c.compute(rho, fix)
+    c.sync()
+    assert np.array_equal(x.cpu().numpy(), ref[0]) and np.array_equal(y.cpu().numpy(), ref[1])
+    c.close()

@@ -138,3 +138,75 @@ def test_requests_of_one_design_run_in_order():
     srv.close()
     assert done == [16 * k for k in range(20)]
     assert ex.max_running == 1
+
+
+class FakeCtxExecutor(FakeExecutor):
+    """A fake executor that can add contexts to a resident design (each a further concurrent
+    request of that design), costing `ctx_size` bytes each."""
+
+    def __init__(self, sizes, ctx_size, duration=0.003):
+        super().__init__(sizes, duration)
+        self.ctx_size = ctx_size
+        self.ctxs = {}
+        self.max_ctx_running = 0
+
+    def context_footprint(self, spec):
+        return self.ctx_size
+
+    def create(self, design_id, spec):
+        st = super().create(design_id, spec)
+        self.ctxs[design_id] = 1
+        return st
+
+    def add_context(self, st):
+        with self.lock:
+            self.ctxs[st["id"]] += 1
+            self.resident[st["id"]] += self.ctx_size
+            self.max_bytes = max(self.max_bytes, sum(self.resident.values()))
+
+    def destroy(self, st):
+        super().destroy(st)
+        self.ctxs.pop(st["id"], None)
+
+    def launch(self, st, rho, slot, ctx=0):
+        with self.lock:
+            self.calls += 1
+            key = (st["id"], ctx)
+            assert key not in {(r[0], r[2]) for r in self.running}, "one context runs one request"
+            assert ctx < self.ctxs[st["id"]]
+            self.running.add((st["id"], slot, ctx))
+            self.max_running = max(self.max_running, len(self.running))
+            per = sum(1 for r in self.running if r[0] == st["id"])
+            self.max_ctx_running = max(self.max_ctx_running, per)
+        return (st["id"], slot, time.perf_counter() + self.duration, rho, ctx)
+
+    def result(self, tok):
+        with self.lock:
+            self.running.discard((tok[0], tok[1], tok[4]))
+        return tok[0], float(tok[3].sum())
+
+
+def test_several_requests_of_one_design_run_on_their_own_contexts():
+    """With an executor that can add contexts, up to max_inflight requests of one design run at
+    once (each on its own context), the budget counts every context, every result is right, and
+    a context that does not fit the budget is not added (the request waits instead)."""
+    ex = FakeCtxExecutor({0: 30, 1: 30}, ctx_size=10)
+    srv = ImfServer(ex, hbm_budget=100, slots=4, max_inflight=3)
+    srv.register(0, _spec(0))
+    srv.register(1, _spec(1))
+    futs = [(k, srv.submit(k % 2, np.full((1, 4, 4), k, np.float32))) for k in range(40)]
+    for k, f in futs:
+        did, s = f.result(timeout=30)
+        assert did == k % 2 and s == 16 * k
+    srv.close()
+    assert ex.max_ctx_running >= 2 and ex.max_ctx_running <= 3
+    assert ex.max_bytes <= 100
+    assert srv.stats.max_contexts <= 3
+    # a budget with no room for a second context keeps one request per design in flight
+    ex = FakeCtxExecutor({0: 95}, ctx_size=10)
+    srv = ImfServer(ex, hbm_budget=100, slots=4, max_inflight=3)
+    srv.register(0, _spec(0))
+    futs = [srv.submit(0, np.full((1, 4, 4), k, np.float32)) for k in range(8)]
+    assert [f.result(timeout=30)[1] for f in futs] == [16 * k for k in range(8)]
+    srv.close()
+    assert ex.max_ctx_running == 1 and ex.max_bytes <= 100
