@@ -487,7 +487,7 @@ class Workload:
         imf = binding.Imf(self.shape, orient_batch=a.orient_batch, precision=self.prec, erode_groups=a.erode_groups,
                           fft_stages_only=a.fft_stages_only, accessible_by_sweep=by_sweep,
                           fft_wide_pencils=a.fft_wide_pencils, erode_levels=a.erode_levels, fft_tma=a.fft_tma,
-                          fft_tma_x=a.fft_tma_x, sweep_loop=a.sweep_loop)
+                          fft_tma_x=a.fft_tma_x, sweep_loop=a.sweep_loop, erode_xt=a.erode_xt)
         imf.set_tools(self.d.tools)
         return imf
 
@@ -856,6 +856,8 @@ def main():
                     help="inverse x pass fed by tensor copies (imf_options.fft_tma_x; -1 default)")
     ap.add_argument("--sweep-loop", action="store_true",
                     help="sweep with each thread walking the batch's orientations (early exit per word)")
+    ap.add_argument("--erode-xt", type=int, default=0,
+                    help="x outputs per thread of the minimum over sharp points (imf_options.erode_xt: 8, 16; 0 default)")
     ap.add_argument("--erode-levels", action="store_true",
                     help="minimum over sharp points with dyadic min levels instead of pairwise minima per run")
     ap.add_argument("--fft-stages-only", action="store_true",

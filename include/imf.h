@@ -129,6 +129,10 @@ typedef struct {
                                 word and orientation of the batch; 1 = each thread walks the
                                 batch's orientations for its word and stops once the word is
                                 fully accessible (same results; slower where measured)         */
+    int erode_xt;            /* minimum over sharp points, pairwise form: consecutive x outputs
+                                per thread, 8 (1024 threads per block) or 16 (512 threads, fewer
+                                shared loads per output and run, half the resident warps; slower
+                                where measured); same results; 0 = library default (8)         */
 } imf_options;
 
 /* Fill *opt with the defaults above (grid 0x0x0, which imf_create rejects). */

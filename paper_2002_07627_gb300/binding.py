@@ -42,7 +42,8 @@ class ImfOptions(ctypes.Structure):
                 ("separate_yx_passes", ctypes.c_int), ("plan_only", ctypes.c_int),
                 ("sharp_sampling", ctypes.c_int), ("sharp_k", ctypes.c_int), ("fft_wide_pencils", ctypes.c_int),
                 ("fft_tma", ctypes.c_int), ("erode_levels", ctypes.c_int),
-                ("fft_tma_x", ctypes.c_int), ("sweep_loop", ctypes.c_int)]
+                ("fft_tma_x", ctypes.c_int), ("sweep_loop", ctypes.c_int),
+                ("erode_xt", ctypes.c_int)]
 
 
 class ImfToolInfo(ctypes.Structure):
@@ -197,7 +198,7 @@ class Imf:
                  recheck_band=0.0, orient_batch=0, hbm_budget_bytes=0, voxel=1.0, erode_groups=0, fft_stages_only=False,
                  accessible_by_sweep=False, separate_yx_passes=False, plan_only=False, sharp_sampling=IMF_SHARP_ALL,
                  sharp_k=1, fft_wide_pencils=-1, fft_tma=-1, erode_levels=False, fft_tma_x=-1,
-                 sweep_loop=False):
+                 sweep_loop=False, erode_xt=0):
         self.lib = load()
         opt = ImfOptions()
         self.lib.imf_default_options(ctypes.byref(opt))
@@ -217,6 +218,7 @@ class Imf:
         opt.erode_levels = int(erode_levels)
         opt.fft_tma_x = int(fft_tma_x)
         opt.sweep_loop = int(sweep_loop)
+        opt.erode_xt = int(erode_xt)
         self.shape = (nz, ny, nx)
         self.opt = opt
         h = ctypes.c_void_p()

@@ -31,53 +31,90 @@ __device__ __forceinline__ float fmin3(float a, float b, float c)
     return r;
 }
 
-// One run of length L for the thread's kErXT consecutive outputs: acc[j] = min(acc[j],
-// s[j], ..., s[j + L - 1]). For L >= 4 the minima of neighbouring pairs, p[i] = min(s[i], s[i+1]),
-// are formed once and shared by the overlapping windows (L + 6 + 8 ceil(L/2) comparisons for the
-// 8 outputs instead of 8 L); min is exact, so the grouping does not change the result.
-template <int L> __device__ __forceinline__ void run_min(const float *__restrict__ s, float *acc)
+// Window values of a run of length L that one output combines: the L loaded values themselves
+// for L <= 3, else ceil(L / 3) minima of three neighbours T[i] = min(s[i], s[i+1], s[i+2]) (the
+// last block starts at L - 3 and may overlap its neighbour; min is exact and idempotent, so the
+// cover does not change the result).
+template <int L> __host__ __device__ constexpr int nblk() { return L <= 3 ? L : (L + 2) / 3; }
+template <int L> __host__ __device__ constexpr int blk(int m) { return L <= 3 ? m : (m + 1 < nblk<L>() ? 3 * m : L - 3); }
+
+// loads the window of one run for XT consecutive outputs and forms its block values V
+template <int XT, int L> __device__ __forceinline__ void run_blocks(const float *__restrict__ s, float *V)
 {
-    float w[kErXT + L - 1];
+    float w[XT + L - 1];
 #pragma unroll
-    for (int i = 0; i < kErXT + L - 1; ++i) w[i] = s[i];
-    if constexpr (L >= 4) {
-        float p[kErXT + L - 2];
+    for (int i = 0; i < XT + L - 1; ++i) w[i] = s[i];
+    if constexpr (L <= 3) {
 #pragma unroll
-        for (int i = 0; i < kErXT + L - 2; ++i) p[i] = fminf(w[i], w[i + 1]);
-#pragma unroll
-        for (int j = 0; j < kErXT; ++j) {
-            float m = acc[j];
-#pragma unroll
-            for (int t = 0; t + 1 < L; t += 4) {
-                if (t + 3 < L) m = fmin3(m, p[j + t], p[j + t + 2]);
-                else m = fminf(m, p[j + t]);
-            }
-            if (L & 1) m = fminf(m, w[j + L - 1]);
-            acc[j] = m;
-        }
+        for (int i = 0; i < XT + L - 1; ++i) V[i] = w[i];
     } else {
 #pragma unroll
-        for (int j = 0; j < kErXT; ++j) {
-            float m = acc[j];
+        for (int i = 0; i < XT + L - 3; ++i) V[i] = fmin3(w[i], w[i + 1], w[i + 2]);
+    }
+}
+template <int XT, int L> __host__ __device__ constexpr int nv() { return L <= 3 ? XT + L - 1 : XT + L - 3; }
+
+// One run of length L for the thread's XT consecutive outputs: acc[j] = min(acc[j], s[j], ...,
+// s[j + L - 1]), as three-input minima over the run's block values (XT + L - 1 shared loads,
+// nv three-input minima to form the blocks, ceil(nblk / 2) per output).
+template <int XT, int L> __device__ __forceinline__ void run_min(const float *__restrict__ s, float *acc)
+{
+    float V[nv<XT, L>()];
+    run_blocks<XT, L>(s, V);
+    constexpr int K = nblk<L>();
 #pragma unroll
-            for (int t = 0; t < L; t += 2) {
-                if (t + 1 < L) m = fmin3(m, w[j + t], w[j + t + 1]);
-                else m = fminf(m, w[j + t]);
-            }
-            acc[j] = m;
+    for (int j = 0; j < XT; ++j) {
+        float m = acc[j];
+#pragma unroll
+        for (int b = 0; b < K; b += 2) {
+            if (b + 1 < K) m = fmin3(m, V[j + blk<L>(b)], V[j + blk<L>(b + 1)]);
+            else m = fminf(m, V[j + blk<L>(b)]);
         }
+        acc[j] = m;
     }
 }
 
-template <int L> __device__ __forceinline__ void run_group(const int2 *sruns, int q0, int q1, const float *tb, float *acc)
+// Two runs of the same length with an odd block count, merged so that no output spends a
+// two-input minimum on a lone block: K three-input minima per output instead of K + 1.
+template <int XT, int L> __device__ __forceinline__ void run_pair(const float *__restrict__ s0, const float *__restrict__ s1,
+                                                                float *acc)
 {
-    for (int q = q0; q < q1; ++q) run_min<L>(tb + sruns[q].x, acc);
+    float V0[nv<XT, L>()], V1[nv<XT, L>()];
+    run_blocks<XT, L>(s0, V0);
+    run_blocks<XT, L>(s1, V1);
+    constexpr int K = nblk<L>();
+#pragma unroll
+    for (int j = 0; j < XT; ++j) {
+        float m = acc[j];
+#pragma unroll
+        for (int b = 0; b < 2 * K; b += 2) {
+            const float u = b < K ? V0[j + blk<L>(b)] : V1[j + blk<L>(b - K)];
+            const float v = b + 1 < K ? V0[j + blk<L>(b + 1)] : V1[j + blk<L>(b + 1 - K)];
+            m = fmin3(m, u, v);
+        }
+        acc[j] = m;
+    }
+}
+
+// pairing pays where the block count is odd and both windows stay in registers
+template <int XT, int L> __host__ __device__ constexpr bool pair_ok()
+{
+    return (nblk<L>() & 1) && 2 * (XT + L - 1) + XT <= (XT <= 8 ? 48 : 100);
+}
+
+template <int XT, int L> __device__ __forceinline__ void run_group(const int2 *sruns, int q0, int q1, const float *tb, float *acc)
+{
+    int q = q0;
+    if constexpr (pair_ok<XT, L>())
+        for (; q + 1 < q1; q += 2) run_pair<XT, L>(tb + sruns[q].x, tb + sruns[q + 1].x, acc);
+    for (; q < q1; ++q) run_min<XT, L>(tb + sruns[q].x, acc);
 }
 
 // Asynchronous fill of a chunk's g tile, one warp per tile row; cells outside the window (read
 // only by outputs beyond the grid, which are masked) are zero-filled. Rows are short (a few
 // copies per lane), so the row position advances without division and each lane's copies of a
 // row are unrolled four at a time. The caller commits and waits.
+template <int NT>
 __device__ __forceinline__ void fill_tile(const Erode2Args &a, const float *g, const ErodeChunk &ch, int X0, int Y0,
                                           int Z0, uint32_t sbase, int warp, int lane)
 {
@@ -85,7 +122,7 @@ __device__ __forceinline__ void fill_tile(const Erode2Args &a, const float *g, c
     const int txh = ch.txh, tyh = ch.tyh, nrow = tyh * ch.tzh;
     const int pz = ch.pitch_z, py = ch.pitch_y;
     const bool xin = gx0 + txh <= a.wx;
-    constexpr int NW = kErThreads / 32;
+    constexpr int NW = NT / 32;
     int iy = warp % tyh, iz = warp / tyh;
     // row pointers advance by NW rows per step (and by one plane minus tyh rows per wrap)
     const long gstep = (long)NW * a.gpx, gwrap = (long)a.gpy * a.gpx - (long)tyh * a.gpx;
@@ -123,14 +160,14 @@ __device__ __forceinline__ void fill_tile(const Erode2Args &a, const float *g, c
     }
 }
 
-__global__ void __launch_bounds__(kErThreads, kErBlocksPerSM) erode2_kernel(Erode2Args a)
+template <int XT> __global__ void __launch_bounds__(er_threads(XT), 1) erode2_kernel(Erode2Args a)
 {
     extern __shared__ float tile[];
     __shared__ int2 sruns[kErMaxRunsPerChunk];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // lane = ty_lo (8) x tz_lo (4); warp = tx (kErTX / kErXT) x ty_hi (kErTY / 8) x tz_hi
-    constexpr int NXT = kErTX / kErXT, NYH = kErTY / 8;
-    static_assert(NXT * NYH * (kErTZ / 4) * 32 == kErThreads, "erosion block shape");
+    // lane = ty_lo (8) x tz_lo (4); warp = tx (kErTX / XT) x ty_hi (kErTY / 8) x tz_hi
+    constexpr int NT = er_threads(XT), NXT = kErTX / XT, NYH = kErTY / 8;
+    static_assert(NXT * NYH * (kErTZ / 4) * 32 == NT, "erosion block shape");
     const int tx = warp % NXT, ty = ((warp / NXT) % NYH) * 8 + (lane & 7), tz = (warp / (NXT * NYH)) * 4 + (lane >> 3);
     const int tiles_z = (a.nz + kErTZ - 1) / kErTZ;
     const int grp = blockIdx.z / tiles_z;
@@ -140,10 +177,10 @@ __global__ void __launch_bounds__(kErThreads, kErBlocksPerSM) erode2_kernel(Erod
     float *frow = a.f + ((long)z * a.ny + y) * a.nx;
     // the running minimum starts from f; outputs outside the grid start at 0 so that they
     // never keep a warp busy
-    float acc[kErXT];
+    float acc[XT];
 #pragma unroll
-    for (int j = 0; j < kErXT; ++j) {
-        const int x = X0 + tx * kErXT + j;
+    for (int j = 0; j < XT; ++j) {
+        const int x = X0 + tx * XT + j;
         acc[j] = (y < a.ny && z < a.nz && x < a.nx) ? frow[x] : 0.f;
     }
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tile);
@@ -154,7 +191,7 @@ __global__ void __launch_bounds__(kErThreads, kErBlocksPerSM) erode2_kernel(Erod
         // warp (or the whole block) is done
         bool done = true;
 #pragma unroll
-        for (int j = 0; j < kErXT; ++j) done = done && acc[j] <= 0.f;
+        for (int j = 0; j < XT; ++j) done = done && acc[j] <= 0.f;
         if (__syncthreads_and(done)) continue;
         const bool warp_done = __all_sync(0xffffffffu, done);
         for (int c = a.chunk_start[og]; c < a.chunk_start[og + 1]; ++c) {
@@ -162,42 +199,42 @@ __global__ void __launch_bounds__(kErThreads, kErBlocksPerSM) erode2_kernel(Erod
             const int pz = ch.pitch_z, py = ch.pitch_y;
             const int run0 = ch.run0, nrun = ch.run1 - ch.run0;
             __syncthreads();
-            fill_tile(a, g, ch, X0, Y0, Z0, sbase, warp, lane);
-            for (int q = threadIdx.x; q < nrun; q += kErThreads) sruns[q] = a.runs[run0 + q];
+            fill_tile<NT>(a, g, ch, X0, Y0, Z0, sbase, warp, lane);
+            for (int q = threadIdx.x; q < nrun; q += NT) sruns[q] = a.runs[run0 + q];
             asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
             __syncthreads();
             if (warp_done) continue;
-            const float *tb = tile + tz * pz + ty * py + tx * kErXT;
+            const float *tb = tile + tz * pz + ty * py + tx * XT;
             const int *le = ch.lend;
-            run_group<1>(sruns, le[0], le[1], tb, acc);
-            run_group<2>(sruns, le[1], le[2], tb, acc);
-            run_group<3>(sruns, le[2], le[3], tb, acc);
-            run_group<4>(sruns, le[3], le[4], tb, acc);
-            run_group<5>(sruns, le[4], le[5], tb, acc);
-            run_group<6>(sruns, le[5], le[6], tb, acc);
-            run_group<7>(sruns, le[6], le[7], tb, acc);
-            run_group<8>(sruns, le[7], le[8], tb, acc);
-            run_group<9>(sruns, le[8], le[9], tb, acc);
-            run_group<10>(sruns, le[9], le[10], tb, acc);
-            run_group<11>(sruns, le[10], le[11], tb, acc);
-            run_group<12>(sruns, le[11], le[12], tb, acc);
-            run_group<13>(sruns, le[12], le[13], tb, acc);
-            run_group<14>(sruns, le[13], le[14], tb, acc);
-            run_group<15>(sruns, le[14], le[15], tb, acc);
-            run_group<16>(sruns, le[15], le[16], tb, acc);
+            run_group<XT, 1>(sruns, le[0], le[1], tb, acc);
+            run_group<XT, 2>(sruns, le[1], le[2], tb, acc);
+            run_group<XT, 3>(sruns, le[2], le[3], tb, acc);
+            run_group<XT, 4>(sruns, le[3], le[4], tb, acc);
+            run_group<XT, 5>(sruns, le[4], le[5], tb, acc);
+            run_group<XT, 6>(sruns, le[5], le[6], tb, acc);
+            run_group<XT, 7>(sruns, le[6], le[7], tb, acc);
+            run_group<XT, 8>(sruns, le[7], le[8], tb, acc);
+            run_group<XT, 9>(sruns, le[8], le[9], tb, acc);
+            run_group<XT, 10>(sruns, le[9], le[10], tb, acc);
+            run_group<XT, 11>(sruns, le[10], le[11], tb, acc);
+            run_group<XT, 12>(sruns, le[11], le[12], tb, acc);
+            run_group<XT, 13>(sruns, le[12], le[13], tb, acc);
+            run_group<XT, 14>(sruns, le[13], le[14], tb, acc);
+            run_group<XT, 15>(sruns, le[14], le[15], tb, acc);
+            run_group<XT, 16>(sruns, le[15], le[16], tb, acc);
         }
     }
     if (y < a.ny && z < a.nz) {
         if (a.ngroups == 1) {
 #pragma unroll
-            for (int j = 0; j < kErXT; ++j) {
-                const int x = X0 + tx * kErXT + j;
+            for (int j = 0; j < XT; ++j) {
+                const int x = X0 + tx * XT + j;
                 if (x < a.nx) frow[x] = acc[j];
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < kErXT; ++j) {
-                const int x = X0 + tx * kErXT + j;
+            for (int j = 0; j < XT; ++j) {
+                const int x = X0 + tx * XT + j;
                 if (x < a.nx) atomicMin(reinterpret_cast<unsigned int *>(frow + x), __float_as_uint(__fadd_rn(acc[j], 0.f)));
             }
         }
@@ -295,7 +332,7 @@ __global__ void __launch_bounds__(kErThreads, kErBlocksPerSM) erode3_kernel(Erod
             const ErodeChunk &ch = a.chunks[c];
             const int run0 = ch.run0, nrun = ch.run1 - ch.run0;
             __syncthreads();
-            fill_tile(a, g, ch, X0, Y0, Z0, sbase, warp, lane);
+            fill_tile<kErThreads>(a, g, ch, X0, Y0, Z0, sbase, warp, lane);
             for (int q = threadIdx.x; q < nrun; q += kErThreads) sruns[q] = a.runs[run0 + q];
             asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
             __syncthreads();
@@ -397,20 +434,32 @@ int erode3_blocks_per_sm(size_t smem)
     return n < 1 ? 1 : n;
 }
 
-void launch_erode2(const Erode2Args &a, size_t smem, cudaStream_t s)
+template <int XT> void launch_erode2_xt(const Erode2Args &a, size_t smem, cudaStream_t s)
 {
     // the static descriptor table counts against the default 48 KB, so always raise the limit
-    cudaFuncSetAttribute(erode2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(erode2_kernel<XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((a.nx + kErTX - 1) / kErTX, (a.ny + kErTY - 1) / kErTY, ((a.nz + kErTZ - 1) / kErTZ) * a.ngroups);
-    erode2_kernel<<<grid, kErThreads, smem, s>>>(a);
+    erode2_kernel<XT><<<grid, er_threads(XT), smem, s>>>(a);
 }
 
-int erode2_blocks_per_sm(size_t smem)
+template <int XT> int erode2_bps_xt(size_t smem)
 {
-    cudaFuncSetAttribute(erode2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(erode2_kernel<XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, erode2_kernel, kErThreads, smem) != cudaSuccess) n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, erode2_kernel<XT>, er_threads(XT), smem) != cudaSuccess)
+        n = 1;
     return n < 1 ? 1 : n;
+}
+
+void launch_erode2(const Erode2Args &a, size_t smem, int xt, cudaStream_t s)
+{
+    if (xt == 8) launch_erode2_xt<8>(a, smem, s);
+    else launch_erode2_xt<16>(a, smem, s);
+}
+
+int erode2_blocks_per_sm(size_t smem, int xt)
+{
+    return xt == 8 ? erode2_bps_xt<8>(smem) : erode2_bps_xt<16>(smem);
 }
 
 } // namespace imf

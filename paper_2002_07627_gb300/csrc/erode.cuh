@@ -20,6 +20,8 @@ constexpr int kErMaxL3 = 31;
 // longest tile row the level kernel builds levels for (four cells per lane of a warp)
 constexpr int kErMaxRow3 = 128;
 constexpr int kErThreads = (kErTX / kErXT) * kErTY * kErTZ;
+// threads of a block with xt consecutive x outputs per thread
+__host__ __device__ constexpr int er_threads(int xt) { return (kErTX / xt) * kErTY * kErTZ; }
 constexpr int kErBlocksPerSM = 1024 / kErThreads;            // 64 registers per thread
 constexpr int kErMaxRunsPerChunk = 2 * kErThreads;
 // shared-memory tile budget per block: kErBlocksPerSM blocks of tile + run table fit in 228 KB
@@ -45,8 +47,10 @@ struct Erode2Args {
     int ngroups;                 // orientation groups per tile (blockIdx.z = group * tiles_z + tile z)
     float *f;
 };
-void launch_erode2(const Erode2Args &a, size_t smem, cudaStream_t s);
-int erode2_blocks_per_sm(size_t smem);
+// xt = consecutive x outputs per thread: 8 (1024 threads, 64 registers each) or 16 (512 threads,
+// 128 registers each); the plan does not depend on it
+void launch_erode2(const Erode2Args &a, size_t smem, int xt, cudaStream_t s);
+int erode2_blocks_per_sm(size_t smem, int xt);
 // The same minimum with dyadic min levels built in place in the tile (runs up to kErMaxL3, tile
 // rows up to kErMaxRow3); planned with plan_erode(..., kErMaxL3).
 void launch_erode3(const Erode2Args &a, size_t smem, cudaStream_t s);

@@ -596,6 +596,8 @@ imf_status ensure_work(imf_handle h)
 
 // Pencils per block of the big-factor axis kernel (AxisArgs::wide): the option, or the default.
 int fft_wide(imf_handle h) { return h->opt.fft_wide_pencils >= 0 ? h->opt.fft_wide_pencils : kFftWideDefault; }
+// consecutive x outputs per thread of the pairwise minimum over sharp points
+int erode_xt(const imf_options &o) { return o.erode_xt > 0 ? o.erode_xt : 8; }
 
 // the two-pass split of a pass, or none (radix stages) when the handle asks for stages only
 template <typename Args> void set_split(imf_handle h, Args &a, const int *sp)
@@ -683,6 +685,7 @@ void imf_default_options(imf_options *opt)
     opt->erode_levels = 0;
     opt->fft_tma_x = -1;
     opt->sweep_loop = 0;
+    opt->erode_xt = 0;
 }
 
 imf_status imf_create(const imf_options *opt, imf_handle *out)
@@ -700,6 +703,7 @@ imf_status imf_create(const imf_options *opt, imf_handle *out)
     if (opt->sharp_sampling < IMF_SHARP_ALL || opt->sharp_sampling > IMF_SHARP_NEAREST) return IMF_ERR_INVALID_ARG;
     if (opt->fft_wide_pencils < -1 || opt->fft_wide_pencils > 3) return IMF_ERR_INVALID_ARG;
     if (opt->fft_tma_x < -1 || opt->fft_tma_x > 1) return IMF_ERR_INVALID_ARG;
+    if (opt->erode_xt != 0 && opt->erode_xt != 8 && opt->erode_xt != 16) return IMF_ERR_INVALID_ARG;
     if (opt->fft_tma < -1 || opt->fft_tma > 15 || (opt->fft_tma >= 0 && ((opt->fft_tma & 3) == 3 || (opt->fft_tma >> 2) == 3)))
         return IMF_ERR_INVALID_ARG;
     if (opt->sharp_sampling == IMF_SHARP_NEAREST && opt->sharp_k < 1) return IMF_ERR_INVALID_ARG;
@@ -1019,7 +1023,8 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
             h->nsm = n;
-        t.erode_bps = t.erode_levels ? erode3_blocks_per_sm(t.erode_smem) : erode2_blocks_per_sm(t.erode_smem);
+        t.erode_bps = t.erode_levels ? erode3_blocks_per_sm(t.erode_smem)
+                                      : erode2_blocks_per_sm(t.erode_smem, erode_xt(h->opt));
     }
     st = IMF_OK;
     auto bail = [&](imf_status s2) { free_tool(h, t); return s2; };
@@ -1166,7 +1171,7 @@ imf_status tail_batch(imf_handle h, const Tool &t, const float *rho, const uint8
         a.ngroups = std::max(1, std::min(G, nb));
         Launch L(h, KID_ERODE, s);
         if (t.erode_levels) launch_erode3(a, t.erode_smem, s);
-        else launch_erode2(a, t.erode_smem, s);
+        else launch_erode2(a, t.erode_smem, erode_xt(h->opt), s);
     }
     h->last_batch_base = o0;
     h->last_batch_n = nb;
@@ -1562,14 +1567,15 @@ imf_status imf_autotune(imf_handle h, const float *rho_omega, const uint8_t *fix
             int *field;
             std::vector<int> values;
         };
-        const Knob knobs[5] = {{&h->opt.fft_stages_only, {0, 1}},
+        const Knob knobs[6] = {{&h->opt.fft_stages_only, {0, 1}},
                                {&h->opt.fft_tma, {-1, 1, 0, 10}},
                                {&h->opt.fft_wide_pencils, {-1, 0}},
                                {&h->opt.fft_tma_x, {-1, 0}},
-                               {&h->opt.erode_groups, {0, 2, 4, 8, 16}}};
+                               {&h->opt.erode_groups, {0, 2, 4, 8, 16}},
+                               {&h->opt.erode_xt, {0, 8}}};
         float cur = 1e30f;
         st = time_now(&cur);
-        for (int k = 0; k < 5 && st == IMF_OK; ++k) {
+        for (int k = 0; k < 6 && st == IMF_OK; ++k) {
             const int keep = *knobs[k].field;
             int best_v = keep;
             for (int v : knobs[k].values) {

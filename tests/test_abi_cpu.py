@@ -99,6 +99,10 @@ def test_default_options_and_create_checks(lib):
     opt.lambda_ = 1.5
     assert lib.imf_create(ctypes.byref(opt), ctypes.byref(h)) == 1      # lambda out of range
     opt.lambda_ = 0.01
+    assert opt.erode_xt == 0
+    opt.erode_xt = 12
+    assert lib.imf_create(ctypes.byref(opt), ctypes.byref(h)) == 1      # 8 or 16 outputs per thread only
+    opt.erode_xt = 0
     assert lib.imf_create(ctypes.byref(opt), ctypes.byref(h)) == 0
     # host-side argument errors need no GPU
     assert lib.imf_compute(h, None, None, None, None, None, None, None) == 5   # no tool yet

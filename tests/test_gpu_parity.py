@@ -693,3 +693,30 @@ def test_sweep_loop_equals_parallel_sweep():
         b = run_gpu(d, orient_batch=ob, accessible_by_sweep=True)
         assert np.array_equal(a["accessible"], b["accessible"]), ob
         check_against_oracle(d, a, ref)
+
+
+@pytest.mark.parametrize("seed,n", [(5, (37, 45, 70)), (12, (90, 30, 26))])
+def test_erosion_outputs_per_thread_forms_agree(seed, n):
+    """The pairwise minimum over sharp points with 8 and with 16 consecutive x outputs per thread
+    (option erode_xt; 8 is the default) takes the minimum of the same candidates, in three-value
+    blocks and merged run pairs whose cover only overlaps (min is exact): f, f_bar, Gamma and A
+    are bit-identical on grids whose x extent is no multiple of either, for every orientation
+    group split, and the 16-wide form meets the contract against the oracle; runs of every length
+    up to the cap (a 40-voxel cutter along x) are exercised."""
+    d = _small3d(seed=seed, n=n, n_orient=9)
+    base = run_gpu(d, orient_batch=5, erode_xt=16)
+    for g in (0, 1, 3):
+        got = run_gpu(d, orient_batch=5, erode_groups=g, erode_xt=8)
+        for k in ("f", "fbar", "secluded", "accessible"):
+            assert np.array_equal(got[k], base[k]), (g, k)
+    check_against_oracle(d, base, oracle_ref(d))
+    c, s_ = np.cos(np.pi / 4), np.sin(np.pi / 4)
+    quats = np.array([[c, 0, s_, 0], [c, 0, -s_, 0], [1, 0, 0, 0], [0.9, 0.3, 0.3, 0.1]])
+    quats = quats / np.linalg.norm(quats, axis=1, keepdims=True)
+    rho = synth.beam_density((90, 30, 26), n_beams=8, seed=seed)
+    d2 = synth.Design(rho, synth.slab_fixture(rho.shape, 2, axis="z"), [synth.cylinder_tool(2, 40, 3, 4, quats)])
+    a = run_gpu(d2, orient_batch=4, erode_xt=16)
+    b = run_gpu(d2, orient_batch=4, erode_xt=8)
+    for k in ("f", "fbar", "secluded", "accessible"):
+        assert np.array_equal(a[k], b[k]), k
+    check_against_oracle(d2, a, oracle_ref(d2))
