@@ -4,7 +4,8 @@
 //
 // A block stays resident and walks a strided list of items (group of R = 256 / A window rows,
 // orientation slot). One thread issues a tiled tensor copy of an item's R rows of half spectrum
-// (Hs complex each, contiguous rows) into a shared-memory stage; two stages alternate, so the
+// (Hs complex each, contiguous rows) into a shared-memory stage (128-byte aligned, as tensor
+// copies require); two stages alternate, so the
 // next item's rows are in flight while the current ones are transformed. Both factors of the
 // split are template arguments of the loop (only the splits the planner picks are built), and
 // every wait on a copy is bounded (IMF_ERR_TIMEOUT, own copies drained, then return).
@@ -24,6 +25,10 @@ struct XParams {
     int R, ngroups, norient;
     long items;
 };
+
+// complex elements per stage: R rows of hs, rounded up to 128 bytes so that every stage (a
+// tensor-copy destination) starts on a 128-byte boundary whatever R = 256 / A is
+__host__ __device__ inline size_t x_stage(const XParams &P) { return ((size_t)P.R * P.hs + 15) & ~(size_t)15; }
 
 __device__ __forceinline__ void x_issue(const XParams &P, const void *map, long it, float2 *dst, uint64_t *bar)
 {
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(kXT) irfft2_tma_kernel(const __grid_constant__
     const int A = a.A2, B = a.B2, M = a.M, Ap = A | 1;
     const int ld = (M > B * Ap ? M : B * Ap) + 1, fp = (2 * M + 31) & ~31;
     unsigned char *base = smraw + ((128 - (tc::smem_addr(smraw) & 127)) & 127);
-    const size_t stage = (size_t)P.R * P.hs;
+    const size_t stage = x_stage(P);
     float2 *st = reinterpret_cast<float2 *>(base);
     float2 *tile = st + kXStages * stage;
     float2 *twM = tile + (size_t)P.R * ld, *twP = twM + M;
@@ -134,7 +139,7 @@ size_t x_tma_smem(const XParams &P)
     const IrfftArgs &a = P.a;
     const int A = a.A2, B = a.B2, M = a.M, Ap = A | 1;
     const int ld = (M > B * Ap ? M : B * Ap) + 1, fp = (2 * M + 31) & ~31;
-    return 128 + (size_t)kXStages * P.R * P.hs * 8 + (size_t)P.R * ld * 8 + (size_t)(2 * M + 2) * 8 + 16 +
+    return 128 + (size_t)kXStages * x_stage(P) * 8 + (size_t)P.R * ld * 8 + (size_t)(2 * M + 2) * 8 + 16 +
            (size_t)P.R * fp + 8 * kXStages + 8;
 }
 

@@ -657,6 +657,24 @@ def test_tma_fed_axis_passes_equal_the_one_shot_kernels():
 
 
 
+@pytest.mark.parametrize("nx,split", [(120, (10, 7)), (132, (15, 5))])
+def test_copy_fed_x_pass_with_odd_rows_per_item(nx, split):
+    """The copy-fed x pass takes R = 256 / A rows per item; with A = 10 or 15 (R = 25, 17) the R
+    rows of half spectrum are no whole number of 128-byte lines, and each of the two stages must
+    still start on a 128-byte boundary (tensor copies require it). With enough items that every
+    block reuses its stages, the pass equals the one-shot x pass bit for bit and meets the
+    contract against the oracle."""
+    d = _small3d(seed=7, n=(nx, 60, 40), n_orient=8)
+    got = run_gpu(d, orient_batch=8, separate_yx_passes=True)
+    M = got["imf"].tool_info(0).P[0] // 2
+    assert M == split[0] * split[1]
+    assert "irfft_x_threshold" in _kernels_run(got["imf"], d)
+    one = run_gpu(d, orient_batch=8, separate_yx_passes=True, fft_tma_x=0)
+    for k in ("f", "fbar", "secluded", "accessible"):
+        assert np.array_equal(got[k], one[k]), k
+    check_against_oracle(d, got, oracle_ref(d))
+
+
 @pytest.mark.parametrize("seed,n", [(4, (37, 45, 70)), (9, (61, 23, 50))])
 def test_level_minimum_equals_pairwise_minimum(seed, n):
     """The minimum over sharp points with dyadic min levels built in the tile (option) and with
