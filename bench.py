@@ -183,6 +183,8 @@ def traffic_record(kernel, workload, orient_per_launch=None):
     with open(p) as fh:
         d = json.load(fh)
     rec = d.get(kernel)
+    if rec and "workload" not in rec:
+        rec = rec.get(workload)          # records keyed by workload
     if not rec or rec.get("workload") != workload:
         return None
     srcs = rec.get("sources") or [rec.get("source")]
