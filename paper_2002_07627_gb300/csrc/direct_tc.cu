@@ -4,19 +4,27 @@
 // For a group of orientations r_0 .. r_{N-1} and its union tap list v_0 .. v_{K-1} (every
 // offset that lies in at least one R_n T):
 //   g_{r_n}(t) = sum_k A[t, k] B[n, k],   A[t, k] = rho_O(t + v_k),   B[n, k] = 1_{R_n T}(v_k).
-// A block computes D = A B^T for 128 consecutive translations along x (M = 128) and all N
-// orientations of the group, accumulating in TMEM (FP32). rho_O enters as two BF16 terms
-// rho_O = hi + lo (the binary tool indicator is exact in BF16), so D = A_hi B^T + A_lo B^T and the
-// input error is below 2^-16 of rho_O. B is loaded once per block by a bulk (TMA) copy in
-// the K-major canonical layout; A is built in shared memory, chunk by chunk, by eight producer
-// warps (two threads per tile row, half a chunk each) from a padded copy of rho_O that holds
-// (hi, lo) in one 32-bit word; one thread issues the MMAs; the same eight warps read D back
-// with tcgen05.ld (warp w reads TMEM lanes 32 (w mod 4) .. + 31 and half of the columns) and
-// write g, the free bits and the near-threshold list in the layout of the FFT path. Every mbarrier wait is bounded; on a
-// timeout the block records IMF_ERR_TIMEOUT, stops, and still frees its TMEM.
+// A block walks tiles of 128 translations (32 consecutive x by 2 y by 2 z, or 32 by 4 by 1 in
+// 2D; MMA M = 128) and computes D = A B^T for all N orientations of the group, accumulating in
+// TMEM (FP32). rho_O enters as two BF16 terms rho_O = hi + lo (the binary tool indicator is exact
+// in BF16), so D = A_hi B^T + A_lo B^T and the input error is below 2^-16 of rho_O.
+//
+// Data movement: the rho_O neighbourhood a tile reads (a box of (hi, lo) words, the tile
+// dilated by the union's extent) arrives by one tiled tensor copy, issued for the next tile as
+// soon as every producer has built its last chunk of the current one, so that it lands while the
+// last MMAs and the epilogue of the current tile run; B arrives 64 taps at a time by bulk
+// copies into four slots (with the chunk's tap offsets), two chunks ahead of the A build; sixteen
+// producer warps (four threads per tile row, a quarter of a chunk each) build A in shared memory
+// from the box, in the K-major canonical layout, chunk by chunk into two stages; one thread issues
+// the MMAs; the same sixteen warps read D back with tcgen05.ld (warp w reads TMEM lanes
+// 32 (w mod 4) .. + 31 and every fourth group of 8 columns)
+// and write g, the free bits and the near-threshold list in the layout of the FFT path. Every
+// mbarrier wait is bounded; on a timeout the block records IMF_ERR_TIMEOUT, stops, waits for its
+// own copies and MMAs, and still frees its TMEM.
 #include <cfloat>
 #include <cuda_bf16.h>
 
+#include "fft_tma.cuh"
 #include "imf_internal.cuh"
 #include "tc_primitives.cuh"
 
@@ -26,9 +34,30 @@ namespace {
 
 constexpr int kDM = 128;          // translations per tile (MMA M)
 constexpr int kDKC = 64;          // taps per chunk
-constexpr int kDProd = 256;       // 8 producer / epilogue warps: two threads per tile row
+constexpr int kDProd = 512;       // 16 producer / epilogue warps: four threads per tile row
 constexpr int kDThreads = kDProd + 32;   // + 1 MMA warp
 constexpr uint32_t kStageBytes = kDM * kDKC * 2;   // one BF16 operand chunk
+constexpr int kBSlots = 4;        // B chunk slots
+constexpr int kBAhead = 2;        // B copies run this many chunks ahead of the A build (slot reuse:
+                                  // chunk gc + kBAhead takes the slot of chunk gc - 2, whose MMAs
+                                  // the build of chunk gc has seen complete; six ahead in eight
+                                  // slots measured slower: the slots crowd out larger groups)
+
+// byte offsets of the regions of the kernel's dynamic shared memory (after 1024-byte alignment)
+struct DirectLayout {
+    uint32_t bchunk, box_bytes, b_off, box_off, bar_off, total;
+};
+__host__ __device__ inline DirectLayout direct_layout(int N, long box_words)
+{
+    DirectLayout L;
+    L.bchunk = (uint32_t)N * 128 + 256;                         // N rows x 64 taps of BF16, then the 64 taps' box offsets
+    L.box_bytes = (uint32_t)((box_words * 4 + 127) / 128 * 128);
+    L.b_off = 4 * kStageBytes;                                  // A: [stage][hi, lo]
+    L.box_off = L.b_off + kBSlots * L.bchunk;
+    L.bar_off = L.box_off + L.box_bytes;
+    L.total = L.bar_off + (9 + kBSlots) * 8 + 16;
+    return L;
+}
 
 __device__ __forceinline__ uint16_t bf16_bits_rn(float x)
 {
@@ -63,67 +92,73 @@ __global__ void rho_hl_kernel(const float *rho, const uint8_t *fix, int nx, int 
 // ---------------------------------------------------------------------------------------
 // the direct kernel
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kDThreads, 2) direct_corr_kernel(DirectArgs a)
+__global__ void __launch_bounds__(kDThreads, 1) direct_corr_kernel(const __grid_constant__ CUtensorMap box_map,
+                                                                    DirectArgs a)
 {
-    extern __shared__ __align__(1024) uint8_t dsm[];
-    const uint32_t bbytes = (uint32_t)a.kpad * a.N * 2;
-    uint8_t *Bs = dsm;
-    uint8_t *Ast = dsm + ((bbytes + 1023) & ~1023u);          // [stage][hi, lo]
-    uint64_t *bars = (uint64_t *)(Ast + 4 * kStageBytes);       // full[2], empty[2], bload, dfull, dempty
-    uint64_t *full = bars, *empty = bars + 2, *bload = bars + 4, *dfull = bars + 5, *dempty = bars + 6;
-    uint32_t *tmem_slot = (uint32_t *)(bars + 8);
+    extern __shared__ uint8_t dsm_raw[];
+    uint8_t *dsm = dsm_raw + ((1024 - (tc::smem_addr(dsm_raw) & 1023)) & 1023);
+    const DirectLayout Lo = direct_layout(a.N, (long)a.BX * a.BY * a.BZ);
+    uint8_t *Ast = dsm;
+    uint8_t *Bst = dsm + Lo.b_off;
+    uint32_t *boxes = reinterpret_cast<uint32_t *>(dsm + Lo.box_off);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(dsm + Lo.bar_off);
+    // full[2] (A built), empty[2] (stage's MMAs done), bfull[4] (B copy), boxfull (box copy),
+    // boxfree (every producer done with the box), dfull, dempty, drain
+    uint64_t *full = bars, *empty = bars + 2, *bfull = bars + 4, *boxfull = bars + 4 + kBSlots;
+    uint64_t *boxfree = boxfull + 1, *dfull = boxfull + 2, *dempty = boxfull + 3, *drain = boxfull + 4;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(boxfull + 5);
     __shared__ int s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nchunk = a.kpad / kDKC;
-    const int ntiles = a.ntiles_x * a.wy * a.wz;
+    const int ntiles = a.ntx * a.nty * a.ntz;
+    const int G = gridDim.x;
+    const long mine = (int)blockIdx.x < ntiles ? (ntiles - (int)blockIdx.x + G - 1) / G : 0;
+    const long total = mine * nchunk;
+    const uint32_t box_words = (uint32_t)a.BX * a.BY * a.BZ;
     uint32_t ncols = 32;
     while (ncols < (uint32_t)a.N) ncols <<= 1;
 
     if (threadIdx.x == 0) {
         s_abort = 0;
-        tc::mbar_init(&full[0], kDProd);
-        tc::mbar_init(&full[1], kDProd);
-        tc::mbar_init(&empty[0], 1);
-        tc::mbar_init(&empty[1], 1);
-        tc::mbar_init(bload, 1);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&full[i], kDProd);
+            tc::mbar_init(&empty[i], 1);
+        }
+        tc::mbar_init(boxfull, 1);
+        tc::mbar_init(boxfree, kDProd);
+        for (int i = 0; i < kBSlots; ++i) tc::mbar_init(&bfull[i], 1);
         tc::mbar_init(dfull, 1);
         tc::mbar_init(dempty, kDProd);
-        tc::mbar_init(bars + 7, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        tc::mbar_init(drain, 1);
+        tc::fence_mbar_init();
     }
-    if (warp == 8) tc::tmem_alloc(tmem_slot, ncols);
+    if (warp == kDProd / 32) tc::tmem_alloc(tmem_slot, ncols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 8) {
+    if (warp == kDProd / 32) {
         // ------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            tc::mbar_expect_tx(bload, bbytes);
-            for (uint32_t off = 0; off < bbytes; off += 32768u) {
-                const uint32_t n = min(32768u, bbytes - off);
-                tc::bulk_g2s(Bs + off, (const uint8_t *)a.bmat + off, n, bload);
-            }
-            bool ok = tc::mbar_wait(bload, 0);
             const uint32_t idesc = tc::make_idesc_bf16(kDM, a.N);
-            const uint32_t bsa = tc::smem_addr(Bs), asa = tc::smem_addr(Ast);
+            const uint32_t asa = tc::smem_addr(Ast), bsa = tc::smem_addr(Bst);
+            bool ok = true;
             long gc = 0;
-            int tcount = 0;
-            for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++tcount) {
-                if (tcount > 0) ok = tc::mbar_wait(dempty, (tcount - 1) & 1);
+            for (long k = 0; ok && k < mine; ++k) {
+                if (k > 0) ok = tc::mbar_wait(dempty, (uint32_t)((k - 1) & 1));
                 tc::fence_after();
                 for (int c = 0; ok && c < nchunk; ++c, ++gc) {
-                    const int s = (int)(gc & 1);
-                    const uint32_t u = (uint32_t)(gc >> 1);
-                    if (!(ok = tc::mbar_wait(&full[s], u & 1))) break;
+                    const int s = (int)(gc & 1), bs = (int)(gc % kBSlots);
+                    if (!(ok = tc::mbar_wait(&full[s], (uint32_t)((gc >> 1) & 1)))) break;
+                    if (!(ok = tc::mbar_wait(&bfull[bs], (uint32_t)((gc / kBSlots) & 1)))) break;
                     tc::fence_after();
 #pragma unroll
                     for (int ks = 0; ks < kDKC / 16; ++ks) {
                         const uint32_t ahi = asa + (2 * s) * kStageBytes + ks * 2 * (kDM * 16);
                         const uint32_t alo = ahi + kStageBytes;
-                        const uint32_t bk = bsa + (uint32_t)((c * kDKC + ks * 16) / 8) * (a.N * 16);
+                        const uint32_t bk = bsa + bs * Lo.bchunk + (uint32_t)ks * 2 * (a.N * 16);   // 16-byte aligned
                         const uint64_t bd = tc::make_desc(bk, a.N * 16, 128);
                         tc::mma_bf16(tmem, tc::make_desc(ahi, kDM * 16, 128), bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
                         tc::mma_bf16(tmem, tc::make_desc(alo, kDM * 16, 128), bd, idesc, 1u);
@@ -137,57 +172,104 @@ __global__ void __launch_bounds__(kDThreads, 2) direct_corr_kernel(DirectArgs a)
                 atomicExch(&s_abort, 1);
             }
             // drain: every MMA this thread issued has completed before TMEM is freed
-            tc::mma_commit(bars + 7);
-            if (!tc::mbar_wait(bars + 7, 0)) atomicExch(a.status, kDevTimeout);
+            tc::mma_commit(drain);
+            if (!tc::mbar_wait(drain, 0)) atomicExch(a.status, kDevTimeout);
         }
         __syncwarp();
     } else {
         // ------------------------------------------------------- producers / epilogue
         const int m = threadIdx.x & (kDM - 1);      // row of the tile = TMEM lane
-        const int half = threadIdx.x >> 7;          // which half of each chunk / of the columns
+        const int quarter = threadIdx.x >> 7;       // which quarter of each chunk / of the column groups
+        const int xl = m & 31, yl = (m >> 5) % a.TY, zl = (m >> 5) / a.TY;
+        const int base_m = a.sx + xl + a.BX * (yl + a.BY * zl);
+        // copies issued by thread 0: the last box use and B use per slot (-1: none)
+        long last_box = -1, last_b[kBSlots];
+        for (int i = 0; i < kBSlots; ++i) last_b[i] = -1;
+        auto issue_box = [&](long k) {
+            const int t = (int)blockIdx.x + (int)k * G;
+            const int tx = t % a.ntx, r = t / a.ntx, ty = r % a.nty, tz = r / a.nty;
+            const int cx = 32 * tx - a.kx + a.vlo[0] + a.lox - a.sx;     // a multiple of 4
+            const int cy = a.TY * ty - a.ky + a.vlo[1] + a.loy;
+            const int cz = a.TZ * tz - a.kz + a.vlo[2] + a.loz;
+            tc::mbar_expect_tx(boxfull, box_words * 4);
+            tc::tma_load_3d(boxes, &box_map, cx, cy, cz, boxfull);
+            last_box = k;
+        };
+        auto issue_b = [&](long g2) {
+            const int slot = (int)(g2 % kBSlots);
+            const int c = (int)(g2 % nchunk);
+            const uint32_t bbytes = Lo.bchunk - 256;
+            tc::mbar_expect_tx(&bfull[slot], Lo.bchunk);
+            tc::bulk_g2s(Bst + slot * Lo.bchunk, reinterpret_cast<const uint8_t *>(a.bmat) + (size_t)c * bbytes, bbytes,
+                         &bfull[slot]);
+            tc::bulk_g2s(Bst + slot * Lo.bchunk + bbytes, a.tapoff + c * kDKC, 256, &bfull[slot]);
+            last_b[slot] = g2;
+        };
+        if (threadIdx.x == 0) {
+            if (mine > 0) issue_box(0);
+            for (long g2 = 0; g2 < kBAhead && g2 < total; ++g2) issue_b(g2);
+        }
         long gc = 0;
-        int tcount = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tcount) {
-            const int xs = t % a.ntiles_x, row = t / a.ntiles_x;
-            const int y = row % a.wy, z = row / a.wy;
-            const int x = xs * kDM + m;
-            const int xc = min(x, a.wx - 1);
-            // translation t = window index - kmax; padded index = t + lo
-            const long pbase = ((long)(z - a.kz + a.loz) * a.PY + (y - a.ky + a.loy)) * a.PX + (xc - a.kx + a.lox);
+        for (long k = 0; k < mine; ++k) {
+            if (!(ok = tc::mbar_wait(boxfull, (uint32_t)(k & 1)))) break;
+            const uint32_t *box = boxes + base_m;
             for (int c = 0; c < nchunk; ++c, ++gc) {
                 const int s = (int)(gc & 1);
                 const uint32_t u = (uint32_t)(gc >> 1);
                 if (u > 0 && !(ok = tc::mbar_wait(&empty[s], (u - 1) & 1))) break;
                 if (*((volatile int *)&s_abort)) { ok = false; break; }
+                // slot (gc + kBAhead) mod kBSlots last held chunk gc - 2, whose MMAs the wait above
+                // saw complete
+                if (threadIdx.x == 0 && gc + kBAhead < total) {
+                    tc::fence_async_smem();      // the slot's tap offsets were read by the generic proxy
+                    issue_b(gc + kBAhead);
+                }
+                // this chunk's tap offsets arrived with its B (issued kBAhead chunks ago)
+                const int bs = (int)(gc % kBSlots);
+                if (!(ok = tc::mbar_wait(&bfull[bs], (uint32_t)((gc / kBSlots) & 1)))) break;
                 uint8_t *Ahi = Ast + (2 * s) * kStageBytes, *Alo = Ahi + kStageBytes;
-                const int *taps = a.tapoff + c * kDKC;
-                // 8 consecutive taps per step: one 16-byte store per operand (a warp writes 512
-                // contiguous bytes of the canonical layout, no bank conflicts)
+                const int *taps = reinterpret_cast<const int *>(Bst + bs * Lo.bchunk + (Lo.bchunk - 256));
+                // 8 taps per step: eight words of the box, one 16-byte store per operand (a warp
+                // reads 32 consecutive words per tap and writes 512 contiguous bytes)
 #pragma unroll
-                for (int kk = half * (kDKC / 2); kk < (half + 1) * (kDKC / 2); kk += 8) {
+                for (int kk = quarter * (kDKC / 4); kk < (quarter + 1) * (kDKC / 4); kk += 8) {
+                    const int4 o0 = *reinterpret_cast<const int4 *>(taps + kk);
+                    const int4 o1 = *reinterpret_cast<const int4 *>(taps + kk + 4);
                     uint32_t w[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) w[e] = __ldg(a.rhohl + pbase + __ldg(taps + kk + e));
+                    w[0] = box[o0.x]; w[1] = box[o0.y]; w[2] = box[o0.z]; w[3] = box[o0.w];
+                    w[4] = box[o1.x]; w[5] = box[o1.y]; w[6] = box[o1.z]; w[7] = box[o1.w];
                     uint4 vh, vl;
                     vh.x = (w[0] & 0xffffu) | (w[1] << 16); vl.x = (w[0] >> 16) | (w[1] & 0xffff0000u);
                     vh.y = (w[2] & 0xffffu) | (w[3] << 16); vl.y = (w[2] >> 16) | (w[3] & 0xffff0000u);
                     vh.z = (w[4] & 0xffffu) | (w[5] << 16); vl.z = (w[4] >> 16) | (w[5] & 0xffff0000u);
                     vh.w = (w[6] & 0xffffu) | (w[7] << 16); vl.w = (w[6] >> 16) | (w[7] & 0xffff0000u);
                     const uint32_t off = tc::kmajor_offset(m, kk, kDM);
-                    *(uint4 *)(Ahi + off) = vh;
-                    *(uint4 *)(Alo + off) = vl;
+                    *reinterpret_cast<uint4 *>(Ahi + off) = vh;
+                    *reinterpret_cast<uint4 *>(Alo + off) = vl;
                 }
                 tc::fence_async_smem();
                 tc::mbar_arrive(&full[s]);
             }
             if (!ok) break;
-            if (!(ok = tc::mbar_wait(dfull, tcount & 1))) break;
+            // this tile's reads of the box are done: once every producer says so, thread 0 refills
+            // it with the next tile's box (generic-proxy reads before the async-proxy write)
+            tc::mbar_arrive(boxfree);
+            if (threadIdx.x == 0 && k + 1 < mine) {
+                if (!(ok = tc::mbar_wait(boxfree, (uint32_t)(k & 1)))) break;
+                tc::fence_async_smem();
+                issue_box(k + 1);
+            }
+            if (!(ok = tc::mbar_wait(dfull, (uint32_t)(k & 1)))) break;
             tc::fence_after();
-            // epilogue: D row m, this warp's half of the columns (= orientations of the group)
-            const bool valid = x < a.wx;
+            // epilogue: D row m, this warp's groups of 8 columns (= orientations of the group)
+            const int t = (int)blockIdx.x + (int)k * G;
+            const int tx = t % a.ntx, r = t / a.ntx, ty = r % a.nty, tz = r / a.nty;
             const int q = warp & 3;
-            for (int n0 = half * (a.N / 2); n0 < (half + 1) * (a.N / 2); n0 += 8) {
+            const int x = 32 * tx + lane, y = a.TY * ty + q % a.TY, z = a.TZ * tz + q / a.TY;
+            const bool rowv = y < a.wy && z < a.wz;             // uniform across the warp
+            const bool valid = rowv && x < a.wx;
+            for (int n0 = quarter * 8; n0 < a.N; n0 += 32) {
                 float v[8];
                 tc::tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)n0, v);
 #pragma unroll
@@ -199,7 +281,7 @@ __global__ void __launch_bounds__(kDThreads, 2) direct_corr_kernel(DirectArgs a)
                     if (valid) g[x] = gv;
                     const unsigned fb = __ballot_sync(0xffffffffu, valid && gv <= a.theta);
                     uint32_t *bw = a.bits + (long)n * a.b_so + (long)z * a.b_sz + (long)y * a.b_sy;
-                    if (lane == 0 && xs * kDM + q * 32 < a.wx) bw[(xs * kDM + q * 32) >> 5] = fb;
+                    if (lane == 0 && rowv) bw[tx] = fb;
                     if (a.flag) {
                         const bool near = valid && fabsf(gv - a.theta) <= a.band;
                         const unsigned nm = __ballot_sync(0xffffffffu, near);
@@ -230,11 +312,18 @@ __global__ void __launch_bounds__(kDThreads, 2) direct_corr_kernel(DirectArgs a)
             atomicExch(a.status, kDevTimeout);
             atomicExch(&s_abort, 1);
         }
+        // no copy of this block may still be landing in shared memory when it ends: wait (bounded)
+        // for the last phase of every buffer thread 0 filled
+        if (threadIdx.x == 0) {
+            if (last_box >= 0) tc::mbar_wait(boxfull, (uint32_t)(last_box & 1));
+            for (int i = 0; i < kBSlots; ++i)
+                if (last_b[i] >= 0) tc::mbar_wait(&bfull[i], (uint32_t)((last_b[i] / kBSlots) & 1));
+        }
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 8) tc::tmem_dealloc(tmem, ncols);
+    if (warp == kDProd / 32) tc::tmem_dealloc(tmem, ncols);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -297,11 +386,7 @@ __global__ void __launch_bounds__(128, 1) mma_selftest_kernel(const uint16_t *A,
 
 } // namespace
 
-size_t direct_smem_bytes(int kpad, int N)
-{
-    const size_t b = ((size_t)kpad * N * 2 + 1023) & ~(size_t)1023;
-    return b + 4 * (size_t)kStageBytes + 8 * sizeof(uint64_t) + 16;
-}
+size_t direct_smem_bytes(int N, long box_words) { return 1024 + direct_layout(N, box_words).total; }
 
 void launch_rho_hl(const float *rho, const uint8_t *fix, int nx, int ny, int nz, int lox, int loy, int loz, int PX,
                    int PY, int PZ, uint32_t *out, cudaStream_t s)
@@ -312,13 +397,22 @@ void launch_rho_hl(const float *rho, const uint8_t *fix, int nx, int ny, int nz,
     rho_hl_kernel<<<(int)b, 256, 0, s>>>(rho, fix, nx, ny, nz, lox, loy, loz, PX, PY, PZ, out);
 }
 
-void launch_direct(const DirectArgs &a, int nsm, cudaStream_t s)
+bool launch_direct(const DirectArgs &a, int nsm, cudaStream_t s)
 {
-    const size_t smem = direct_smem_bytes(a.kpad, a.N);
-    cudaFuncSetAttribute(direct_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int ntiles = a.ntiles_x * a.wy * a.wz;
-    const int grid = ntiles < 2 * nsm ? ntiles : 2 * nsm;
-    direct_corr_kernel<<<grid, kDThreads, smem, s>>>(a);
+    CUtensorMap map;
+    const uint64_t dims[3] = {(uint64_t)a.PX, (uint64_t)a.PY, (uint64_t)a.PZ};
+    const uint64_t strides[2] = {(uint64_t)a.PX * 4, (uint64_t)a.PX * a.PY * 4};
+    const uint32_t box[3] = {(uint32_t)a.BX, (uint32_t)a.BY, (uint32_t)a.BZ};
+    if (!tma_fft::encode_tiled_u32(&map, a.rhohl, 3, dims, strides, box)) return false;
+    const size_t smem = direct_smem_bytes(a.N, (long)a.BX * a.BY * a.BZ);
+    if (cudaFuncSetAttribute(direct_corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int ntiles = a.ntx * a.nty * a.ntz;
+    const int grid = ntiles < nsm ? ntiles : nsm;
+    if (grid > 0) direct_corr_kernel<<<grid, kDThreads, smem, s>>>(map, a);
+    return true;
 }
 
 int run_mma_selftest(const uint16_t *A, const uint16_t *B, float *D, int N, int K, int *status, cudaStream_t s)

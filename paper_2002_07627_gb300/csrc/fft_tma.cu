@@ -56,8 +56,10 @@ bool encode(CUtensorMap *m, const void *ptr, int rank, int nx, long rows, long r
 
 } // namespace
 
-bool encode_tiled(CUtensorMap *m, const void *ptr, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
-                  const uint32_t *box)
+namespace {
+
+bool encode_tiled_es(CUtensorMap *m, const void *ptr, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
+                     const uint32_t *box, int es_bytes, CUtensorMapDataType dt)
 {
     EncodeFn fn = encode_fn();
     if (!fn || rank < 1 || rank > 5 || (reinterpret_cast<uint64_t>(ptr) & 15)) return false;
@@ -73,10 +75,24 @@ bool encode_tiled(CUtensorMap *m, const void *ptr, int rank, const uint64_t *dim
         stride[i] = strides_bytes[i];
         if (stride[i] == 0 || stride[i] % 16 || stride[i] >= (1ull << 40)) return false;
     }
-    if ((box[0] * 8) % 16) return false;
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)rank, const_cast<void *>(ptr), dim, stride, bx, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    if (((uint64_t)box[0] * es_bytes) % 16) return false;
+    return fn(m, dt, (cuuint32_t)rank, const_cast<void *>(ptr), dim, stride, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+} // namespace
+
+bool encode_tiled(CUtensorMap *m, const void *ptr, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
+                  const uint32_t *box)
+{
+    return encode_tiled_es(m, ptr, rank, dims, strides_bytes, box, 8, CU_TENSOR_MAP_DATA_TYPE_UINT64);
+}
+
+bool encode_tiled_u32(CUtensorMap *m, const void *ptr, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
+                      const uint32_t *box)
+{
+    return encode_tiled_es(m, ptr, rank, dims, strides_bytes, box, 4, CU_TENSOR_MAP_DATA_TYPE_UINT32);
 }
 
 int sm_count()

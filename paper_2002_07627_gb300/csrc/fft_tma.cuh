@@ -36,6 +36,9 @@ int sm_count();   // multiprocessors of the current device (fft_tma.cu)
 // bytes, box in elements; false when a tensor map cannot describe it (fft_tma.cu).
 bool encode_tiled(CUtensorMap *m, const void *ptr, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
                   const uint32_t *box);
+// the same for 4-byte elements (the direct path's packed BF16 hi / lo words)
+bool encode_tiled_u32(CUtensorMap *m, const void *ptr, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
+                      const uint32_t *box);
 // shortest pencil of the 16-slot shape the persistent kernel is built for (shorter ones, on
 // tiny grids, keep the one-shot kernel; fewer instances keep the build short)
 constexpr int kMinLength = 64;

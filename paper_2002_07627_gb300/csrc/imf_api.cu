@@ -12,6 +12,7 @@
 // The translation window holds t in [-kmax, n - 1 - kmin] per axis at index t + kmax, where
 // kmin / kmax bound the cutter and sharp-point offsets of every orientation of the tool.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <map>
@@ -86,6 +87,8 @@ struct Tool {
     int dG = 0;                          // orientations per group
     std::vector<int> grp_start, grp_kpad, grp_N;
     std::vector<long> grp_tap_off, grp_b_off;
+    std::vector<std::array<int, 7>> grp_box;    // per group: union minimum (x, y, z), box BX BY BZ, sx
+    int dTY = 2, dTZ = 2;                // tile of 32 x dTY x dTZ translations
     int *d_taps = nullptr;
     uint16_t *d_bmat = nullptr;
     int dlo[3] = {0, 0, 0}, dP[3] = {1, 1, 1};
@@ -409,13 +412,17 @@ void free_tool(imf_handle h, Tool &t)
     t = Tool();
 }
 
-constexpr size_t kDirectSmemLimit = 220 * 1024;
+constexpr size_t kDirectSmemLimit = 224 * 1024;
 
 // byte offset of element (row r, column k) in a K-major canonical tile with R rows
 inline size_t tc_kmajor(int r, int k, int R) { return (size_t)(k >> 3) * (R * 16) + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
 
-// Groups of consecutive orientations, their union tap lists (linear offsets in the padded
-// copy of rho_O) and B matrices (BF16 0/1, K-major canonical layout, N rows).
+// Groups of consecutive orientations, their union tap lists (word offsets in the box of rho_O a
+// tile of the direct kernel reads) and B matrices (BF16 0/1, K-major canonical layout, N rows).
+// The group size minimises a cost model of the kernel: per tile and 64 taps of the union, the A
+// build (about 512 shared-memory wavefronts, whatever N) or the MMAs and their operand reads
+// (about 4.6 N + 256 cycles), whichever is larger, summed over the groups; groups whose box and
+// buffers do not fit shared memory are not taken.
 bool plan_direct(Tool &t, const int n[3], int vlo[3], int vhi[3], std::vector<int> &taps, std::vector<uint16_t> &bm)
 {
     for (int c = 0; c < 3; ++c) {
@@ -423,56 +430,107 @@ bool plan_direct(Tool &t, const int n[3], int vlo[3], int vhi[3], std::vector<in
         const int hi = std::max(0, vhi[c] - t.kmin[c]);
         t.dP[c] = n[c] + t.dlo[c] + hi;
     }
-    const long PX = t.dP[0], PY = t.dP[1];
-    for (int G = std::min(256, (t.n_orient + 15) / 16 * 16); G >= 16; G -= 16) {
-        std::vector<int> gs, gk, gn;
-        std::vector<long> gto, gbo;
-        std::vector<int> tp;
-        std::vector<uint16_t> b;
-        bool fits = true;
-        double macs = 0;
-        for (int o0 = 0; o0 < t.n_orient && fits; o0 += G) {
-            const int nb = std::min(G, t.n_orient - o0);
-            const int N = (nb + 15) / 16 * 16;
-            std::vector<long> uni;
-            for (int i = o0; i < o0 + nb; ++i)
-                for (size_t m = 0; m < t.rt[i].size(); m += 3)
-                    uni.push_back(((long)t.rt[i][m + 2] * PY + t.rt[i][m + 1]) * PX + t.rt[i][m]);
-            std::sort(uni.begin(), uni.end());
-            uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
-            const int kpad = std::max(64, (int)((uni.size() + 63) / 64 * 64));
-            if (direct_smem_bytes(kpad, N) > kDirectSmemLimit) { fits = false; break; }
-            gs.push_back(o0);
-            gk.push_back(kpad);
-            gn.push_back(N);
-            gto.push_back((long)tp.size());
-            gbo.push_back((long)b.size());
-            for (int k = 0; k < kpad; ++k) tp.push_back(k < (int)uni.size() ? (int)uni[k] : 0);
-            const size_t b0 = b.size();
-            b.resize(b0 + (size_t)N * kpad, 0);
-            for (int i = o0; i < o0 + nb; ++i)
-                for (size_t m = 0; m < t.rt[i].size(); m += 3) {
-                    const long off = ((long)t.rt[i][m + 2] * PY + t.rt[i][m + 1]) * PX + t.rt[i][m];
-                    const int k = (int)(std::lower_bound(uni.begin(), uni.end(), off) - uni.begin());
-                    b[b0 + tc_kmajor(i - o0, k, N) / 2] = 0x3F80;    // BF16 1.0
+    t.dP[0] = (t.dP[0] + 3) & ~3;           // rows of 16-byte multiples (tensor-map stride)
+    t.dTY = n[2] == 1 ? 4 : 2;
+    t.dTZ = n[2] == 1 ? 1 : 2;
+    const int EX = vhi[0] - vlo[0] + 1, EY = vhi[1] - vlo[1] + 1;
+    auto key = [&](const int32_t *v) {
+        return ((long)(v[2] - vlo[2]) * EY + (v[1] - vlo[1])) * EX + (v[0] - vlo[0]);
+    };
+    // union of a group as sorted keys, with its bounds
+    auto group_union = [&](int o0, int nb, std::vector<long> &uni, int glo[3], int ghi[3]) {
+        uni.clear();
+        for (int c = 0; c < 3; ++c) { glo[c] = 1 << 30; ghi[c] = -(1 << 30); }
+        for (int i = o0; i < o0 + nb; ++i)
+            for (size_t m = 0; m < t.rt[i].size(); m += 3) {
+                uni.push_back(key(&t.rt[i][m]));
+                for (int c = 0; c < 3; ++c) {
+                    glo[c] = std::min(glo[c], t.rt[i][m + c]);
+                    ghi[c] = std::max(ghi[c], t.rt[i][m + c]);
                 }
-            const long tiles = (long)((t.win[0] + 127) / 128) * t.win[1] * t.win[2];
-            macs += 2.0 * tiles * 128.0 * N * kpad;
+            }
+        std::sort(uni.begin(), uni.end());
+        uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
+    };
+    auto box_of = [&](const int glo[3], const int ghi[3], int &BX, int &BY, int &BZ) {
+        BX = (3 + 32 + ghi[0] - glo[0] + 3) & ~3;
+        BY = t.dTY + ghi[1] - glo[1];
+        BZ = t.dTZ + ghi[2] - glo[2];
+        return BX <= 256 && BY <= 256 && BZ <= 256 &&
+               direct_smem_bytes(16, (long)BX * BY * BZ) <= kDirectSmemLimit;
+    };
+    int bestG = 0;
+    double best = 1e300;
+    std::vector<long> uni;
+    for (int G = std::min(256, (t.n_orient + 15) / 16 * 16); G >= 16; G -= 16) {
+        bool fits = true;
+        double cost = 0;
+        for (int o0 = 0; o0 < t.n_orient && fits; o0 += G) {
+            const int nb = std::min(G, t.n_orient - o0), N = (nb + 15) / 16 * 16;
+            int glo[3], ghi[3], BX, BY, BZ;
+            group_union(o0, nb, uni, glo, ghi);
+            fits = box_of(glo, ghi, BX, BY, BZ) && direct_smem_bytes(N, (long)BX * BY * BZ) <= kDirectSmemLimit;
+            const int kpad = std::max(64, (int)((uni.size() + 63) / 64 * 64));
+            cost += kpad * std::max(512.0, 4.6 * N + 256.0);
         }
-        if (!fits) continue;
-        gs.push_back(t.n_orient);
-        t.dG = G;
-        t.grp_start = gs;
-        t.grp_kpad = gk;
-        t.grp_N = gn;
-        t.grp_tap_off = gto;
-        t.grp_b_off = gbo;
-        t.direct_macs = macs;
-        taps.swap(tp);
-        bm.swap(b);
-        return true;
+        if (fits && cost < best) {
+            best = cost;
+            bestG = G;
+        }
     }
-    return false;
+    if (!bestG) return false;
+    const int G = bestG;
+    std::vector<int> gs, gk, gn;
+    std::vector<long> gto, gbo;
+    std::vector<std::array<int, 7>> gbox;
+    std::vector<int> tp;
+    std::vector<uint16_t> b;
+    double macs = 0;
+    for (int o0 = 0; o0 < t.n_orient; o0 += G) {
+        const int nb = std::min(G, t.n_orient - o0), N = (nb + 15) / 16 * 16;
+        int glo[3], ghi[3], BX, BY, BZ;
+        group_union(o0, nb, uni, glo, ghi);
+        box_of(glo, ghi, BX, BY, BZ);
+        const int kpad = std::max(64, (int)((uni.size() + 63) / 64 * 64));
+        const int sx = (((glo[0] - t.kmax[0] + t.dlo[0]) % 4) + 4) % 4;
+        gs.push_back(o0);
+        gk.push_back(kpad);
+        gn.push_back(N);
+        gbox.push_back({glo[0], glo[1], glo[2], BX, BY, BZ, sx});
+        gto.push_back((long)tp.size());
+        gbo.push_back((long)b.size());
+        for (int k = 0; k < kpad; ++k) {
+            int off = 0;
+            if (k < (int)uni.size()) {
+                const long kx = uni[k] % EX, ky = (uni[k] / EX) % EY, kz = uni[k] / ((long)EX * EY);
+                const int vx = (int)kx + vlo[0], vy = (int)ky + vlo[1], vz = (int)kz + vlo[2];
+                off = (vx - glo[0]) + BX * ((vy - glo[1]) + BY * (vz - glo[2]));
+            }
+            tp.push_back(off);
+        }
+        const size_t b0 = b.size();
+        b.resize(b0 + (size_t)N * kpad, 0);
+        for (int i = o0; i < o0 + nb; ++i)
+            for (size_t m = 0; m < t.rt[i].size(); m += 3) {
+                const int k = (int)(std::lower_bound(uni.begin(), uni.end(), key(&t.rt[i][m])) - uni.begin());
+                b[b0 + tc_kmajor(i - o0, k, N) / 2] = 0x3F80;    // BF16 1.0
+            }
+        const long tiles = (long)((t.win[0] + 31) / 32) * ((t.win[1] + t.dTY - 1) / t.dTY) *
+                           ((t.win[2] + t.dTZ - 1) / t.dTZ);
+        macs += 2.0 * tiles * 128.0 * N * kpad;
+    }
+    gs.push_back(t.n_orient);
+    t.dG = G;
+    t.grp_start = gs;
+    t.grp_kpad = gk;
+    t.grp_N = gn;
+    t.grp_tap_off = gto;
+    t.grp_b_off = gbo;
+    t.grp_box = gbox;
+    t.direct_macs = macs;
+    taps.swap(tp);
+    bm.swap(b);
+    return true;
 }
 
 // Sizes of the per-handle work buffers for the current tools (elements; see ensure_work).
@@ -1220,19 +1278,26 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
                 if (op.recheck) CU(cudaMemsetAsync(fcount, 0, sizeof(int), s));
                 {
                     DirectArgs a{};
-                    a.rhohl = h->rhohl; a.PX = t.dP[0]; a.PY = t.dP[1];
+                    a.rhohl = h->rhohl; a.PX = t.dP[0]; a.PY = t.dP[1]; a.PZ = t.dP[2];
                     a.lox = t.dlo[0]; a.loy = t.dlo[1]; a.loz = t.dlo[2];
                     a.tapoff = t.d_taps + t.grp_tap_off[gi]; a.kpad = t.grp_kpad[gi];
                     a.bmat = t.d_bmat + t.grp_b_off[gi]; a.N = t.grp_N[gi]; a.nb = nb;
+                    const std::array<int, 7> &bx = t.grp_box[gi];
+                    a.vlo[0] = bx[0]; a.vlo[1] = bx[1]; a.vlo[2] = bx[2];
+                    a.BX = bx[3]; a.BY = bx[4]; a.BZ = bx[5]; a.sx = bx[6];
+                    a.TY = t.dTY; a.TZ = t.dTZ;
                     a.wx = t.win[0]; a.wy = t.win[1]; a.wz = t.win[2];
-                    a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2]; a.ntiles_x = (t.win[0] + 127) / 128;
+                    a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2];
+                    a.ntx = (t.win[0] + 31) / 32; a.nty = (t.win[1] + t.dTY - 1) / t.dTY;
+                    a.ntz = (t.win[2] + t.dTZ - 1) / t.dTZ;
                     a.g = h->g; a.g_sy = t.gpx; a.g_sz = (long)t.win[1] * t.gpx; a.g_so = gso_;
                     a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso_;
                     a.theta = (float)t.theta; a.band = (float)t.band; a.flag = op.recheck;
                     a.flags = h->flags; a.flag_count = fcount; a.flag_total = h->dev_small + 4;
                     a.flag_cap = h->flag_cap; a.status = status; a.orient_base = o0;
                     Launch L(h, KID_DIRECT, s);
-                    launch_direct(a, h->nsm, s);
+                    if (!launch_direct(a, h->nsm, s))
+                        return fail(h, IMF_ERR_CUDA, "direct path: the rho_O box cannot be described by a tensor map");
                 }
                 TRY(tail_batch(h, t, rho, fix, o0, nb, s));
                 h->last_tool = ti;

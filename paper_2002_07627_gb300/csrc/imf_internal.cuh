@@ -188,15 +188,19 @@ void launch_plan_remove(const uint32_t *set, long words, uint32_t *remaining, cu
 
 // Direct collision convolution on the tensor cores (direct_tc.cu).
 struct DirectArgs {
-    const uint32_t *rhohl;       // padded rho_O as (hi | lo << 16) BF16 pairs
-    int PX, PY;                  // padded pitches
+    const uint32_t *rhohl;       // padded rho_O as (hi | lo << 16) BF16 pairs, [PZ][PY][PX], PX % 4 == 0
+    int PX, PY, PZ;              // padded extents
     int lox, loy, loz;           // padding before the grid along x, y, z
-    const int *tapoff;           // union taps of the group as linear offsets in the padded array
+    const int *tapoff;           // union taps of the group as word offsets in the tile's box
     int kpad;                    // taps, padded to a multiple of 64 (padding taps have B = 0)
     const uint16_t *bmat;        // B [N x kpad] BF16 0/1 in the K-major canonical layout
     int N, nb;                   // MMA N (multiple of 16) and orientations in the group
+    int vlo[3];                  // smallest union offset of the group (x, y, z)
+    int BX, BY, BZ;              // box of rho_O words a tile reads (BX % 4 == 0)
+    int sx;                      // x offset of the tile's first translation in its box (0..3)
+    int TY, TZ;                  // tile of 32 x TY x TZ = 128 translations (TY TZ = 4)
     int wx, wy, wz, kx, ky, kz;  // translation window and kmax (t = window index - kmax)
-    int ntiles_x;                // ceil(wx / 128)
+    int ntx, nty, ntz;           // tiles along x, y, z
     float *g;
     long g_sy, g_sz, g_so;
     uint32_t *bits;
@@ -209,10 +213,12 @@ struct DirectArgs {
     int *status;
     int orient_base;
 };
-size_t direct_smem_bytes(int kpad, int N);
+// dynamic shared memory of the direct kernel for a group with MMA N and a box of `box_words`
+size_t direct_smem_bytes(int N, long box_words);
 void launch_rho_hl(const float *rho, const uint8_t *fix, int nx, int ny, int nz, int lox, int loy, int loz, int PX,
                    int PY, int PZ, uint32_t *out, cudaStream_t s);
-void launch_direct(const DirectArgs &a, int nsm, cudaStream_t s);
+// false when the box cannot be described by a tensor map (the caller reports it)
+bool launch_direct(const DirectArgs &a, int nsm, cudaStream_t s);
 int run_mma_selftest(const uint16_t *A, const uint16_t *B, float *D, int N, int K, int *status, cudaStream_t s);
 
 void launch_fill_f32(float *p, float v, long n, cudaStream_t s);
