@@ -163,7 +163,6 @@ __device__ __forceinline__ void fill_tile(const Erode2Args &a, const float *g, c
 template <int XT> __global__ void __launch_bounds__(er_threads(XT), 1) erode2_kernel(Erode2Args a)
 {
     extern __shared__ float tile[];
-    __shared__ int2 sruns[kErMaxRunsPerChunk];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // lane = ty_lo (8) x tz_lo (4); warp = tx (kErTX / XT) x ty_hi (kErTY / 8) x tz_hi
     constexpr int NT = er_threads(XT), NXT = kErTX / XT, NYH = kErTY / 8;
@@ -198,6 +197,8 @@ template <int XT> __global__ void __launch_bounds__(er_threads(XT), 1) erode2_ke
             const ErodeChunk &ch = a.chunks[c];
             const int pz = ch.pitch_z, py = ch.pitch_y;
             const int run0 = ch.run0, nrun = ch.run1 - ch.run0;
+            // the chunk's run descriptors sit behind its tile
+            int2 *sruns = reinterpret_cast<int2 *>(tile + er_runs_offset(ch.tzh, pz));
             __syncthreads();
             fill_tile<NT>(a, g, ch, X0, Y0, Z0, sbase, warp, lane);
             for (int q = threadIdx.x; q < nrun; q += NT) sruns[q] = a.runs[run0 + q];
@@ -302,7 +303,6 @@ __device__ __forceinline__ void build_level(float *tile, const ErodeChunk &ch, i
 __global__ void __launch_bounds__(kErThreads, kErBlocksPerSM) erode3_kernel(Erode2Args a)
 {
     extern __shared__ float tile[];
-    __shared__ int2 sruns[kErMaxRunsPerChunk];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NXT = kErTX / kErXT, NYH = kErTY / 8;
     static_assert(NXT * NYH * (kErTZ / 4) * 32 == kErThreads, "erosion block shape");
@@ -331,6 +331,7 @@ __global__ void __launch_bounds__(kErThreads, kErBlocksPerSM) erode3_kernel(Erod
         for (int c = a.chunk_start[og]; c < a.chunk_start[og + 1]; ++c) {
             const ErodeChunk &ch = a.chunks[c];
             const int run0 = ch.run0, nrun = ch.run1 - ch.run0;
+            int2 *sruns = reinterpret_cast<int2 *>(tile + er_runs_offset(ch.tzh, ch.pitch_z));
             __syncthreads();
             fill_tile<kErThreads>(a, g, ch, X0, Y0, Z0, sbase, warp, lane);
             for (int q = threadIdx.x; q < nrun; q += kErThreads) sruns[q] = a.runs[run0 + q];
@@ -436,7 +437,6 @@ int erode3_blocks_per_sm(size_t smem)
 
 template <int XT> void launch_erode2_xt(const Erode2Args &a, size_t smem, cudaStream_t s)
 {
-    // the static descriptor table counts against the default 48 KB, so always raise the limit
     cudaFuncSetAttribute(erode2_kernel<XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((a.nx + kErTX - 1) / kErTX, (a.ny + kErTY - 1) / kErTY, ((a.nz + kErTZ - 1) / kErTZ) * a.ngroups);
     erode2_kernel<XT><<<grid, er_threads(XT), smem, s>>>(a);

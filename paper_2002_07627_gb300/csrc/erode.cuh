@@ -23,10 +23,13 @@ constexpr int kErThreads = (kErTX / kErXT) * kErTY * kErTZ;
 // threads of a block with xt consecutive x outputs per thread
 __host__ __device__ constexpr int er_threads(int xt) { return (kErTX / xt) * kErTY * kErTZ; }
 constexpr int kErBlocksPerSM = 1024 / kErThreads;            // 64 registers per thread
-constexpr int kErMaxRunsPerChunk = 2 * kErThreads;
-// shared-memory tile budget per block: kErBlocksPerSM blocks of tile + run table fit in 228 KB
-// (one 1024-thread block: 208 KB of tile + 16 KB of run descriptors)
-constexpr size_t kErodeBudget = (kErThreads >= 1024 ? 208 : kErThreads >= 512 ? 104 : 50) * 1024;
+// most run descriptors of one chunk (larger chunks are split)
+constexpr int kErMaxRunsPerChunk = 2048;
+// dynamic shared memory of one block (one per SM): a chunk's g tile followed by its run
+// descriptors (8 bytes each), sized per chunk so that the tile takes what the runs leave
+constexpr size_t kErodeBudget = 222 * 1024;
+// float offset of a chunk's run descriptors behind its tile of tzh planes (8-byte aligned)
+__host__ __device__ constexpr int er_runs_offset(int tzh, int pitch_z) { return (tzh * pitch_z + 1) & ~1; }
 struct ErodeChunk {
     int run0, run1;              // runs of this chunk, sorted by length
     int lend[kErMaxL3 + 1];      // runs of length L are run0 + lend[L-1] .. run0 + lend[L] - 1

@@ -27,9 +27,10 @@ inline bool bank_free(int P, int Q)
 }
 
 // Runs along x (at most maxL long) of the sharp points `sh` (offset triples) of one orientation,
-// grouped in dz-chunks whose g tile fits kErodeBudget bytes; appends the chunks and their (tile offset,
-// length) runs and raises smem_max to the largest tile. K = kmax of the tool's cutter offsets
-// (the translation window starts at t = -K).
+// grouped in dz-chunks whose g tile and run descriptors fit kErodeBudget bytes together (each
+// chunk takes as many dz as fit, from the largest down); appends the chunks and their (tile
+// offset, length) runs and raises smem_max to the largest tile plus descriptors. K = kmax of the
+// tool's cutter offsets (the translation window starts at t = -K).
 
 inline void plan_erode(const std::vector<int32_t> &sh, const int K[3], std::vector<ErodeChunk> &chunks,
                 std::vector<int2> &runs, size_t &smem_max, int maxL = kErMaxL)
@@ -60,10 +61,25 @@ inline void plan_erode(const std::vector<int32_t> &sh, const int K[3], std::vect
     const int P = txh | 1;
     int Q = tyh * P;
     while (!bank_free(P, Q)) ++Q;
-    int planes = (int)(kErodeBudget / (4 * (size_t)Q));
-    int dzc = planes - kErTZ + 1;
-    if (dzc < 1) dzc = 1;
+    std::map<int, int> runs_at;                               // dz -> runs
+    for (const Run &r : rr) ++runs_at[r.dz];
+    const int planes = (int)(kErodeBudget / (4 * (size_t)Q));
+    const int dzc_max = std::max(1, planes - kErTZ + 1);
+    int dzc = dzc_max;
     for (int hi = kmx[2]; hi >= kmn[2]; hi -= dzc) {
+        // the most dz (down from hi) whose tile and descriptors fit the budget together
+        dzc = 1;
+        for (int d = 1; d <= dzc_max && hi - d + 1 >= kmn[2]; ++d) {
+            long nr = 0;
+            for (int z = hi - d + 1; z <= hi; ++z) {
+                auto it = runs_at.find(z);
+                if (it != runs_at.end()) nr += it->second;
+            }
+            const size_t bytes = 4 * (size_t)er_runs_offset(kErTZ + d - 1, Q) +
+                                 8 * (size_t)std::min<long>(nr, kErMaxRunsPerChunk);
+            if (bytes > kErodeBudget) break;
+            dzc = d;
+        }
         const int lo = std::max(kmn[2], hi - dzc + 1);
         std::vector<int2> cr;
         for (const Run &r : rr) {
@@ -90,7 +106,10 @@ inline void plan_erode(const std::vector<int32_t> &sh, const int K[3], std::vect
             ch.ox = K[0] - kmx[0]; ch.oy = K[1] - kmx[1]; ch.oz = K[2] - hi;
             chunks.push_back(ch);
         }
-        smem_max = std::max(smem_max, (size_t)(kErTZ + (hi - lo)) * Q * sizeof(float));
+        for (size_t b = 0; b < cr.size(); b += kErMaxRunsPerChunk) {
+            const size_t nr = std::min(cr.size(), b + (size_t)kErMaxRunsPerChunk) - b;
+            smem_max = std::max(smem_max, 4 * (size_t)er_runs_offset(kErTZ + (hi - lo), Q) + 8 * nr);
+        }
     }
 }
 

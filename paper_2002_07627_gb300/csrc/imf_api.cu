@@ -1071,7 +1071,7 @@ imf_status imf_set_tool(imf_handle h, int tool_id, const uint8_t *holder, const 
         if (!t.erode_levels || rows_fit) break;
         t.erode_levels = false;
     }
-    if (t.erode_smem + kErMaxRunsPerChunk * sizeof(int2) > 227 * 1024) {
+    if (t.erode_smem > 227 * 1024) {
         free_tool(h, t);
         return fail(h, IMF_ERR_INVALID_ARG, "sharp-point set too wide for the tiled minimum (%zu bytes of tile)",
                     t.erode_smem);

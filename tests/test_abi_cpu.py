@@ -221,8 +221,8 @@ def test_erosion_plan_covers_every_sharp_point_once_within_the_tile(lib, case, m
     """The plan of the tiled minimum over sharp points (Eq. eq_imf_2), decoded with only the
     window origin K and each chunk's tile origin: its runs cover every sharp point exactly once,
     sit in length groups of at most 16 (the pairwise kernel) or 31 (the level kernel), every
-    thread position reads inside its chunk's tile, the tile fits the budget and the 32 lanes of
-    a warp (8 rows x 4 planes) hit 32 banks."""
+    thread position reads inside its chunk's tile, the tile and its run descriptors fit the
+    budget together and the 32 lanes of a warp (8 rows x 4 planes) hit 32 banks."""
     sh = np.asarray(_plan_cases()[case], np.int64)
     rng = np.random.default_rng(case)
     K = sh.max(0) + rng.integers(0, 5, size=3)      # any window origin at or beyond the largest offset
@@ -235,7 +235,9 @@ def test_erosion_plan_covers_every_sharp_point_once_within_the_tile(lib, case, m
         assert P % 2 == 1 and P >= txh and Q >= tyh * P
         banks = {(tz * Q + ty * P) % 32 for tz in range(4) for ty in range(8)}
         assert len(banks) == 32
-        assert tzh * Q * 4 <= max(c["budget"], c["tz"] * Q * 4) and tzh * Q * 4 <= smem
+        # tile and run descriptors (8 bytes each, 8-byte aligned behind the tile) fit together
+        need = 4 * ((tzh * Q + 1) // 2 * 2) + 8 * (run1 - run0)
+        assert need <= max(c["budget"], 4 * c["tz"] * Q + 8 * c["maxruns"]) and need <= smem
         assert 0 < run1 - run0 <= c["maxruns"] and lend[0] == 0 and lend[c["maxl"]] == run1 - run0
         for Lr in range(1, c["maxl"] + 1):
             seg = runs[run0 + lend[Lr - 1]: run0 + lend[Lr]]
