@@ -103,11 +103,19 @@ __device__ __forceinline__ void x_items(const XParams &P, const void *map, float
     }
 }
 
-__global__ void __launch_bounds__(kXT) irfft2_tma_kernel(const __grid_constant__ CUtensorMap map, XParams P)
+// blocks per SM an instance is compiled for: three (80 registers) where that keeps the split's
+// registers without spilling, two for the longest ones (M above 210)
+__host__ __device__ constexpr int x_min_blocks(int na, int nb) { return na * nb > 210 ? 2 : 3; }
+
+// one instance per split (A, B) of the x length, so that each gets its own register allocation
+template <int NA, int NB>
+__global__ void __launch_bounds__(kXT, x_min_blocks(NA, NB)) irfft2_tma_kernel(const __grid_constant__ CUtensorMap map,
+                                                                               XParams P)
 {
     extern __shared__ unsigned char smraw[];
     const IrfftArgs &a = P.a;
-    const int A = a.A2, B = a.B2, M = a.M, Ap = A | 1;
+    constexpr int A = NA, B = NB, Ap = A | 1;
+    const int M = a.M;
     const int ld = (M > B * Ap ? M : B * Ap) + 1, fp = (2 * M + 31) & ~31;
     unsigned char *base = smraw + ((128 - (tc::smem_addr(smraw) & 127)) & 127);
     const size_t stage = x_stage(P);
@@ -124,14 +132,7 @@ __global__ void __launch_bounds__(kXT) irfft2_tma_kernel(const __grid_constant__
         tc::fence_mbar_init();
     }
     __syncthreads();
-    fft2::with_size(A, [&](auto AA) {
-        constexpr int NA = decltype(AA)::value;
-        fft2::with_size(B, [&](auto BB) {
-            constexpr int NB = decltype(BB)::value;
-            if constexpr (fft2::is_split_choice(NA, NB, fft2::kMaxFactor) && NA * NB >= tma_fft::kMinLength)
-                x_items<NA, NB>(P, &map, st, stage, tile, sflag, twM, twP, bar);
-        });
-    });
+    x_items<NA, NB>(P, &map, st, stage, tile, sflag, twM, twP, bar);
 }
 
 size_t x_tma_smem(const XParams &P)
@@ -166,18 +167,30 @@ bool launch_irfft2_tma(const IrfftArgs &a, int hs, int norient, cudaStream_t s)
     if (!tma_fft::encode_tiled(&map, a.in, 3, dims, strides, box)) return false;
     const size_t smem = x_tma_smem(P);
     if (smem > 227 * 1024) return false;
-    if (cudaFuncSetAttribute(irfft2_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, irfft2_tma_kernel, kXT, smem) != cudaSuccess || per < 1) {
-        cudaGetLastError();
-        return false;
-    }
-    const long blocks = P.items < (long)per * tma_fft::sm_count() ? P.items : (long)per * tma_fft::sm_count();
-    irfft2_tma_kernel<<<(unsigned)blocks, kXT, smem, s>>>(map, P);
-    return true;
+    bool launched = false;
+    fft2::with_size(a.A2, [&](auto AA) {
+        constexpr int NA = decltype(AA)::value;
+        fft2::with_size(a.B2, [&](auto BB) {
+            constexpr int NB = decltype(BB)::value;
+            if constexpr (fft2::is_split_choice(NA, NB, fft2::kMaxFactor) && NA * NB >= tma_fft::kMinLength) {
+                auto kern = irfft2_tma_kernel<NA, NB>;
+                if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+                    cudaGetLastError();
+                    return;
+                }
+                int per = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kXT, smem) != cudaSuccess || per < 1) {
+                    cudaGetLastError();
+                    return;
+                }
+                const long blocks =
+                    P.items < (long)per * tma_fft::sm_count() ? P.items : (long)per * tma_fft::sm_count();
+                kern<<<(unsigned)blocks, kXT, smem, s>>>(map, P);
+                launched = true;
+            }
+        });
+    });
+    return launched;
 }
 
 } // namespace imf
