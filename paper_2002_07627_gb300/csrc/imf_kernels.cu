@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a)
             __syncthreads();
             if (!live || (acc & full) == full) continue;
             // unrolled so that the loads of several runs are in flight at once
-#pragma unroll 4
+#pragma unroll 8
             for (int i = 0; i < cn; ++i) {
                 const int4 d = sp[i];
                 acc |= sweep_pair_bits(base + (long)d.w * a.lstride + d.x, d);
