@@ -259,17 +259,37 @@ __global__ void __launch_bounds__(256) recheck_blocks_kernel(RecheckArgs a)
         const int tx = i - a.kx, ty = y - a.ky, tz = z - a.kz;
         float s = 0.f, c = 0.f;
         const int m1 = a.rt_start[og + 1];
-        for (int m = a.rt_start[og] + threadIdx.x; m < m1; m += blockDim.x) {
+        // rho_O at tool voxel m (0 outside the grid: adding it is exact, so the sum is the sum
+        // over the voxels inside)
+        auto tap = [&](int m) -> float {
             const uint32_t p = __ldg(a.rt_off + m);
             const int x = tx + (int)(p & 1023u) - 512;
             const int yy = ty + (int)((p >> 10) & 1023u) - 512;
             const int zz = tz + (int)((p >> 20) & 1023u) - 512;
-            if (x < 0 || yy < 0 || zz < 0 || x >= a.nx || yy >= a.ny || zz >= a.nz) continue;
+            if (x < 0 || yy < 0 || zz < 0 || x >= a.nx || yy >= a.ny || zz >= a.nz) return 0.f;
             const long idx = ((long)zz * a.ny + yy) * a.nx + x;
             float r = __ldg(a.rho + idx);
             if (a.fix && a.fix[idx]) r = fminf(1.f, r + 1.f);
+            return r;
+        };
+        // four taps per step, loaded together and summed in the order of the one-at-a-time loop
+        constexpr int U = 4;
+        int m = a.rt_start[og] + threadIdx.x;
+        for (; m + (U - 1) * (int)blockDim.x < m1; m += U * blockDim.x) {
+            float r[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) r[u] = tap(m + u * blockDim.x);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float t, err;
+                two_sum(s, r[u], t, err);
+                s = t;
+                c += err;
+            }
+        }
+        for (; m < m1; m += blockDim.x) {
             float t, err;
-            two_sum(s, r, t, err);
+            two_sum(s, tap(m), t, err);
             s = t;
             c += err;
         }
