@@ -1185,7 +1185,7 @@ imf_status tail_batch(imf_handle h, const Tool &t, const float *rho, const uint8
         a.bits = h->bits; a.b_sy = t.wpr; a.b_sz = (long)t.win[1] * t.wpr; a.b_so = bso;
         a.theta = t.theta; a.orient_base = o0;
         Launch L(h, KID_RECHECK, s);
-        launch_recheck_blocks(a, 152 * 8, s);
+        launch_recheck_blocks(a, 152 * 64, s);     // up to 64 points (warps) in flight per SM
     }
     if (h->run_sweep) {
         const long lstride = (long)h->bits_n * h->slots;

@@ -70,7 +70,7 @@ __global__ void scatter_tool_kernel(float *dst, int Px, int Py, int Pz, const ui
 
 // ---------------------------------------------------------------------------------------
 // Near-threshold re-check: g(t) = sum_{v in RT} rho_O(t + v) by a compensated FP32 sum
-// (Neumaier), compared with theta in FP64 (recheck_blocks_kernel below: one block per flagged
+// (Neumaier), compared with theta in FP64 (recheck_blocks_kernel below: one warp per flagged
 // translation).
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
@@ -245,14 +245,16 @@ __global__ void plan_remove_kernel(const uint32_t *set, long words, uint32_t *re
         rem[w] &= ~set[w];
 }
 
-// Block-per-point variant of the re-check: 256 threads split the tool voxels of one flagged
-// translation, then a compensated block reduction.
+// Warp-per-point re-check: the 32 lanes of a warp split the tool voxels of one flagged
+// translation (eight taps per lane in flight at once: the gathers of rho and of the fixture mostly
+// miss in L2), each lane keeps a compensated FP32 sum, the warp combines them with compensated
+// shuffles and lane 0 compares the total with theta in FP64.
 __global__ void __launch_bounds__(256) recheck_blocks_kernel(RecheckArgs a)
 {
-    __shared__ float rs[8], rc[8];
     const int n = min(*a.count, a.cap);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int e = blockIdx.x; e < n; e += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)(gridDim.x * (blockDim.x >> 5));
+    for (int e = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); e < n; e += warps) {
         const int2 fl = a.flags[e];
         const int og = fl.x, lin = fl.y;
         const int i = lin % a.wx, y = (lin / a.wx) % a.wy, z = lin / (a.wx * a.wy);
@@ -272,13 +274,12 @@ __global__ void __launch_bounds__(256) recheck_blocks_kernel(RecheckArgs a)
             if (a.fix && a.fix[idx]) r = fminf(1.f, r + 1.f);
             return r;
         };
-        // four taps per step, loaded together and summed in the order of the one-at-a-time loop
-        constexpr int U = 4;
-        int m = a.rt_start[og] + threadIdx.x;
-        for (; m + (U - 1) * (int)blockDim.x < m1; m += U * blockDim.x) {
+        constexpr int U = 8;
+        int m = a.rt_start[og] + lane;
+        for (; m + (U - 1) * 32 < m1; m += U * 32) {
             float r[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) r[u] = tap(m + u * blockDim.x);
+            for (int u = 0; u < U; ++u) r[u] = tap(m + u * 32);
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 float t, err;
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(256) recheck_blocks_kernel(RecheckArgs a)
                 c += err;
             }
         }
-        for (; m < m1; m += blockDim.x) {
+        for (; m < m1; m += 32) {
             float t, err;
             two_sum(s, tap(m), t, err);
             s = t;
@@ -302,17 +303,8 @@ __global__ void __launch_bounds__(256) recheck_blocks_kernel(RecheckArgs a)
             s = t;
             c = c + c2 + err;
         }
-        if (lane == 0) { rs[warp] = s; rc[warp] = c; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float S = rs[0], C = rc[0];
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-                float t, err;
-                two_sum(S, rs[w], t, err);
-                S = t;
-                C = C + rc[w] + err;
-            }
-            const double tot = (double)S + (double)C;
+        if (lane == 0) {
+            const double tot = (double)s + (double)c;
             const long slot = og - a.orient_base;
             a.g[slot * a.g_so + (long)z * a.g_sz + (long)y * a.g_sy + i] = (float)tot;
             uint32_t *w = a.bits + slot * a.b_so + (long)z * a.b_sz + (long)y * a.b_sy + (i >> 5);
@@ -320,7 +312,6 @@ __global__ void __launch_bounds__(256) recheck_blocks_kernel(RecheckArgs a)
             if (tot <= a.theta) atomicOr(w, bit);
             else atomicAnd(w, ~bit);
         }
-        __syncthreads();
     }
 }
 
@@ -456,7 +447,9 @@ void launch_plan_remove(const uint32_t *set, long words, uint32_t *remaining, cu
 
 void launch_recheck_blocks(const RecheckArgs &a, int max_points, cudaStream_t s)
 {
-    int blocks = max_points < 1 ? 1 : (max_points > 152 * 8 ? 152 * 8 : max_points);
+    // eight points (warps) per block, at most eight blocks per SM
+    const int want = (max_points + 7) / 8;
+    int blocks = want < 1 ? 1 : (want > 152 * 8 ? 152 * 8 : want);
     recheck_blocks_kernel<<<blocks, 256, 0, s>>>(a);
 }
 
