@@ -99,18 +99,10 @@ __device__ __forceinline__ void run_items(const Params &P, const void *in_map, c
     for (long k = 0; k < mine; ++k) {
         const int s = (int)(k % kStages);
         const bool timeout = !tc::mbar_wait(&bar[s], (uint32_t)((k / kStages) & 1));
-        if (__syncthreads_or(timeout)) {
-            if (threadIdx.x == 0) {
-                if (a.status) atomicCAS(a.status, 0, (int)IMF_ERR_TIMEOUT);
-                // drain this block's copies still in flight (bounded) before leaving
-                const long issued = k + kStages < mine ? k + kStages : mine;
-                for (long q = k; q < issued; ++q) tc::mbar_wait(&bar[q % kStages], (uint32_t)((q / kStages) & 1));
-            }
-            return;
-        }
         const long it = first + k * G;
         const float2 *sin_ = st + s * stage, *smul = sin_ + half;
-        // pass 1: slot p = n1 < NB reads x[n1 + NB n2] (times the factor) from the stage
+        // pass 1: slot p = n1 < NB reads x[n1 + NB n2] (times the factor) from the stage and
+        // transforms it in registers (after a timeout the values are not used)
         float2 v[NA];
         const bool act = p < NB;
         if (act) {
@@ -120,9 +112,20 @@ __device__ __forceinline__ void run_items(const Params &P, const void *in_map, c
                 v[n2] = sin_[j * W + w];
                 if (MUL) v[n2] = c_mul(v[n2], smul[j * W + w]);
             }
+            fft2::dft_reg<S, NA>(v);
+            fft2::twiddle<S, NA>(v, p, tw);
         }
-        // the stage is free (and the previous item's tile reads are done) past this barrier
-        __syncthreads();
+        // one barrier: the stage is free, the previous item's tile reads are done, and every
+        // thread knows whether a copy timed out
+        if (__syncthreads_or(timeout)) {
+            if (threadIdx.x == 0) {
+                if (a.status) atomicCAS(a.status, 0, (int)IMF_ERR_TIMEOUT);
+                // drain this block's copies still in flight (bounded) before leaving
+                const long issued = k + kStages < mine ? k + kStages : mine;
+                for (long q = k; q < issued; ++q) tc::mbar_wait(&bar[q % kStages], (uint32_t)((q / kStages) & 1));
+            }
+            return;
+        }
         if (threadIdx.x == 0 && k + kStages < mine) {
             // generic-proxy reads of the stage above, async-proxy writes into it next
             tc::fence_async_smem();
@@ -130,8 +133,6 @@ __device__ __forceinline__ void run_items(const Params &P, const void *in_map, c
                                &bar[s]);
         }
         if (act) {
-            fft2::dft_reg<S, NA>(v);
-            fft2::twiddle<S, NA>(v, p, tw);
 #pragma unroll
             for (int k2 = 0; k2 < NA; ++k2) tile[(p * NA + k2) * W + w] = v[k2];
         }
