@@ -185,15 +185,18 @@ __global__ void __launch_bounds__(kDThreads, 1) direct_corr_kernel(const __grid_
         // copies issued by thread 0: the last box use and B use per slot (-1: none)
         long last_box = -1, last_b[kBSlots];
         for (int i = 0; i < kBSlots; ++i) last_b[i] = -1;
-        auto issue_box = [&](long k) {
+        // box use b = (tile k = b / nslab, slab b % nslab)
+        auto issue_box = [&](long b) {
+            const long k = b / a.nslab;
+            const int sl = (int)(b - k * a.nslab);
             const int t = (int)blockIdx.x + (int)k * G;
             const int tx = t % a.ntx, r = t / a.ntx, ty = r % a.nty, tz = r / a.nty;
             const int cx = 32 * tx - a.kx + a.vlo[0] + a.lox - a.sx;     // a multiple of 4
             const int cy = a.TY * ty - a.ky + a.vlo[1] + a.loy;
-            const int cz = a.TZ * tz - a.kz + a.vlo[2] + a.loz;
+            const int cz = a.TZ * tz - a.kz + a.vlo[2] + a.loz + a.slab_z0[sl];
             tc::mbar_expect_tx(boxfull, box_words * 4);
             tc::tma_load_3d(boxes, &box_map, cx, cy, cz, boxfull);
-            last_box = k;
+            last_box = b;
         };
         auto issue_b = [&](long g2) {
             const int slot = (int)(g2 % kBSlots);
@@ -209,12 +212,14 @@ __global__ void __launch_bounds__(kDThreads, 1) direct_corr_kernel(const __grid_
             if (mine > 0) issue_box(0);
             for (long g2 = 0; g2 < kBAhead && g2 < total; ++g2) issue_b(g2);
         }
-        long gc = 0;
+        long gc = 0, bu = 0;                      // chunks and box uses so far
+        const long units = mine * a.nslab;
         bool ok = true;
         for (long k = 0; k < mine; ++k) {
-            if (!(ok = tc::mbar_wait(boxfull, (uint32_t)(k & 1)))) break;
+          for (int sl = 0; sl < a.nslab; ++sl, ++bu) {
+            if (!(ok = tc::mbar_wait(boxfull, (uint32_t)(bu & 1)))) break;
             const uint32_t *box = boxes + base_m;
-            for (int c = 0; c < nchunk; ++c, ++gc) {
+            for (int c = a.slab_c0[sl]; c < a.slab_c0[sl + 1]; ++c, ++gc) {
                 const int s = (int)(gc & 1);
                 const uint32_t u = (uint32_t)(gc >> 1);
                 if (u > 0 && !(ok = tc::mbar_wait(&empty[s], (u - 1) & 1))) break;
@@ -252,14 +257,16 @@ __global__ void __launch_bounds__(kDThreads, 1) direct_corr_kernel(const __grid_
                 tc::mbar_arrive(&full[s]);
             }
             if (!ok) break;
-            // this tile's reads of the box are done: once every producer says so, thread 0 refills
-            // it with the next tile's box (generic-proxy reads before the async-proxy write)
+            // this slab's reads of the box are done: once every producer says so, thread 0 refills
+            // it with the next slab's or tile's box (generic-proxy reads before the async-proxy write)
             tc::mbar_arrive(boxfree);
-            if (threadIdx.x == 0 && k + 1 < mine) {
-                if (!(ok = tc::mbar_wait(boxfree, (uint32_t)(k & 1)))) break;
+            if (threadIdx.x == 0 && bu + 1 < units) {
+                if (!(ok = tc::mbar_wait(boxfree, (uint32_t)(bu & 1)))) break;
                 tc::fence_async_smem();
-                issue_box(k + 1);
+                issue_box(bu + 1);
             }
+          }
+          if (!ok) break;
             if (!(ok = tc::mbar_wait(dfull, (uint32_t)(k & 1)))) break;
             tc::fence_after();
             // epilogue: D row m, this warp's groups of 8 columns (= orientations of the group)

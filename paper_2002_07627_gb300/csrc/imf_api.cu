@@ -52,6 +52,16 @@ const char *kKernelNames[KID_COUNT] = {
     "finalize", "absmax_omega0", "penalize", "rho_hi_lo", "direct_corr_tcgen05", "sweep_levels", "fft_yx_inv_threshold",
     "process_plan"};
 
+// Geometry of one orientation group of the direct path: the union's smallest offset, the box of
+// rho_O words a tile reads per z-slab, the tile's x offset in it, and the slabs (first chunk and
+// first union z offset of each).
+struct DirectGroup {
+    int glo[3] = {0, 0, 0};
+    int BX = 0, BY = 0, BZ = 0, sx = 0, nslab = 1;
+    int c0[kDirectMaxSlabs + 1] = {0};
+    int z0[kDirectMaxSlabs] = {0};
+};
+
 struct Tool {
     bool set = false;
     int tx = 0, ty = 0, tz = 0, o[3] = {0, 0, 0}, n_orient = 0;
@@ -87,7 +97,7 @@ struct Tool {
     int dG = 0;                          // orientations per group
     std::vector<int> grp_start, grp_kpad, grp_N;
     std::vector<long> grp_tap_off, grp_b_off;
-    std::vector<std::array<int, 7>> grp_box;    // per group: union minimum (x, y, z), box BX BY BZ, sx
+    std::vector<DirectGroup> grp_geo;    // per group: union minimum, box, z-slabs
     int dTY = 2, dTZ = 2;                // tile of 32 x dTY x dTZ translations
     int *d_taps = nullptr;
     uint16_t *d_bmat = nullptr;
@@ -419,10 +429,11 @@ inline size_t tc_kmajor(int r, int k, int R) { return (size_t)(k >> 3) * (R * 16
 
 // Groups of consecutive orientations, their union tap lists (word offsets in the box of rho_O a
 // tile of the direct kernel reads) and B matrices (BF16 0/1, K-major canonical layout, N rows).
-// The group size minimises a cost model of the kernel: per tile and 64 taps of the union, the A
-// build (about 512 shared-memory wavefronts, whatever N) or the MMAs and their operand reads
-// (about 4.6 N + 256 cycles), whichever is larger, summed over the groups; groups whose box and
-// buffers do not fit shared memory are not taken.
+// A union too tall for one box in shared memory is cut into z-slabs (balanced, each slab's taps
+// padded to whole 64-tap chunks); the box is then loaded once per tile and slab. The group size
+// minimises a cost model of the kernel: per tile and 64 taps of the union, the A build (about 512
+// shared-memory wavefronts, whatever N) or the MMAs and their operand reads (about 4.6 N + 256
+// cycles), whichever is larger, summed over the groups.
 bool plan_direct(Tool &t, const int n[3], int vlo[3], int vhi[3], std::vector<int> &taps, std::vector<uint16_t> &bm)
 {
     for (int c = 0; c < 3; ++c) {
@@ -437,7 +448,12 @@ bool plan_direct(Tool &t, const int n[3], int vlo[3], int vhi[3], std::vector<in
     auto key = [&](const int32_t *v) {
         return ((long)(v[2] - vlo[2]) * EY + (v[1] - vlo[1])) * EX + (v[0] - vlo[0]);
     };
-    // union of a group as sorted keys, with its bounds
+    auto unkey = [&](long k, int v[3]) {
+        v[0] = (int)(k % EX) + vlo[0];
+        v[1] = (int)((k / EX) % EY) + vlo[1];
+        v[2] = (int)(k / ((long)EX * EY)) + vlo[2];
+    };
+    // union of a group as sorted keys (z-major), with its bounds
     auto group_union = [&](int o0, int nb, std::vector<long> &uni, int glo[3], int ghi[3]) {
         uni.clear();
         for (int c = 0; c < 3; ++c) { glo[c] = 1 << 30; ghi[c] = -(1 << 30); }
@@ -452,25 +468,67 @@ bool plan_direct(Tool &t, const int n[3], int vlo[3], int vhi[3], std::vector<in
         std::sort(uni.begin(), uni.end());
         uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
     };
-    auto box_of = [&](const int glo[3], const int ghi[3], int &BX, int &BY, int &BZ) {
-        BX = (3 + 32 + ghi[0] - glo[0] + 3) & ~3;
-        BY = t.dTY + ghi[1] - glo[1];
-        BZ = t.dTZ + ghi[2] - glo[2];
-        return BX <= 256 && BY <= 256 && BZ <= 256 &&
-               direct_smem_bytes(16, (long)BX * BY * BZ) <= kDirectSmemLimit;
+    // box and slabs of a group with MMA N: the tallest slab whose box fits, then balanced slabs
+    auto geometry = [&](const int glo[3], const int ghi[3], int N, DirectGroup &gg) {
+        gg.BX = (3 + 32 + ghi[0] - glo[0] + 3) & ~3;
+        gg.BY = t.dTY + ghi[1] - glo[1];
+        const int EZ = ghi[2] - glo[2] + 1;
+        int sz = 0;
+        for (int h = 1; h <= EZ; ++h) {
+            const int bz = t.dTZ + h - 1;
+            if (bz > 256 || direct_smem_bytes(N, (long)gg.BX * gg.BY * bz) > kDirectSmemLimit) break;
+            sz = h;
+        }
+        if (gg.BX > 256 || gg.BY > 256 || sz < 1) return false;
+        gg.nslab = (EZ + sz - 1) / sz;
+        if (gg.nslab > kDirectMaxSlabs) return false;
+        sz = (EZ + gg.nslab - 1) / gg.nslab;
+        gg.BZ = t.dTZ + sz - 1;
+        for (int c = 0; c < 3; ++c) gg.glo[c] = glo[c];
+        gg.sx = (((glo[0] - t.kmax[0] + t.dlo[0]) % 4) + 4) % 4;
+        for (int sl = 0; sl < gg.nslab; ++sl) gg.z0[sl] = sl * sz;
+        return true;
+    };
+    // padded tap order of a group: per slab, its taps (box word offsets) padded to whole chunks;
+    // pos[i] = padded index of union entry i
+    auto layout = [&](const std::vector<long> &uni, DirectGroup &gg, std::vector<int> *offs, std::vector<int> &pos) {
+        pos.assign(uni.size(), 0);
+        int np = 0;
+        size_t i = 0;
+        const int sz = gg.nslab > 1 ? gg.z0[1] : gg.BZ - t.dTZ + 1;
+        for (int sl = 0; sl < gg.nslab; ++sl) {
+            gg.c0[sl] = np / 64;
+            int v[3];
+            for (; i < uni.size(); ++i) {
+                unkey(uni[i], v);
+                if ((v[2] - gg.glo[2]) / sz != sl) break;
+                pos[i] = np++;
+                if (offs)
+                    offs->push_back((v[0] - gg.glo[0]) + gg.BX * ((v[1] - gg.glo[1]) + gg.BY * (v[2] - gg.glo[2] - gg.z0[sl])));
+            }
+            while (np % 64 || np == gg.c0[sl] * 64) {
+                ++np;
+                if (offs) offs->push_back(0);
+            }
+        }
+        gg.c0[gg.nslab] = np / 64;
+        return np;
     };
     int bestG = 0;
     double best = 1e300;
     std::vector<long> uni;
+    std::vector<int> pos;
     for (int G = std::min(256, (t.n_orient + 15) / 16 * 16); G >= 16; G -= 16) {
         bool fits = true;
         double cost = 0;
         for (int o0 = 0; o0 < t.n_orient && fits; o0 += G) {
             const int nb = std::min(G, t.n_orient - o0), N = (nb + 15) / 16 * 16;
-            int glo[3], ghi[3], BX, BY, BZ;
+            int glo[3], ghi[3];
+            DirectGroup gg;
             group_union(o0, nb, uni, glo, ghi);
-            fits = box_of(glo, ghi, BX, BY, BZ) && direct_smem_bytes(N, (long)BX * BY * BZ) <= kDirectSmemLimit;
-            const int kpad = std::max(64, (int)((uni.size() + 63) / 64 * 64));
+            fits = geometry(glo, ghi, N, gg);
+            if (!fits) break;
+            const int kpad = layout(uni, gg, nullptr, pos);
             cost += kpad * std::max(512.0, 4.6 * N + 256.0);
         }
         if (fits && cost < best) {
@@ -482,38 +540,29 @@ bool plan_direct(Tool &t, const int n[3], int vlo[3], int vhi[3], std::vector<in
     const int G = bestG;
     std::vector<int> gs, gk, gn;
     std::vector<long> gto, gbo;
-    std::vector<std::array<int, 7>> gbox;
+    std::vector<DirectGroup> geo;
     std::vector<int> tp;
     std::vector<uint16_t> b;
     double macs = 0;
     for (int o0 = 0; o0 < t.n_orient; o0 += G) {
         const int nb = std::min(G, t.n_orient - o0), N = (nb + 15) / 16 * 16;
-        int glo[3], ghi[3], BX, BY, BZ;
+        int glo[3], ghi[3];
+        DirectGroup gg;
         group_union(o0, nb, uni, glo, ghi);
-        box_of(glo, ghi, BX, BY, BZ);
-        const int kpad = std::max(64, (int)((uni.size() + 63) / 64 * 64));
-        const int sx = (((glo[0] - t.kmax[0] + t.dlo[0]) % 4) + 4) % 4;
+        geometry(glo, ghi, N, gg);
         gs.push_back(o0);
-        gk.push_back(kpad);
-        gn.push_back(N);
-        gbox.push_back({glo[0], glo[1], glo[2], BX, BY, BZ, sx});
         gto.push_back((long)tp.size());
         gbo.push_back((long)b.size());
-        for (int k = 0; k < kpad; ++k) {
-            int off = 0;
-            if (k < (int)uni.size()) {
-                const long kx = uni[k] % EX, ky = (uni[k] / EX) % EY, kz = uni[k] / ((long)EX * EY);
-                const int vx = (int)kx + vlo[0], vy = (int)ky + vlo[1], vz = (int)kz + vlo[2];
-                off = (vx - glo[0]) + BX * ((vy - glo[1]) + BY * (vz - glo[2]));
-            }
-            tp.push_back(off);
-        }
+        const int kpad = layout(uni, gg, &tp, pos);
+        gk.push_back(kpad);
+        gn.push_back(N);
+        geo.push_back(gg);
         const size_t b0 = b.size();
         b.resize(b0 + (size_t)N * kpad, 0);
         for (int i = o0; i < o0 + nb; ++i)
             for (size_t m = 0; m < t.rt[i].size(); m += 3) {
                 const int k = (int)(std::lower_bound(uni.begin(), uni.end(), key(&t.rt[i][m])) - uni.begin());
-                b[b0 + tc_kmajor(i - o0, k, N) / 2] = 0x3F80;    // BF16 1.0
+                b[b0 + tc_kmajor(i - o0, pos[k], N) / 2] = 0x3F80;    // BF16 1.0
             }
         const long tiles = (long)((t.win[0] + 31) / 32) * ((t.win[1] + t.dTY - 1) / t.dTY) *
                            ((t.win[2] + t.dTZ - 1) / t.dTZ);
@@ -526,7 +575,7 @@ bool plan_direct(Tool &t, const int n[3], int vlo[3], int vhi[3], std::vector<in
     t.grp_N = gn;
     t.grp_tap_off = gto;
     t.grp_b_off = gbo;
-    t.grp_box = gbox;
+    t.grp_geo = geo;
     t.direct_macs = macs;
     taps.swap(tp);
     bm.swap(b);
@@ -1282,9 +1331,12 @@ static imf_status compute_impl(imf_handle h, const float *rho, const uint8_t *fi
                     a.lox = t.dlo[0]; a.loy = t.dlo[1]; a.loz = t.dlo[2];
                     a.tapoff = t.d_taps + t.grp_tap_off[gi]; a.kpad = t.grp_kpad[gi];
                     a.bmat = t.d_bmat + t.grp_b_off[gi]; a.N = t.grp_N[gi]; a.nb = nb;
-                    const std::array<int, 7> &bx = t.grp_box[gi];
-                    a.vlo[0] = bx[0]; a.vlo[1] = bx[1]; a.vlo[2] = bx[2];
-                    a.BX = bx[3]; a.BY = bx[4]; a.BZ = bx[5]; a.sx = bx[6];
+                    const DirectGroup &gg = t.grp_geo[gi];
+                    a.vlo[0] = gg.glo[0]; a.vlo[1] = gg.glo[1]; a.vlo[2] = gg.glo[2];
+                    a.BX = gg.BX; a.BY = gg.BY; a.BZ = gg.BZ; a.sx = gg.sx;
+                    a.nslab = gg.nslab;
+                    for (int sl = 0; sl <= gg.nslab; ++sl) a.slab_c0[sl] = gg.c0[sl];
+                    for (int sl = 0; sl < gg.nslab; ++sl) a.slab_z0[sl] = gg.z0[sl];
                     a.TY = t.dTY; a.TZ = t.dTZ;
                     a.wx = t.win[0]; a.wy = t.win[1]; a.wz = t.win[2];
                     a.kx = t.kmax[0]; a.ky = t.kmax[1]; a.kz = t.kmax[2];

@@ -187,6 +187,8 @@ void launch_plan_remove(const uint32_t *set, long words, uint32_t *remaining, cu
 // Tiled minimum over sharp points: erode.cuh.
 
 // Direct collision convolution on the tensor cores (direct_tc.cu).
+// most z-slabs the direct path splits one orientation group's union into
+constexpr int kDirectMaxSlabs = 32;
 struct DirectArgs {
     const uint32_t *rhohl;       // padded rho_O as (hi | lo << 16) BF16 pairs, [PZ][PY][PX], PX % 4 == 0
     int PX, PY, PZ;              // padded extents
@@ -196,7 +198,10 @@ struct DirectArgs {
     const uint16_t *bmat;        // B [N x kpad] BF16 0/1 in the K-major canonical layout
     int N, nb;                   // MMA N (multiple of 16) and orientations in the group
     int vlo[3];                  // smallest union offset of the group (x, y, z)
-    int BX, BY, BZ;              // box of rho_O words a tile reads (BX % 4 == 0)
+    int BX, BY, BZ;              // box of rho_O words a tile reads per z-slab (BX % 4 == 0)
+    int nslab;                   // z-slabs of the union: the box is loaded once per tile and slab
+    int slab_c0[kDirectMaxSlabs + 1];  // first 64-tap chunk of each slab (slab_c0[nslab] = kpad / 64)
+    int slab_z0[kDirectMaxSlabs];      // first union z offset of each slab, relative to vlo[2]
     int sx;                      // x offset of the tile's first translation in its box (0..3)
     int TY, TZ;                  // tile of 32 x TY x TZ = 128 translations (TY TZ = 4)
     int wx, wy, wz, kx, ky, kz;  // translation window and kmax (t = window index - kmax)
