@@ -315,7 +315,8 @@ imf_status imf_get_tool_info(imf_handle h, int tool_id, imf_tool_info *out);
 
 /* Select the collision path of a tool: IMF_FP32_FFT (needs the spectra, i.e. the handle was not
  * created with IMF_BF16_DIRECT) or IMF_BF16_DIRECT (available when every orientation group's
- * union of rotated tool voxels fits the tensor-core kernel). Synchronous. With IMF_AUTO the
+ * union of rotated tool voxels fits the tensor-core kernel in at most 32 z-slabs of a tile's
+ * shared-memory box, which holds for tools tens of voxels across). Synchronous. With IMF_AUTO the
  * path starts as IMF_FP32_FFT and imf_autotune keeps the faster of the two.
  * Errors: IMF_ERR_INVALID_ARG when the path is not available. */
 imf_status imf_set_path(imf_handle h, int tool_id, int path);
