@@ -321,7 +321,8 @@ def run_serve(args):
         tool = synth.cylinder_tool(3, 20, 8, 16, synth.fibonacci_quats(nr))
         specs[i] = DesignSpec(rho.shape, [tool], fix)
         rhos[i] = rho
-    srv = ImfServer(GpuExecutor(args.streams), hbm_budget=int(args.serve_budget_gb * (1 << 30)), slots=args.streams)
+    srv = ImfServer(GpuExecutor(args.streams, high_priority_slots=args.serve_high_prio),
+                    hbm_budget=int(args.serve_budget_gb * (1 << 30)), slots=args.streams)
     for i, sp in specs.items():
         srv.register(i, sp)
     # warm every design once (setup: tool spectra), then measure each rate
@@ -355,7 +356,8 @@ def run_serve(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"served IMF: {len(specs)} TO loops, cubic grids 64-{args.serve_max_grid} "
                                   f"log-uniform, 32-128 orientations, Poisson arrivals",
-                      "slots": args.streams, "hbm_budget_gb": args.serve_budget_gb},
+                      "slots": args.streams, "high_priority_slots": args.serve_high_prio,
+                      "hbm_budget_gb": args.serve_budget_gb},
            "rates": rates, "evictions": st.evictions, "creations": st.creations,
            "max_running": st.max_running}
     print(json.dumps(out), flush=True)
@@ -929,6 +931,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[50, 200, 500, 1000, 2000])
+    ap.add_argument("--serve-high-prio", type=int, default=0,
+                    help="stream slots at high priority for small requests (-1: half of them, 0: none)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -103,6 +103,7 @@ class ImfServer:
         self.max_inflight = max(1, int(max_inflight)) if hasattr(executor, "add_context") else 1
         self.poll_s = poll_s
         self.specs = {}
+        self.small_units = 0
         self.resident = collections.OrderedDict()   # design_id -> _Resident (LRU order)
         self.pending = collections.deque()
         self.running = {}                           # slot -> (req, token)
@@ -117,6 +118,20 @@ class ImfServer:
     def register(self, design_id, spec: DesignSpec):
         with self._lock:
             self.specs[design_id] = spec
+            # requests at most this size (voxel-orientations) count as small: the median design
+            units = sorted(sp.units for sp in self.specs.values())
+            self.small_units = units[(len(units) - 1) // 2]
+
+    def _pick_slot(self, free, design_id):
+        """A free slot for a request: with an executor that reports stream priorities, small
+        requests take a high-priority slot and large ones a low-priority slot when one is free."""
+        prio = getattr(self.ex, "slot_priority", None)
+        if prio is not None:
+            want = 1 if self.specs[design_id].units <= self.small_units else 0
+            for i, sl in enumerate(free):
+                if prio(sl) == want:
+                    return free.pop(i)
+        return free.pop(0)
 
     def submit(self, design_id, rho: np.ndarray) -> Future:
         fut = Future()
@@ -241,7 +256,7 @@ class ImfServer:
                 self.resident[req.design_id] = r
                 self.stats.creations += 1
                 self.stats.max_resident_bytes = max(self.stats.max_resident_bytes, self._resident_bytes())
-            slot = free.pop(0)
+            slot = self._pick_slot(free, req.design_id)
             self.resident.move_to_end(req.design_id)
             ctx = r.free.pop(0)
             try:
@@ -279,14 +294,24 @@ class ImfServer:
 class GpuExecutor:
     """Runs requests through libimf on a pool of CUDA streams, one stream per slot."""
 
-    def __init__(self, slots: int, device: int = 0, orient_batch: int = 16):
+    def __init__(self, slots: int, device: int = 0, orient_batch: int = 16, high_priority_slots: int = 0):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
-        self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
+        # the first `high_priority_slots` streams (-1: half of them; none by default) get the
+        # device's highest stream priority, and the server puts small requests there so that their
+        # blocks are scheduled ahead of a large request's. It lowers the median latency under
+        # light load but starves the large requests: the 99th percentile grows at every rate
+        nhi = slots // 2 if high_priority_slots < 0 else min(slots, high_priority_slots)
+        self._prio = [1 if i < nhi else 0 for i in range(slots)]
+        self.streams = [torch.cuda.Stream(self.dev, priority=-1 if i < nhi else 0) for i in range(slots)]
         # orientations per device batch of every served handle; the admission footprint counts
         # the work buffers of exactly that many slots
         self.orient_batch = int(orient_batch)
+
+    def slot_priority(self, slot: int) -> int:
+        """1 for a high-priority stream, 0 otherwise."""
+        return self._prio[slot]
 
     def footprint(self, spec: DesignSpec) -> int:
         """Bytes a served design holds on the device: the library's planned footprint (spectra,

@@ -210,3 +210,50 @@ def test_several_requests_of_one_design_run_on_their_own_contexts():
     assert [f.result(timeout=30)[1] for f in futs] == [16 * k for k in range(8)]
     srv.close()
     assert ex.max_ctx_running == 1 and ex.max_bytes <= 100
+
+
+class FakePrioExecutor(FakeExecutor):
+    """A fake executor whose first two of four slots are high-priority streams; it records the
+    slot priority each design's launches got."""
+
+    def __init__(self, sizes, duration=0.01):
+        super().__init__(sizes, duration)
+        self.prio_of = {}
+
+    def slot_priority(self, slot):
+        return 1 if slot < 2 else 0
+
+    def launch(self, st, rho, slot):
+        with self.lock:
+            self.prio_of.setdefault(st["id"], set()).add(self.slot_priority(slot))
+        return super().launch(st, rho, slot)
+
+
+def test_small_requests_take_high_priority_slots():
+    """With an executor that reports stream priorities, requests of designs no larger than the
+    median registered design go to high-priority slots and larger ones to low-priority slots
+    whenever a slot of the wanted kind is free; every result is still right."""
+    ex = FakePrioExecutor({i: 10 for i in range(4)})
+    srv = ImfServer(ex, hbm_budget=1000, slots=4)
+    tool = synth.planar_tool(n_orient=2)
+    shapes = {0: (1, 4, 4), 1: (1, 4, 4), 2: (1, 12, 12), 3: (1, 12, 12)}
+    for i, sh in shapes.items():
+        srv.register(i, DesignSpec(sh, [tool], fixture=i))
+    assert srv.small_units == 4 * 4 * 2
+    # one wave of four requests, one per design, queued while the server loop waits on its lock,
+    # so that one admission pass places all four into the four free slots
+    from concurrent.futures import Future
+    from paper_2002_07627_gb300.serve import _Req
+    futs = []
+    with srv._lock:
+        for i in range(4):
+            f = Future()
+            srv.pending.append(_Req(i, np.full(shapes[i], i + 1, np.float32), time.perf_counter(), f))
+            futs.append((i, f))
+        srv._wake.notify()
+    for i, f in futs:
+        did, s = f.result(timeout=30)
+        assert did == i and s == (i + 1) * np.prod(shapes[i])
+    srv.close()
+    assert ex.prio_of[0] == {1} and ex.prio_of[1] == {1}
+    assert ex.prio_of[2] == {0} and ex.prio_of[3] == {0}
