@@ -314,8 +314,8 @@ def run_serve(args):
     rng = np.random.default_rng(0)
     specs, rhos = {}, {}
     for i in range(args.serve_loops):
-        n = int(round(np.exp(rng.uniform(np.log(64), np.log(args.serve_max_grid)))))
-        nr = int(rng.integers(32, 129))
+        n = int(round(np.exp(rng.uniform(np.log(args.serve_min_grid), np.log(args.serve_max_grid)))))
+        nr = int(rng.integers(args.serve_orient[0], args.serve_orient[1] + 1))
         rho = synth.beam_density((n, n, n), n_beams=max(4, int(40 * (n / 128) ** 2)), seed=100 + i)
         fix = synth.slab_fixture(rho.shape, max(2, n // 24), axis="z")
         tool = synth.cylinder_tool(3, 20, 8, 16, synth.fibonacci_quats(nr))
@@ -354,8 +354,9 @@ def run_serve(args):
     out = {"metric": METRIC, "value": best["throughput"], "unit": UNIT, "n_gpus": 1,
            "steps": sum(r["requests"] for r in rates), "warmup": len(specs), "ms_per_step": best["p50_ms"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"served IMF: {len(specs)} TO loops, cubic grids 64-{args.serve_max_grid} "
-                                  f"log-uniform, 32-128 orientations, Poisson arrivals",
+           "config": {"workload": f"served IMF: {len(specs)} TO loops, cubic grids {args.serve_min_grid}-"
+                                  f"{args.serve_max_grid} log-uniform, {args.serve_orient[0]}-{args.serve_orient[1]} "
+                                  f"orientations, Poisson arrivals",
                       "slots": args.streams, "high_priority_slots": args.serve_high_prio,
                       "hbm_budget_gb": args.serve_budget_gb},
            "rates": rates, "evictions": st.evictions, "creations": st.creations,
@@ -927,7 +928,9 @@ def main():
     ap.add_argument("--batch-designs", type=int, default=64)
     ap.add_argument("--streams", type=int, default=8)
     ap.add_argument("--serve-loops", type=int, default=8)
+    ap.add_argument("--serve-min-grid", type=int, default=64)
     ap.add_argument("--serve-max-grid", type=int, default=256)
+    ap.add_argument("--serve-orient", type=int, nargs=2, default=[32, 128], metavar=("MIN", "MAX"))
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[50, 200, 500, 1000, 2000])
