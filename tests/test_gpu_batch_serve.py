@@ -45,7 +45,7 @@ def _check_vs_oracle(d, fbar, sec, lam=0.01):
     """f_bar and Gamma of one design against the FP64 oracle, away from the allowance
     discontinuity (the IMF contract of the plain form)."""
     ref = oracle.imf(d)
-    # away from the allowance discontinuity, judged on f / M before the allowance
+    # away from the allowance discontinuity, compared on f / M before the allowance
     M = float(ref["M"])
     pre = ref["f"] / M if M > 0 else np.zeros_like(ref["f"])
     clear = np.abs(pre - lam) > 1e-4

@@ -86,7 +86,7 @@ def check_against_oracle(design, got, ref, theta_rel=0.01, lam=0.01):
     # the oracle's own accessible set obeys the same bounds (pins the bound computation)
     Ao = ref["accessible"] != 0
     assert not (sure & om0 & ~Ao).any() and not (Ao & ~sure & ~maybe).any()
-    # f_bar and Gamma away from the allowance discontinuity, judged on the normalised IMF before
+    # f_bar and Gamma away from the allowance discontinuity, compared on the normalised IMF before
     # the allowance (f / M): after it, a point just below lambda reads 0 and would look clear
     M = float(ref["M"])
     pre = ref["f"] / M if M > 0 else np.zeros_like(ref["f"])
