@@ -78,7 +78,9 @@ def test_batch_runner_graphs_and_autotune_match_plain_compute():
     br.close()
 
 
-def test_served_result_is_the_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("high_prio", [0, 2])
+def test_served_result_is_the_same_alone_and_in_the_mix(high_prio):
+    """high_prio: stream slots at the device's highest priority (small requests go there)."""
     _need_gpu()
     from paper_2002_07627_gb300.serve import DesignSpec, GpuExecutor, ImfServer
     ds = _designs()
@@ -89,7 +91,7 @@ def test_served_result_is_the_same_alone_and_in_the_mix():
     alone = srv.submit("a", ds[0].rho).result(timeout=120)
     srv.close()
     # in the mix: other designs' requests before, around and after it, 3 slots
-    srv = ImfServer(GpuExecutor(3), hbm_budget=8 << 30, slots=3)
+    srv = ImfServer(GpuExecutor(3, high_priority_slots=high_prio), hbm_budget=8 << 30, slots=3)
     for i, s in enumerate(specs):
         srv.register(i, s)
     futs = []
