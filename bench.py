@@ -406,8 +406,10 @@ def kernel_rooflines(imf, info, shape, n_orient, steps, sweep_route, workload):
             ab = algorithmic_bytes(name, info, shape, nb, bits=sweep_route)
             if ab is not None:
                 ach = ab / avg_s / 1e9
+                # the inverse passes' traffic grows with the orientations of a launch
+                per_o = nb if name in ("fft_z_inv_mul", "fft_y_inv", "irfft_x_threshold") else None
                 e.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                          "traffic": traffic_record(name, workload), "peak_source": peak_src,
+                          "traffic": traffic_record(name, workload, per_o), "peak_source": peak_src,
                           "algorithmic_bytes_per_launch": ab})
             else:
                 e.update({"bound": "latency", "note": "no fixed algorithmic byte count (work depends on the data)"})
