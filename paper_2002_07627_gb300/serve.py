@@ -19,6 +19,7 @@ from __future__ import annotations
 import collections
 import threading
 import time
+import warnings
 from concurrent.futures import Future
 from dataclasses import dataclass, field
 
@@ -374,7 +375,11 @@ class GpuExecutor:
         torch = self.torch
         s = self.streams[slot]
         c = st["ctxs"][ctx]
-        c["h_rho"].numpy()[...] = rho
+        # host copies through torch (several threads, without the interpreter lock) rather than
+        # numpy: at 256^3 a request moves 64 MB in and 80 MB out on the host
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore", UserWarning)      # read-only inputs are only read
+            c["h_rho"].copy_(torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float32)))
         with torch.cuda.stream(s):
             c["rho"].copy_(c["h_rho"], non_blocking=True)
             c["imf"].compute(c["rho"], st["fix"], c["fbar"], c["sec"], stream=s)
@@ -391,4 +396,4 @@ class GpuExecutor:
         ev, c = token
         ev.synchronize()
         c["imf"].sync()
-        return c["h_fbar"].numpy().copy(), c["h_sec"].numpy().copy()
+        return c["h_fbar"].clone().numpy(), c["h_sec"].clone().numpy()
