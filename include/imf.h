@@ -323,18 +323,26 @@ imf_status imf_set_path(imf_handle h, int tool_id, int path);
 
 /* Tensor-core self-test: D[128 x N] = A[128 x K] B[N x K]^T for HOST row-major BF16 bit
  * patterns A, B and a HOST FP32 result D, computed by the same tcgen05 / TMEM / descriptor
- * code the direct path uses (N a multiple of 16 in [16, 256], K a multiple of 16). Synchronous. */
+ * code the direct path uses (N a multiple of 16 in [16, 256], K a multiple of 16, both operands
+ * within 200 KB of shared memory: (128 + N) K 2 bytes). Synchronous; not tied to a handle.
+ * Errors: IMF_ERR_INVALID_ARG (NULL, N or K out of range; checked before any allocation),
+ * IMF_ERR_OOM, IMF_ERR_CUDA, IMF_ERR_TIMEOUT (a bounded wait of the kernel ran out). */
 imf_status imf_selftest_mma(int N, int K, const uint16_t *A, const uint16_t *B, float *D);
 
 /* Copy the resampled offsets of one orientation to HOST int32 [n][3] (x, y, z) arrays:
  * which = 0 (R T), 1 (R K), 2 (sharp points). *n receives the count; `out` may be NULL to
- * query it; `cap` is the capacity of `out` in triples. Synchronous. */
+ * query it; `cap` is the capacity of `out` in triples. Synchronous.
+ * Errors: IMF_ERR_INVALID_ARG (NULL h or n, tool not set, orient or which out of range, cap
+ * below the count). */
 imf_status imf_get_offsets(imf_handle h, int tool_id, int orient, int which, int32_t *out,
                            long cap, long *n);
 
 /* Copy the last batch's collision field g (FP32, the translation window of `tool_id`) and
  * its free bits into HOST buffers, for tests: the last orientation batch of the last
- * imf_compute is kept when `keep` was enabled with imf_set_debug. Synchronous. */
+ * imf_compute is kept when `keep` was enabled with imf_set_debug. g_out may be NULL to read
+ * only the caller's orientation index of the slot. Synchronous.
+ * Errors: IMF_ERR_INVALID_ARG (NULL handle, no batch computed yet, slot out of range, cap
+ * below the window's floats). */
 imf_status imf_set_debug(imf_handle h, int keep_last_g);
 imf_status imf_get_last_g(imf_handle h, int slot, float *g_out, long cap, int *orient_out);
 
@@ -355,6 +363,7 @@ typedef struct {
     size_t owned_bytes;      /* device bytes the handle owns now                           */
 } imf_stats;
 
+/* Errors: IMF_ERR_INVALID_ARG (NULL). */
 imf_status imf_get_stats(imf_handle h, imf_stats *out);
 
 /* Device footprint of a handle, from the plan of its tools (the sizes App. B's memory-budgeted
@@ -377,7 +386,8 @@ imf_status imf_footprint(imf_handle h, int slots, imf_footprint_info *out);
 /* Per-kernel timing with CUDA events on the launching stream (off by default). When on,
  * every launch is bracketed by events; imf_get_kernel_times accumulates their durations. */
 imf_status imf_set_profiling(imf_handle h, int on);
-/* name/ms/count of kernel class `i` (0 <= i < n_kernels); synchronizes the handle's stream. */
+/* name/ms/count of kernel class `i` (0 <= i < n_kernels); synchronizes the handle's stream.
+ * These three return IMF_ERR_INVALID_ARG for a NULL handle (and i out of range). */
 imf_status imf_get_kernel_time(imf_handle h, int i, const char **name, double *total_ms,
                                long *count);
 imf_status imf_reset_kernel_times(imf_handle h);

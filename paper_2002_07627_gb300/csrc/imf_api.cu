@@ -1757,6 +1757,9 @@ imf_status imf_set_path(imf_handle h, int tool_id, int path)
 imf_status imf_selftest_mma(int N, int K, const uint16_t *A, const uint16_t *B, float *D)
 {
     if (!A || !B || !D) return IMF_ERR_INVALID_ARG;
+    // the shapes the self-test kernel takes (checked again by its launcher), before any allocation
+    if (N < 16 || N > 256 || N % 16 || K < 16 || K % 16 || (128L + N) * K * 2 + 64 > 200L * 1024)
+        return IMF_ERR_INVALID_ARG;
     uint16_t *dA = nullptr, *dB = nullptr;
     float *dD = nullptr;
     int *dst = nullptr;

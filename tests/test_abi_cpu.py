@@ -119,6 +119,22 @@ def test_default_options_and_create_checks(lib):
     lib.imf_destroy(None)
 
 
+def test_mma_selftest_rejects_bad_shapes_on_the_host(lib):
+    """The tensor-core self-test checks N, K and the operands' shared-memory size before any
+    allocation (the arrays below are never read): N outside [16, 256] or not a multiple of 16,
+    K below 16 or not a multiple of 16, and (128 + N) K 2 bytes above 200 KB are refused."""
+    import ctypes
+    f = lib.imf_selftest_mma
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    a = (ctypes.c_uint16 * 16)()
+    d = (ctypes.c_float * 16)()
+    for n, k in ((0, 16), (8, 16), (24, 16), (272, 16), (16, 0), (16, 8), (16, 24), (16, -16),
+                 (256, 512), (16, 720)):
+        assert f(n, k, ctypes.addressof(a), ctypes.addressof(a), ctypes.addressof(d)) == 1, (n, k)
+    assert f(16, 16, None, ctypes.addressof(a), ctypes.addressof(d)) == 1
+
+
 def test_noalloc_penalty_rejects_bad_arguments_on_the_host(lib):
     """The allocation-free penalty checks its arguments before any CUDA call: NULL arrays,
     n < 1, n above the scratch limit, w_acc outside [0, 1) and tau outside [0, 1] are refused
